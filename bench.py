@@ -1,0 +1,331 @@
+"""Benchmark of the cased-well simulator on the 20 m full-scale well.
+
+Workload: Nr = 180 (dr 2.5 mm) + 16 PML cells, Ntheta = 64, Nz = 8192
+(dz 2.5 mm) + 2 x 16 PML cells = 103,215,104 cells, FP32, graded cement top,
+correlated rock noise, 8 kHz axis monopole, 16 axis receivers.  One bench
+step = `--chunk` leapfrog steps (one CUDA-graph replay) of the whole grid;
+the metric is cell-updates per second including PML cells.  The state
+(3.7 GB of fields) is far larger than L2, so no flush is needed between
+steps.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+Under torchrun every rank runs an independent replica on its own GPU
+(the single-well problem does not shard without a halo exchange) and
+rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2302_13907_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def alg_bytes_split(g, elem=4):
+    """Algorithmic bytes per cell-update of the split kernels: each field read
+    once and written once where updated, the material ID read once, PML memory
+    variables read and written in their slabs."""
+    cells = g.nth * g.NR * g.NZ
+    fr = g.pml_r / g.NR
+    fz = 2 * g.pml_z / g.NZ
+    vel = 9 * elem + 2 + 3 * elem + fr * 6 * 8 + fz * 3 * 8
+    strs = 9 * elem + 2 + 6 * elem + fr * 6 * 8 + fz * 3 * 8
+    return cells, vel, strs
+
+
+def cpu_sample(sc, seconds=15.0, nz=128):
+    """Oracle on a bounded sample of the workload: the full radius and azimuth
+    of the well, `nz` interior cells around the source, as many steps as fit
+    in ~`seconds` of host time."""
+    import oracle
+    from paper_2302_13907_gb300 import workloads as W
+
+    g = sc.grid
+    ks = int(round(sc.source.z / g.dz))
+    k0 = max(0, ks - nz // 2)
+    crop = W.crop_z(sc.medium, k0, nz)
+    sub = W.Scenario("sample", crop, W.Source(z=sc.source.z - k0 * g.dz, f0=sc.source.f0),
+                     W.on_axis_receivers([sc.source.z - k0 * g.dz]), cfl=sc.cfl, steps=100000)
+    o = oracle.Oracle(sub, max_steps=100000)
+    t0 = time.perf_counter()
+    o.step(5)
+    t1 = time.perf_counter()
+    n = max(5, int(seconds / max((t1 - t0) / 5, 1e-6)))
+    t0 = time.perf_counter()
+    o.step(n)
+    t1 = time.perf_counter()
+    cells = crop.grid.nth * crop.grid.NR * crop.grid.NZ
+    return dict(value=cells * n / (t1 - t0) / 1e9, unit=METRIC, cores=oracle.max_threads(), kind="oracle",
+                sample=f"FP64 oracle, {crop.grid.nth}x{crop.grid.NR}x{crop.grid.NZ} z-crop around the source "
+                       f"({cells} cells), {n} steps, {t1 - t0:.1f} s"), (cells, o)
+
+
+def run_reference(args, ws, rank):
+    """--impl reference: the FP64 CPU oracle on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    from paper_2302_13907_gb300 import workloads as W
+    import oracle
+
+    sc = W.config2()
+    g = sc.grid
+    ks = int(round(sc.source.z / g.dz))
+    nz = 128
+    k0 = max(0, ks - nz // 2)
+    crop = W.crop_z(sc.medium, k0, nz)
+    sub = W.Scenario("sample", crop, W.Source(z=sc.source.z - k0 * g.dz, f0=sc.source.f0),
+                     W.on_axis_receivers([sc.source.z - k0 * g.dz]), cfl=sc.cfl, steps=100000)
+    o = oracle.Oracle(sub, max_steps=100000)
+    cells = crop.grid.nth * crop.grid.NR * crop.grid.NZ
+    per = 10  # leapfrog steps per bench step
+    for _ in range(args.warmup):
+        o.step(per)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(per)
+    dt = time.perf_counter() - t0
+    v = cells * per * args.steps / dt / 1e9
+    line = {"metric": METRIC, "value": v, "unit": METRIC, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": sc.name + " (bounded z-crop sample around the source, FP64 oracle)",
+                       "sample_cells": cells, "steps_per_bench_step": per},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"{crop.grid.nth}x{crop.grid.NR}x{crop.grid.NZ} crop, {per} steps per bench step"},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--chunk", type=int, default=200, help="leapfrog steps per bench step")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        pg = dist
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    from paper_2302_13907_gb300 import workloads as W
+    from paper_2302_13907_gb300.binding import Simulation
+
+    sc = W.config2()
+    g = sc.grid
+    cells = g.nth * g.NR * g.NZ
+    K, Wm, T = args.steps, args.warmup, args.chunk
+    stream = torch.cuda.current_stream()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if uuid and not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+
+    # ---------------- headline: device-resident, graph replays of T steps
+    sim = Simulation(sc, storage=args.storage, kernel=args.kernel, graph_chunk=T, stream=stream.cuda_stream,
+                     max_steps=(K + Wm) * T + 1)
+    for _ in range(Wm):
+        sim.step(T)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = Clocks(uuid)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        sim.step(T)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if pg:
+        pg.barrier()
+    ms = e0.elapsed_time(e1)
+    sim.sync()
+    bytes_held = sim.device_bytes
+    sim.close()
+    del sim
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * cells * T * K / (ms / 1e3) / 1e9
+
+    # ---------------- roofline: per-kernel CUDA events on the launching stream
+    peak, peak_kind = _peaks()
+    elem = 4 if args.storage == "f32" else 2
+    _, b_vel, b_str = alg_bytes_split(g, elem)
+    tsim = Simulation(sc, storage=args.storage, kernel=args.kernel, stream=stream.cuda_stream, timing=True,
+                      max_steps=64)
+    tsim.step(3)
+    base = [tsim.kernel_time(q) for q in range(3)]
+    tsim.step(30)
+    kt = [tsim.kernel_time(q) for q in range(3)]
+    tsim.close()
+    avg = [(kt[q][0] - base[q][0]) / max(1, kt[q][1] - base[q][1]) for q in range(3)]
+    names = ["vel_split", "str_split", "receivers"]
+    qd = 0 if avg[0] >= avg[1] else 1
+    alg = (b_vel if qd == 0 else b_str) * cells
+    achieved = alg / (avg[qd] / 1e3) / 1e9
+    traffic = None
+    tj = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tj):
+        d = json.load(open(tj))
+        ent = d.get("kernels", {}).get(names[qd])
+        if ent and d.get("kernel_hash") == kernel_hash() and ent.get("cells") :
+            traffic = ent["dram_bytes_per_launch"] * cells / ent["cells"]
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": names[qd], "peak_source": f"{peak_kind} hbm_gbs (copy)",
+            "alg_bytes_per_cell": b_vel if qd == 0 else b_str,
+            "kernel_ms": {names[q]: avg[q] for q in range(3)}}
+
+    # ---------------- end to end through the C-ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.empty(sc.medium.cell_id.shape, dtype=torch.int16, pin_memory=True)
+        pinned.numpy().view(np.uint16)[...] = sc.medium.cell_id
+        med_p = W.Medium(g, pinned.numpy().view(np.uint16), sc.medium.rho, sc.medium.vp, sc.medium.vs)
+        sc_p = W.Scenario(sc.name, med_p, sc.source, sc.receivers, sc.cfl, sc.steps)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        s2 = Simulation(sc_p, storage=args.storage, kernel=args.kernel, graph_chunk=T, stream=stream.cuda_stream,
+                        max_steps=K * T)
+        for _ in range(K):
+            s2.step(T)
+        tr = s2.traces()
+        s2.close()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([wall], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            wall = float(t.item())
+        h2d = sc.medium.cell_id.nbytes + sc.medium.rho.nbytes * 4
+        e2e = {"value": ws * cells * T * K / wall / 1e9, "unit": METRIC, "h2d_bytes_per_step": h2d / K,
+               "d2h_bytes_per_step": tr.nbytes / K,
+               "note": "sim_create from pinned host arrays + K x sim_step + sim_traces + sim_destroy, wall clock"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu, _ = cpu_sample(sc)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": K, "warmup": Wm,
+                "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": args.storage if args.storage != "f32" else "f32", "data": "synthetic",
+                "config": {"workload": f"{sc.name}: Nr=180+16 PML, Ntheta=64, Nz=8192+2x16 PML, dr=dz=2.5 mm, "
+                                       f"graded cement top, rock noise, 8 kHz monopole, 16 receivers",
+                           "cells": cells, "leapfrog_steps_per_bench_step": T, "kernel": args.kernel,
+                           "storage": args.storage, "parallelism": f"replicas x{ws}",
+                           "l2": f"inputs larger than L2 ({bytes_held / 1e9:.1f} GB resident)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": K * T * 3, "clocks": ck}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

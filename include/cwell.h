@@ -1,0 +1,168 @@
+/*
+ * cwell.h -- C-ABI of the GB300 cased-well acoustic simulator.
+ *
+ * The library advances the first-order velocity-stress system of elasticity
+ * in cylindrical coordinates (r, theta, z) -- Eq. 1 of "Parallel Modeling of
+ * the Acoustic Signal Propagation in a Cased Well" (arXiv 2302.13907), with
+ * zero initial data (Eq. 2), a liquid modelled by a vanishing shear modulus
+ * (Sec. 2), medium parameters attached to the cell centre of a staggered
+ * grid (Sec. 3), a PML at the outer radius and at both z ends (Sec. 1,
+ * Sec. 6), a volumetric point source with a Ricker pulse delayed by 2/f0
+ * (Sec. 2) -- on one GPU, with hand-written sm_103a CUDA kernels.
+ *
+ * Conventions shared by every call:
+ *  - Cell (i, j, k): r = (i + 1/2) dr, theta = j * 2 pi / nth, depth
+ *    z = (k - pml_z) dz; i in [0, NR), j in [0, nth), k in [0, NZ) with
+ *    NR = nr + pml_r and NZ = nz + 2 pml_z.  Host arrays are [theta][r][z]
+ *    with z fastest.  SI units throughout.
+ *  - Staggering of the nine unknowns (field index in brackets):
+ *    [0] v_r (i, j, k)     [1] v_phi (i+1/2, j+1/2, k)   [2] v_z (i+1/2, j, k+1/2)
+ *    [3] s_rr, [4] s_phiphi, [5] s_zz at the cell centre (i+1/2, j, k)
+ *    [6] s_rphi (i, j+1/2, k)  [7] s_phiz (i+1/2, j+1/2, k+1/2)  [8] s_rz (i, j, k+1/2)
+ *    where an integer r index i means r = i dr.
+ *  - Return codes: 0 on success, a negative SIM_E* code otherwise; the
+ *    message of the last failure of a handle is sim_last_error(handle).
+ *    No call aborts, traps or exits the process.
+ *  - Ownership: every input is deep-copied by the create calls; the caller
+ *    keeps its host buffers.  Device memory belongs to the handle and is
+ *    released by the destroy calls.
+ *  - Asynchrony: the step/run calls enqueue work on the handle's CUDA
+ *    stream and return; errors raised on the device (non-finite field,
+ *    a bounded wait that gave up) are reported by the next sync/traces call.
+ */
+#ifndef CWELL_H
+#define CWELL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIM_OK 0
+#define SIM_EINVAL (-1)      /* invalid argument, checked on the host before any device work */
+#define SIM_ENOMEM (-2)      /* device allocation failed or opts.mem_cap exceeded */
+#define SIM_ECUDA (-3)       /* a CUDA runtime call failed */
+#define SIM_EUNSTABLE (-4)   /* non-finite value detected in the receiver traces */
+#define SIM_ETIMEOUT (-5)    /* a bounded device-side wait gave up */
+#define SIM_EUNSUPPORTED (-6) /* e.g. a solid (mu > 0) cell in ring 0 next to the axis */
+
+#define SIM_FIELD_VR 0
+#define SIM_FIELD_VPHI 1
+#define SIM_FIELD_VZ 2
+#define SIM_FIELD_SRR 3
+#define SIM_FIELD_SPHIPHI 4
+#define SIM_FIELD_SZZ 5
+#define SIM_FIELD_SRPHI 6
+#define SIM_FIELD_SPHIZ 7
+#define SIM_FIELD_SRZ 8
+
+#define SIM_STORAGE_F32 0
+#define SIM_STORAGE_BF16 1
+#define SIM_STORAGE_F16 2
+
+#define SIM_KERNEL_AUTO 0     /* fastest path for the storage type */
+#define SIM_KERNEL_SPLIT 1    /* separate velocity and stress kernels */
+#define SIM_KERNEL_FUSED 2    /* one time-skewed kernel per step */
+
+/* Grid (Sec. 3): interior cell counts, PML widths in cells, steps in metres.
+ * nth must be even and >= 4; nr >= 2; nz >= 2.  dt > 0 fixes the time step;
+ * otherwise dt = cfl * min over cells of 1 / (Vp sqrt(1/dr^2 + 1/(r dtheta)^2 + 1/dz^2)). */
+typedef struct {
+  int nr, nth, nz, pml_r, pml_z;
+  double dr, dz;
+  double cfl;
+  double dt;
+} sim_grid_t;
+
+/* Medium (Sec. 2-3): per-material density [kg/m^3], P and S speeds [m/s]
+ * (vs = 0 is a liquid, mu = 0); cell_id[nth][NR][NZ] (z fastest) indexes
+ * the material table.  Requires vp^2 >= 2 vs^2 and rho, vp > 0. */
+typedef struct {
+  int n_mat;
+  const double *rho, *vp, *vs;
+  const uint16_t *cell_id;
+} sim_medium_t;
+
+/* Point source (Sec. 2).  kind 0 = volumetric (pressure) source: the three
+ * normal stresses receive dt * amplitude * f(t_{n+1/2}) / V per step, f the
+ * Ricker pulse with dominant frequency f0 and delay 2/f0, V the cell
+ * volume; r < dr places it on the axis, shared by all ring-0 cells of the
+ * nearest depth. Other kinds return SIM_EUNSUPPORTED. */
+typedef struct {
+  int kind;
+  double r, theta, z, f0, amplitude;
+} sim_source_t;
+
+/* Receivers: quantity 0 = pressure -(s_rr + s_phiphi + s_zz)/3 at the
+ * nearest cell centre; r < dr records the mean over the ring-0 cells. */
+typedef struct {
+  int n;
+  const double *r, *theta, *z;
+  int quantity;
+} sim_receivers_t;
+
+/* Options.  Zero-initialised options are valid defaults. */
+typedef struct {
+  int storage;        /* SIM_STORAGE_*: field/coefficient storage; arithmetic is FP32 */
+  int pml_off;        /* 1: rigid walls with no PML (energy-conserving closure) */
+  int graph_chunk;    /* steps per captured CUDA graph; 0 = 64; < 0 = no graph */
+  void *cuda_stream;  /* cudaStream_t to enqueue on; NULL = a stream owned by the handle */
+  size_t mem_cap;     /* bytes of device memory the handle may take; 0 = no cap */
+  int max_steps;      /* trace capacity in steps; 0 = 65536 */
+  int kernel;         /* SIM_KERNEL_* */
+  int timing;         /* 1: bracket each kernel launch with CUDA events (no graph) */
+  int device;         /* CUDA device ordinal */
+} sim_opts_t;
+
+typedef struct sim_s sim_t;
+
+/* Build the device state: validates, computes dt, the material table, PML
+ * profiles and the wavelet on the host in FP64, allocates and uploads.
+ * *out is NULL on failure. */
+int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, const sim_source_t *source,
+               const sim_receivers_t *receivers, const sim_opts_t *opts, sim_t **out);
+
+/* Enqueue nsteps leapfrog steps (velocity to t_{n+1/2}, stress to t_{n+1},
+ * source, receivers; Eq. 1a then Eq. 1b).  nsteps >= 0. */
+int sim_step(sim_t *h, int nsteps);
+
+/* Wait for the handle's stream; reports device-side failures. */
+int sim_sync(sim_t *h);
+
+/* Copy the recorded traces to host memory out[n_rec][n_steps] (row-major,
+ * sample m = value after step m, time (m + 1) dt); cap = capacity of out in
+ * floats.  Synchronises.  *n_rec, *n_steps receive the shape. */
+int sim_traces(sim_t *h, float *out, size_t cap, int *n_rec, int *n_steps);
+
+/* Host copy of field `which` (SIM_FIELD_*) as FP32 [nth][NR][NZ]; n = capacity. */
+int sim_read_field(sim_t *h, int which, float *out, size_t n);
+
+/* Overwrite field `which` from host FP32 [nth][NR][NZ] (initial conditions). */
+int sim_write_field(sim_t *h, int which, const float *in, size_t n);
+
+/* Time step in seconds, steps done so far, device bytes held. */
+double sim_dt(const sim_t *h);
+int sim_steps_done(const sim_t *h);
+size_t sim_device_bytes(const sim_t *h);
+
+/* Kernel timings gathered with opts.timing = 1: for kernel slot q
+ * (0 = main update kernel, 1 = stress kernel of the split path, 2 = receivers),
+ * total milliseconds and launch count so far.  Synchronises. */
+int sim_kernel_time(sim_t *h, int q, double *ms, long *launches);
+
+/* Checkpoint: write / read fields, PML memory variables, step counter and
+ * traces to / from a file.  sim_load needs a handle created with the same
+ * grid, medium, source, receivers and options. */
+int sim_save(sim_t *h, const char *path);
+int sim_load(sim_t *h, const char *path);
+
+void sim_destroy(sim_t *h);
+const char *sim_last_error(const sim_t *h);
+const char *sim_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CWELL_H */

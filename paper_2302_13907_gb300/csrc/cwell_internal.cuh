@@ -1,0 +1,147 @@
+// Internal definitions shared by the cased-well CUDA kernels and host code.
+//
+// Device layout (one GPU, everything resident in HBM):
+//  * each of the nine fields is an array [nth][NR][NZp] of the storage type,
+//    z fastest, NZp = NZ rounded up to 32 so every row starts on a 128-byte
+//    boundary (float4 / 16-byte vector loads along z); the padding and the
+//    wall / axis nodes that are not unknowns (v_r and s_rphi, s_rz at r = 0;
+//    v_z, s_rz, s_phiz at the last z half-node) are held at zero;
+//  * material IDs uint16 [nth][NR][NZp]; a float4 table {rho, lambda, mu,
+//    1/mu} per ID (1/mu = +inf for a liquid, so the four-cell harmonic mean
+//    4 / sum(1/mu) is exactly zero next to a liquid);
+//  * PML memory variables only where the layers are: a radial slab
+//    [12][nth][pml_r][NZp] (six radial differences, six 1/r groups) and a z
+//    slab [6][nth][NR][2 pml_z], FP32.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cwell {
+
+enum { F_VR = 0, F_VP, F_VZ, F_SRR, F_SPP, F_SZZ, F_SRP, F_SPZ, F_SRZ, NF };
+// radial-slab memory variables: radial differences (_R) and 1/r groups (_Q)
+enum { R_VR = 0, R_VP, R_VZ, R_ERR, R_GRP, R_GRZ, Q_VR, Q_VP, Q_VZ, Q_EPP, Q_GRP, Q_GPZ, NPR };
+// z-slab memory variables
+enum { Z_VR = 0, Z_VP, Z_VZ, Z_EZZ, Z_GRZ, Z_GPZ, NPZ };
+
+struct KParams {
+  int nth, NR, NZ, NZp, nr, pml_r, pml_z;
+  long long plane;  // NR * NZp
+  float dtv;        // dt * (velocity scale / stress scale)
+  float dts;        // dt * (stress scale / velocity scale)
+  float inv_dr, inv_dz, inv_dth;
+  const float *inv_ri;  // [NR] 1 / (i dr), 0 at i = 0
+  const float *inv_rh;  // [NR] 1 / ((i + 1/2) dr)
+  const float4 *ab_r;   // [NR] {a, b} at the integer node, {a, b} at the half node: radial difference
+  const float4 *ab_q;   // [NR] the same for the 1/r group (integrated profile)
+  const float4 *ab_z;   // [NZ] {a, b} at the cell centre, {a, b} at the half node
+  const float4 *mat;    // [n_mat] {rho, lambda, mu, 1/mu}
+  const uint16_t *id;   // [nth][NR][NZp]
+  void *f[NF];          // field storage (type set by the kernel template)
+  float *psr[NPR];      // [nth][pml_r][NZp]
+  float *psz[NPZ];      // [nth][NR][2 pml_z]
+  const float *wav;     // [n_wav] stress increment of the source at step n (scaled)
+  int n_wav;
+  int src_i, src_j, src_k;  // src_j < 0: all ring-0 cells
+  int *step;                // device step counter
+};
+
+struct RParams {
+  int nth, NR, NZp, n_rec, cap;
+  long long plane;
+  const void *srr, *spp, *szz;
+  const int *rec;        // [n_rec][3] i, j (-1: ring mean), k
+  float scale;           // -1 / (3 * stress scale)
+  float *traces;         // [n_rec][cap]
+  int *step;
+  int *status;           // bit 0: non-finite sample
+};
+
+// ---------------------------------------------------------------- storage
+template <typename T>
+struct St;
+
+template <>
+struct St<float> {
+  static __device__ __forceinline__ float4 ld4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+  static __device__ __forceinline__ float ld1(const float *p) { return __ldg(p); }
+  static __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+};
+
+template <>
+struct St<__nv_bfloat16> {
+  static __device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p) {
+    uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+    float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.x));
+    float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  static __device__ __forceinline__ float ld1(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+  static __device__ __forceinline__ void st4(__nv_bfloat16 *p, float4 v) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned *>(&a);
+    u.y = *reinterpret_cast<unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+  }
+};
+
+template <>
+struct St<__half> {
+  static __device__ __forceinline__ float4 ld4(const __half *p) {
+    uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+    float2 a = __half22float2(*reinterpret_cast<__half2 *>(&u.x));
+    float2 b = __half22float2(*reinterpret_cast<__half2 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  static __device__ __forceinline__ float ld1(const __half *p) { return __half2float(__ldg(p)); }
+  static __device__ __forceinline__ void st4(__half *p, float4 v) {
+    __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned *>(&a);
+    u.y = *reinterpret_cast<unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ float st_to_float(T x);
+template <>
+__device__ __forceinline__ float st_to_float<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float st_to_float<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <>
+__device__ __forceinline__ float st_to_float<__half>(__half x) { return __half2float(x); }
+
+__device__ __forceinline__ void f4_to(float (&a)[4], float4 v) {
+  a[0] = v.x;
+  a[1] = v.y;
+  a[2] = v.z;
+  a[3] = v.w;
+}
+
+__device__ __forceinline__ void ld_ids(const uint16_t *p, int (&o)[4]) {
+  uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+  o[0] = u.x & 0xffff;
+  o[1] = u.x >> 16;
+  o[2] = u.y & 0xffff;
+  o[3] = u.y >> 16;
+}
+
+// convolutional memory variable: psi <- b psi + a D, returns D + psi
+__device__ __forceinline__ float stretch(float *psi, float a, float b, float D) {
+  float p = b * (*psi) + a * D;
+  *psi = p;
+  return D + p;
+}
+
+}  // namespace cwell
+
+// launchers implemented in the .cu files (host side)
+namespace cwell {
+cudaError_t launch_split(int storage, const KParams &p, cudaStream_t s, cudaEvent_t *ev);
+cudaError_t launch_receivers(int storage, const RParams &p, cudaStream_t s);
+}  // namespace cwell

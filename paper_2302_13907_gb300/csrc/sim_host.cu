@@ -1,0 +1,641 @@
+// Host side of the C-ABI: validation, FP64 set-up (time step, material
+// table, PML profiles, source wavelet, receiver nodes), device allocation,
+// CUDA-graph stepping, traces, checkpoints.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/cwell.h"
+#include "cwell_internal.cuh"
+
+using namespace cwell;
+
+struct sim_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  sim_grid_t grid{};
+  int NR = 0, NZ = 0, NZp = 0;
+  double dt = 0, vscale = 1, sscale = 1;
+  int storage = 0, kernel = SIM_KERNEL_SPLIT, graph_chunk = 64, timing = 0;
+  int n_mat = 0, n_rec = 0, cap = 0;
+  size_t elem = 4;
+  void *f[NF] = {};
+  float *psr[NPR] = {};
+  float *psz[NPZ] = {};
+  uint16_t *id = nullptr;
+  float4 *mat = nullptr, *ab_r = nullptr, *ab_q = nullptr, *ab_z = nullptr;
+  float *inv_ri = nullptr, *inv_rh = nullptr, *wav = nullptr, *traces = nullptr;
+  int *rec = nullptr, *step = nullptr, *status = nullptr;
+  int n_wav = 0;
+  KParams kp{};
+  RParams rp{};
+  int steps_done = 0;
+  size_t bytes = 0, mem_cap = 0, psr_elems = 0, psz_elems = 0;
+  std::vector<void *> allocs;
+  cudaGraphExec_t gexec = nullptr;
+  int gsteps = 0;
+  cudaEvent_t ev[4] = {};
+  double kms[3] = {0, 0, 0};
+  long kcount[3] = {0, 0, 0};
+  std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+static int fail(sim_t *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+static int cuda_fail(sim_t *h, cudaError_t e, const char *what) {
+  return fail(h, SIM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                  \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+static int dev_alloc(sim_t *h, void **p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (h->mem_cap && h->bytes + bytes > h->mem_cap)
+    return fail(h, SIM_ENOMEM, "device memory cap exceeded (" + std::to_string(h->bytes + bytes) + " > " +
+                                   std::to_string(h->mem_cap) + " bytes)");
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, SIM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  h->allocs.push_back(*p);
+  h->bytes += bytes;
+  e = cudaMemsetAsync(*p, 0, bytes, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+  return SIM_OK;
+}
+
+// Ricker pulse, dominant frequency f0, delay 2/f0 (Sec. 2 of the paper)
+static double ricker(double t, double f0) {
+  double a = M_PI * f0 * (t - 2.0 / f0);
+  a = a * a;
+  return (1.0 - 2.0 * a) * exp(-a);
+}
+
+static void cpml(double d, double al, double dt, float *a, float *b) {
+  if (!(d > 0.0)) {
+    *a = 0.f;
+    *b = 1.f;
+    return;
+  }
+  double bb = exp(-(d + al) * dt);
+  *b = (float)bb;
+  *a = (float)(d * (bb - 1.0) / (d + al));
+}
+
+static int validate(const sim_grid_t *g, const sim_medium_t *m, const sim_source_t *s, const sim_receivers_t *r,
+                    const sim_opts_t *o) {
+  if (!g || !m || !s || !r || !o) return fail(nullptr, SIM_EINVAL, "null argument");
+  if (g->nr < 2 || g->nth < 4 || (g->nth & 1) || g->nz < 2 || g->pml_r < 0 || g->pml_z < 0)
+    return fail(nullptr, SIM_EINVAL, "grid: need nr >= 2, nth >= 4 and even, nz >= 2, pml >= 0");
+  if (!(g->dr > 0) || !(g->dz > 0) || !isfinite(g->dr) || !isfinite(g->dz))
+    return fail(nullptr, SIM_EINVAL, "grid: dr, dz must be positive and finite");
+  if (!(g->dt > 0) && !(g->cfl > 0)) return fail(nullptr, SIM_EINVAL, "grid: need dt > 0 or cfl > 0");
+  long long cells = (long long)g->nth * (g->nr + g->pml_r) * (g->nz + 2 * g->pml_z);
+  if (cells > (1LL << 40)) return fail(nullptr, SIM_EINVAL, "grid too large");
+  if (m->n_mat < 1 || m->n_mat > 65536 || !m->rho || !m->vp || !m->vs || !m->cell_id)
+    return fail(nullptr, SIM_EINVAL, "medium: need 1 <= n_mat <= 65536 and non-null arrays");
+  for (int q = 0; q < m->n_mat; q++)
+    if (!(m->rho[q] > 0) || !(m->vp[q] > 0) || !(m->vs[q] >= 0) || m->vp[q] * m->vp[q] < 2.0 * m->vs[q] * m->vs[q] ||
+        !isfinite(m->rho[q]) || !isfinite(m->vp[q]))
+      return fail(nullptr, SIM_EINVAL, "medium: material " + std::to_string(q) + " needs rho, vp > 0, vs >= 0, vp^2 >= 2 vs^2");
+  if (s->kind != 0) return fail(nullptr, SIM_EUNSUPPORTED, "source: only kind 0 (volumetric) is implemented");
+  if (!(s->f0 > 0) || !isfinite(s->amplitude)) return fail(nullptr, SIM_EINVAL, "source: need f0 > 0, finite amplitude");
+  if (!(s->r >= 0) || s->r >= g->nr * g->dr) return fail(nullptr, SIM_EINVAL, "source: r outside the interior");
+  long ks = lround(s->z / g->dz);
+  if (!isfinite(s->z) || ks < 0 || ks >= g->nz) return fail(nullptr, SIM_EINVAL, "source: z outside the interior");
+  if (r->n < 0 || (r->n > 0 && (!r->r || !r->theta || !r->z)) || r->quantity != 0)
+    return fail(nullptr, SIM_EINVAL, "receivers: bad count, arrays or quantity");
+  for (int q = 0; q < r->n; q++) {
+    long kr = lround(r->z[q] / g->dz);
+    if (!isfinite(r->z[q]) || kr < 0 || kr >= g->nz || !(r->r[q] >= 0) || r->r[q] >= g->nr * g->dr)
+      return fail(nullptr, SIM_EINVAL, "receiver " + std::to_string(q) + " outside the interior");
+  }
+  if (o->storage < 0 || o->storage > 2) return fail(nullptr, SIM_EINVAL, "opts: storage must be 0, 1 or 2");
+  if (o->kernel < 0 || o->kernel > 2) return fail(nullptr, SIM_EINVAL, "opts: kernel must be 0, 1 or 2");
+  if (o->max_steps < 0) return fail(nullptr, SIM_EINVAL, "opts: max_steps < 0");
+  return SIM_OK;
+}
+
+static void release(sim_t *h) {
+  if (!h) return;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (auto &e : h->ev)
+    if (e) cudaEventDestroy(e);
+  for (void *p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, const sim_source_t *source,
+                          const sim_receivers_t *receivers, const sim_opts_t *opts, sim_t **out) {
+  if (!out) return fail(nullptr, SIM_EINVAL, "out is null");
+  *out = nullptr;
+  int rc = validate(grid, medium, source, receivers, opts);
+  if (rc) return rc;
+  const sim_grid_t &g = *grid;
+  const int NR = g.nr + g.pml_r, NZ = g.nz + 2 * g.pml_z, nth = g.nth;
+  const int NZp = (NZ + 31) / 32 * 32;
+  const size_t ncell = (size_t)nth * NR * NZ;
+  const uint16_t *cid = medium->cell_id;
+  // material IDs in range; ring 0 (the axis cells) must be a liquid
+  for (size_t c = 0; c < ncell; c++)
+    if (cid[c] >= medium->n_mat) return fail(nullptr, SIM_EINVAL, "medium: cell_id out of range at " + std::to_string(c));
+  for (int j = 0; j < nth; j++)
+    for (int k = 0; k < NZ; k++)
+      if (medium->vs[cid[((size_t)j * NR) * NZ + k]] != 0.0)
+        return fail(nullptr, SIM_EUNSUPPORTED, "medium: ring 0 (next to the axis) must be a liquid");
+
+  sim_t *h = new sim_t();
+  h->grid = g;
+  h->NR = NR;
+  h->NZ = NZ;
+  h->NZp = NZp;
+  h->storage = opts->storage;
+  h->elem = opts->storage == 0 ? 4 : 2;
+  h->kernel = SIM_KERNEL_SPLIT;
+  h->graph_chunk = opts->graph_chunk == 0 ? 64 : opts->graph_chunk;
+  h->timing = opts->timing;
+  h->mem_cap = opts->mem_cap;
+  h->n_mat = medium->n_mat;
+  h->n_rec = receivers->n;
+  h->cap = opts->max_steps ? opts->max_steps : 65536;
+  h->device = opts->device;
+  auto bail = [&](int code) {
+    if (code != SIM_OK) {
+      g_create_err = h->err;
+      release(h);
+      delete h;
+    }
+    return code;
+  };
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaSetDevice"));
+  if (opts->cuda_stream) {
+    h->stream = (cudaStream_t)opts->cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaStreamCreate"));
+    h->own_stream = true;
+  }
+
+  // --- time step: dt = cfl * min over cells 1 / (Vp sqrt(1/dr^2 + 1/(r dth)^2 + 1/dz^2))
+  const double dth = 2.0 * M_PI / nth;
+  if (g.dt > 0) {
+    h->dt = g.dt;
+  } else {
+    double best = INFINITY;
+    for (int i = 0; i < NR; i++) {
+      double cmax = 0.0;
+      for (int j = 0; j < nth; j++) {
+        const uint16_t *row = cid + ((size_t)j * NR + i) * NZ;
+        for (int k = 0; k < NZ; k++) cmax = std::max(cmax, medium->vp[row[k]]);
+      }
+      const double rc = (i + 0.5) * g.dr;
+      const double s = sqrt(1.0 / (g.dr * g.dr) + 1.0 / ((rc * dth) * (rc * dth)) + 1.0 / (g.dz * g.dz));
+      best = std::min(best, 1.0 / (cmax * s));
+    }
+    h->dt = g.cfl * best;
+  }
+  const double dt = h->dt;
+
+  // --- storage scales (FP16 needs the velocities lifted by an impedance)
+  long ks = lround(source->z / g.dz) + g.pml_z;
+  int is = source->r < g.dr ? 0 : (int)floor(source->r / g.dr);
+  int js = source->r < g.dr ? -1 : (int)(((lround(source->theta / dth) % nth) + nth) % nth);
+  if (h->storage == 2) {
+    int m0 = cid[((size_t)(js < 0 ? 0 : js) * NR + is) * NZ + ks];
+    h->sscale = source->amplitude != 0 ? 1.0 / fabs(source->amplitude) : 1.0;
+    h->vscale = h->sscale * medium->rho[m0] * medium->vp[m0];
+  }
+
+  // --- material table {rho, lambda, mu, 1/mu}; Lame from the cell-centre values
+  std::vector<float4> mat(h->n_mat);
+  double vpmax = 0;
+  for (int q = 0; q < h->n_mat; q++) {
+    double rho = medium->rho[q], mu = rho * medium->vs[q] * medium->vs[q];
+    double lam = rho * medium->vp[q] * medium->vp[q] - 2.0 * mu;
+    mat[q] = make_float4((float)rho, (float)lam, (float)mu, mu > 0 ? (float)(1.0 / mu) : INFINITY);
+    vpmax = std::max(vpmax, medium->vp[q]);
+  }
+  // --- radius tables
+  std::vector<float> inv_ri(NR), inv_rh(NR);
+  for (int i = 0; i < NR; i++) {
+    inv_ri[i] = i > 0 ? (float)(1.0 / (i * g.dr)) : 0.f;
+    inv_rh[i] = (float)(1.0 / ((i + 0.5) * g.dr));
+  }
+  // --- PML: d(x) = d0 (x/L)^2, alpha = pi f0, dbar = (1/r) int d for the 1/r group
+  const bool pml = !opts->pml_off;
+  const double al = M_PI * source->f0;
+  const double Lr = g.pml_r * g.dr, Lz = g.pml_z * g.dz;
+  const double d0r = Lr > 0 ? -3.0 * vpmax * log(1e-3) / (2.0 * Lr) : 0.0;
+  const double d0z = Lz > 0 ? -3.0 * vpmax * log(1e-3) / (2.0 * Lz) : 0.0;
+  auto prof = [](double x, double L, double d0) { return (x > 0 && L > 0) ? d0 * (x / L) * (x / L) : 0.0; };
+  auto profbar = [](double x, double r, double L, double d0) {
+    return (x > 0 && L > 0 && r > 0) ? d0 * x * x * x / (3.0 * L * L) / r : 0.0;
+  };
+  std::vector<float4> ab_r(NR), ab_q(NR), ab_z(NZ);
+  for (int i = 0; i < NR; i++) {
+    double xi = pml ? (i - g.nr) * g.dr : 0.0, xh = pml ? (i + 0.5 - g.nr) * g.dr : 0.0;
+    cpml(prof(xi, Lr, d0r), al, dt, &ab_r[i].x, &ab_r[i].y);
+    cpml(prof(xh, Lr, d0r), al, dt, &ab_r[i].z, &ab_r[i].w);
+    cpml(profbar(xi, i * g.dr, Lr, d0r), al, dt, &ab_q[i].x, &ab_q[i].y);
+    cpml(profbar(xh, (i + 0.5) * g.dr, Lr, d0r), al, dt, &ab_q[i].z, &ab_q[i].w);
+  }
+  for (int k = 0; k < NZ; k++) {
+    double xi = std::max((g.pml_z - 0.5 - k) * g.dz, (k - (g.pml_z + g.nz - 0.5)) * g.dz);
+    double xh = std::max((g.pml_z - 1.0 - k) * g.dz, (k + 1.0 - g.pml_z - g.nz) * g.dz);
+    if (!pml) xi = xh = 0.0;
+    cpml(prof(xi, Lz, d0z), al, dt, &ab_z[k].x, &ab_z[k].y);
+    cpml(prof(xh, Lz, d0z), al, dt, &ab_z[k].z, &ab_z[k].w);
+  }
+  // --- source wavelet: per-step increment dt * A * f(t_{n+1/2}) / V of the normal stresses
+  const double vol = js < 0 ? M_PI * g.dr * g.dr * g.dz : (is + 0.5) * g.dr * g.dr * dth * g.dz;
+  int n_pulse = (int)std::min<double>(ceil(8.0 / (source->f0 * dt)) + 1.0, 1e8);
+  h->n_wav = std::max(1, std::min(n_pulse, std::max(h->cap, 1)));
+  if (n_pulse > h->n_wav) h->n_wav = n_pulse;  // the pulse always fits
+  std::vector<float> wav(h->n_wav);
+  for (int n = 0; n < h->n_wav; n++)
+    wav[n] = (float)(dt * source->amplitude * ricker((n + 0.5) * dt, source->f0) / vol * h->sscale);
+  // --- receivers
+  std::vector<int> rec(3 * std::max(1, h->n_rec));
+  for (int q = 0; q < h->n_rec; q++) {
+    bool axis = receivers->r[q] < g.dr;
+    rec[3 * q] = axis ? 0 : (int)floor(receivers->r[q] / g.dr);
+    rec[3 * q + 1] = axis ? -1 : (int)(((lround(receivers->theta[q] / dth) % nth) + nth) % nth);
+    rec[3 * q + 2] = (int)(lround(receivers->z[q] / g.dz) + g.pml_z);
+  }
+
+  // --- device memory
+  const size_t fbytes = (size_t)nth * NR * NZp * h->elem;
+  for (int q = 0; q < NF; q++)
+    if ((rc = dev_alloc(h, &h->f[q], fbytes))) return bail(rc);
+  h->psr_elems = (size_t)nth * g.pml_r * NZp;
+  h->psz_elems = (size_t)nth * NR * 2 * g.pml_z;
+  if (pml) {
+    for (int q = 0; q < NPR; q++)
+      if ((rc = dev_alloc(h, (void **)&h->psr[q], h->psr_elems * 4))) return bail(rc);
+    for (int q = 0; q < NPZ; q++)
+      if ((rc = dev_alloc(h, (void **)&h->psz[q], h->psz_elems * 4))) return bail(rc);
+  }
+  if ((rc = dev_alloc(h, (void **)&h->id, (size_t)nth * NR * NZp * 2))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->mat, mat.size() * sizeof(float4)))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->ab_r, NR * sizeof(float4)))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->ab_q, NR * sizeof(float4)))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->ab_z, NZ * sizeof(float4)))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->inv_ri, NR * 4))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->inv_rh, NR * 4))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->wav, wav.size() * 4))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->rec, rec.size() * 4))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->traces, (size_t)std::max(1, h->n_rec) * h->cap * 4))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->step, 16))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->status, 16))) return bail(rc);
+
+  cudaStream_t st = h->stream;
+#define UP(dst, src, n) \
+  if ((e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st)) != cudaSuccess) return bail(cuda_fail(h, e, "upload"))
+  e = cudaMemcpy2DAsync(h->id, NZp * 2, cid, NZ * 2, NZ * 2, (size_t)nth * NR, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return bail(cuda_fail(h, e, "upload cell_id"));
+  UP(h->mat, mat.data(), mat.size() * sizeof(float4));
+  UP(h->ab_r, ab_r.data(), NR * sizeof(float4));
+  UP(h->ab_q, ab_q.data(), NR * sizeof(float4));
+  UP(h->ab_z, ab_z.data(), NZ * sizeof(float4));
+  UP(h->inv_ri, inv_ri.data(), NR * 4);
+  UP(h->inv_rh, inv_rh.data(), NR * 4);
+  UP(h->wav, wav.data(), wav.size() * 4);
+  UP(h->rec, rec.data(), rec.size() * 4);
+#undef UP
+  // pageable host sources: make the upload complete before the host vectors go away
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaStreamSynchronize"));
+
+  KParams &p = h->kp;
+  p.nth = nth;
+  p.NR = NR;
+  p.NZ = NZ;
+  p.NZp = NZp;
+  p.nr = g.nr;
+  p.pml_r = pml ? g.pml_r : 0;
+  p.pml_z = pml ? g.pml_z : 0;
+  if (!pml) p.nr = NR;  // no radial layer at all
+  p.plane = (long long)NR * NZp;
+  p.dtv = (float)(dt * h->vscale / h->sscale);
+  p.dts = (float)(dt * h->sscale / h->vscale);
+  p.inv_dr = (float)(1.0 / g.dr);
+  p.inv_dz = (float)(1.0 / g.dz);
+  p.inv_dth = (float)(1.0 / dth);
+  p.inv_ri = h->inv_ri;
+  p.inv_rh = h->inv_rh;
+  p.ab_r = h->ab_r;
+  p.ab_q = h->ab_q;
+  p.ab_z = h->ab_z;
+  p.mat = h->mat;
+  p.id = h->id;
+  for (int q = 0; q < NF; q++) p.f[q] = h->f[q];
+  for (int q = 0; q < NPR; q++) p.psr[q] = h->psr[q];
+  for (int q = 0; q < NPZ; q++) p.psz[q] = h->psz[q];
+  p.wav = h->wav;
+  p.n_wav = h->n_wav;
+  p.src_i = is;
+  p.src_j = js;
+  p.src_k = (int)ks;
+  p.step = h->step;
+  RParams &r = h->rp;
+  r.nth = nth;
+  r.NR = NR;
+  r.NZp = NZp;
+  r.n_rec = h->n_rec;
+  r.cap = h->cap;
+  r.plane = p.plane;
+  r.srr = h->f[F_SRR];
+  r.spp = h->f[F_SPP];
+  r.szz = h->f[F_SZZ];
+  r.rec = h->rec;
+  r.scale = (float)(-1.0 / (3.0 * h->sscale));
+  r.traces = h->traces;
+  r.step = h->step;
+  r.status = h->status;
+  if (h->timing)
+    for (auto &ev : h->ev)
+      if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(cuda_fail(h, e, "cudaEventCreate"));
+  *out = h;
+  return SIM_OK;
+}
+
+static cudaError_t enqueue_step(sim_t *h, bool timed) {
+  cudaError_t e = launch_split(h->storage, h->kp, h->stream, timed ? h->ev : nullptr);
+  if (e != cudaSuccess) return e;
+  e = launch_receivers(h->storage, h->rp, h->stream);
+  if (e != cudaSuccess) return e;
+  if (timed) {
+    cudaEventRecord(h->ev[3], h->stream);
+    e = cudaEventSynchronize(h->ev[3]);
+    if (e != cudaSuccess) return e;
+    float a = 0, b = 0, c = 0;
+    cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+    cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
+    cudaEventElapsedTime(&c, h->ev[2], h->ev[3]);
+    h->kms[0] += a;
+    h->kms[1] += b;
+    h->kms[2] += c;
+    h->kcount[0]++;
+    h->kcount[1]++;
+    h->kcount[2]++;
+  }
+  return cudaSuccess;
+}
+
+extern "C" int sim_step(sim_t *h, int nsteps) {
+  if (!h) return SIM_EINVAL;
+  if (nsteps < 0) return fail(h, SIM_EINVAL, "nsteps < 0");
+  CK(h, cudaSetDevice(h->device));
+  int left = nsteps;
+  if (!h->timing && h->graph_chunk > 0 && left >= h->graph_chunk) {
+    if (!h->gexec) {
+      cudaGraph_t graph;
+      CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      for (int q = 0; q < h->graph_chunk && e == cudaSuccess; q++) e = enqueue_step(h, false);
+      cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+      if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch during capture");
+      if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&h->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+      h->gsteps = h->graph_chunk;
+    }
+    while (left >= h->gsteps) {
+      CK(h, cudaGraphLaunch(h->gexec, h->stream));
+      left -= h->gsteps;
+      h->steps_done += h->gsteps;
+    }
+  }
+  for (; left > 0; left--) {
+    cudaError_t e = enqueue_step(h, h->timing != 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+    h->steps_done++;
+  }
+  return SIM_OK;
+}
+
+extern "C" int sim_sync(sim_t *h) {
+  if (!h) return SIM_EINVAL;
+  CK(h, cudaSetDevice(h->device));
+  CK(h, cudaStreamSynchronize(h->stream));
+  int st = 0;
+  CK(h, cudaMemcpy(&st, h->status, 4, cudaMemcpyDeviceToHost));
+  if (st & 1) return fail(h, SIM_EUNSTABLE, "non-finite value in the receiver traces");
+  if (st & 2) return fail(h, SIM_ETIMEOUT, "a bounded device wait gave up");
+  return SIM_OK;
+}
+
+extern "C" int sim_traces(sim_t *h, float *out, size_t cap, int *n_rec, int *n_steps) {
+  if (!h) return SIM_EINVAL;
+  int rc = sim_sync(h);
+  if (rc && rc != SIM_EUNSTABLE) return rc;
+  int ns = std::min(h->steps_done, h->cap);
+  if (n_rec) *n_rec = h->n_rec;
+  if (n_steps) *n_steps = ns;
+  if (!out) return rc;
+  if (cap < (size_t)h->n_rec * ns) return fail(h, SIM_EINVAL, "output buffer too small");
+  if (h->n_rec > 0 && ns > 0)
+    CK(h, cudaMemcpy2D(out, (size_t)ns * 4, h->traces, (size_t)h->cap * 4, (size_t)ns * 4, h->n_rec,
+                       cudaMemcpyDeviceToHost));
+  return rc;
+}
+
+template <typename T>
+__global__ void to_f32(const T *in, float *out, long long n, float scale) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q < n) out[q] = st_to_float<T>(in[q]) * scale;
+}
+template <typename T>
+__global__ void from_f32(const float *in, T *out, long long n, float scale);
+template <>
+__global__ void from_f32<float>(const float *in, float *out, long long n, float scale) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q < n) out[q] = in[q] * scale;
+}
+template <>
+__global__ void from_f32<__nv_bfloat16>(const float *in, __nv_bfloat16 *out, long long n, float scale) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q < n) out[q] = __float2bfloat16_rn(in[q] * scale);
+}
+template <>
+__global__ void from_f32<__half>(const float *in, __half *out, long long n, float scale) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q < n) out[q] = __float2half_rn(in[q] * scale);
+}
+
+static double field_scale(const sim_t *h, int which) { return which <= F_VZ ? h->vscale : h->sscale; }
+
+extern "C" int sim_read_field(sim_t *h, int which, float *out, size_t n) {
+  if (!h) return SIM_EINVAL;
+  if (which < 0 || which >= NF || !out) return fail(h, SIM_EINVAL, "bad field index or buffer");
+  const size_t rows = (size_t)h->grid.nth * h->NR, need = rows * h->NZ;
+  if (n < need) return fail(h, SIM_EINVAL, "output buffer too small");
+  CK(h, cudaSetDevice(h->device));
+  CK(h, cudaStreamSynchronize(h->stream));
+  const long long tot = (long long)rows * h->NZp;
+  float *tmp = nullptr;
+  CK(h, cudaMalloc(&tmp, tot * 4));
+  const float sc = (float)(1.0 / field_scale(h, which));
+  int blocks = (int)((tot + 255) / 256);
+  switch (h->storage) {
+    case 0: to_f32<float><<<blocks, 256, 0, h->stream>>>((const float *)h->f[which], tmp, tot, sc); break;
+    case 1: to_f32<__nv_bfloat16><<<blocks, 256, 0, h->stream>>>((const __nv_bfloat16 *)h->f[which], tmp, tot, sc); break;
+    default: to_f32<__half><<<blocks, 256, 0, h->stream>>>((const __half *)h->f[which], tmp, tot, sc); break;
+  }
+  cudaError_t e = cudaMemcpy2DAsync(out, h->NZ * 4, tmp, h->NZp * 4, h->NZ * 4, rows, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "read field");
+  return SIM_OK;
+}
+
+extern "C" int sim_write_field(sim_t *h, int which, const float *in, size_t n) {
+  if (!h) return SIM_EINVAL;
+  if (which < 0 || which >= NF || !in) return fail(h, SIM_EINVAL, "bad field index or buffer");
+  const size_t rows = (size_t)h->grid.nth * h->NR, need = rows * h->NZ;
+  if (n < need) return fail(h, SIM_EINVAL, "input buffer too small");
+  CK(h, cudaSetDevice(h->device));
+  const long long tot = (long long)rows * h->NZp;
+  float *tmp = nullptr;
+  CK(h, cudaMalloc(&tmp, tot * 4));
+  cudaError_t e = cudaMemsetAsync(tmp, 0, tot * 4, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(tmp, h->NZp * 4, in, h->NZ * 4, h->NZ * 4, rows, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) {
+    const float sc = (float)field_scale(h, which);
+    int blocks = (int)((tot + 255) / 256);
+    switch (h->storage) {
+      case 0: from_f32<float><<<blocks, 256, 0, h->stream>>>(tmp, (float *)h->f[which], tot, sc); break;
+      case 1: from_f32<__nv_bfloat16><<<blocks, 256, 0, h->stream>>>(tmp, (__nv_bfloat16 *)h->f[which], tot, sc); break;
+      default: from_f32<__half><<<blocks, 256, 0, h->stream>>>(tmp, (__half *)h->f[which], tot, sc); break;
+    }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "write field");
+  return SIM_OK;
+}
+
+extern "C" double sim_dt(const sim_t *h) { return h ? h->dt : 0.0; }
+extern "C" int sim_steps_done(const sim_t *h) { return h ? h->steps_done : -1; }
+extern "C" size_t sim_device_bytes(const sim_t *h) { return h ? h->bytes : 0; }
+
+extern "C" int sim_kernel_time(sim_t *h, int q, double *ms, long *launches) {
+  if (!h) return SIM_EINVAL;
+  if (q < 0 || q > 2) return fail(h, SIM_EINVAL, "kernel slot out of range");
+  if (!h->timing) return fail(h, SIM_EINVAL, "handle was created without opts.timing");
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (ms) *ms = h->kms[q];
+  if (launches) *launches = h->kcount[q];
+  return SIM_OK;
+}
+
+// checkpoint file: magic, sizes, step counter, raw device arrays in order
+static const char kMagic[8] = {'C', 'W', 'E', 'L', 'L', 'C', 'K', '1'};
+
+extern "C" int sim_save(sim_t *h, const char *path) {
+  if (!h) return SIM_EINVAL;
+  if (!path) return fail(h, SIM_EINVAL, "null path");
+  CK(h, cudaSetDevice(h->device));
+  CK(h, cudaStreamSynchronize(h->stream));
+  FILE *fp = fopen(path, "wb");
+  if (!fp) return fail(h, SIM_EINVAL, std::string("cannot open ") + path);
+  long long hdr[8] = {h->grid.nth, h->NR, h->NZp, (long long)h->elem, (long long)h->psr_elems,
+                      (long long)h->psz_elems, h->steps_done, (long long)h->n_rec * h->cap};
+  bool ok = fwrite(kMagic, 1, 8, fp) == 8 && fwrite(hdr, sizeof(hdr), 1, fp) == 1;
+  std::vector<char> buf;
+  auto dump = [&](const void *dptr, size_t bytes) {
+    if (!ok || !dptr) return;
+    buf.resize(bytes);
+    ok = cudaMemcpy(buf.data(), dptr, bytes, cudaMemcpyDeviceToHost) == cudaSuccess &&
+         fwrite(buf.data(), 1, bytes, fp) == bytes;
+  };
+  const size_t fbytes = (size_t)h->grid.nth * h->NR * h->NZp * h->elem;
+  for (int q = 0; q < NF; q++) dump(h->f[q], fbytes);
+  for (int q = 0; q < NPR; q++) dump(h->psr[q], h->psr_elems * 4);
+  for (int q = 0; q < NPZ; q++) dump(h->psz[q], h->psz_elems * 4);
+  dump(h->traces, (size_t)h->n_rec * h->cap * 4);
+  dump(h->step, 4);
+  if (fclose(fp) != 0) ok = false;
+  return ok ? SIM_OK : fail(h, SIM_EINVAL, "checkpoint write failed");
+}
+
+extern "C" int sim_load(sim_t *h, const char *path) {
+  if (!h) return SIM_EINVAL;
+  if (!path) return fail(h, SIM_EINVAL, "null path");
+  CK(h, cudaSetDevice(h->device));
+  CK(h, cudaStreamSynchronize(h->stream));
+  FILE *fp = fopen(path, "rb");
+  if (!fp) return fail(h, SIM_EINVAL, std::string("cannot open ") + path);
+  char mg[8];
+  long long hdr[8];
+  bool ok = fread(mg, 1, 8, fp) == 8 && memcmp(mg, kMagic, 8) == 0 && fread(hdr, sizeof(hdr), 1, fp) == 1;
+  ok = ok && hdr[0] == h->grid.nth && hdr[1] == h->NR && hdr[2] == h->NZp && hdr[3] == (long long)h->elem &&
+       hdr[4] == (long long)h->psr_elems && hdr[5] == (long long)h->psz_elems &&
+       hdr[7] == (long long)h->n_rec * h->cap;
+  if (!ok) {
+    fclose(fp);
+    return fail(h, SIM_EINVAL, "checkpoint does not match this handle");
+  }
+  std::vector<char> buf;
+  auto load = [&](void *dptr, size_t bytes) {
+    if (!ok || !dptr) return;
+    buf.resize(bytes);
+    ok = fread(buf.data(), 1, bytes, fp) == bytes &&
+         cudaMemcpy(dptr, buf.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  const size_t fbytes = (size_t)h->grid.nth * h->NR * h->NZp * h->elem;
+  for (int q = 0; q < NF; q++) load(h->f[q], fbytes);
+  for (int q = 0; q < NPR; q++) load(h->psr[q], h->psr_elems * 4);
+  for (int q = 0; q < NPZ; q++) load(h->psz[q], h->psz_elems * 4);
+  load(h->traces, (size_t)h->n_rec * h->cap * 4);
+  load(h->step, 4);
+  fclose(fp);
+  if (!ok) return fail(h, SIM_EINVAL, "checkpoint read failed");
+  h->steps_done = (int)hdr[6];
+  return SIM_OK;
+}
+
+extern "C" void sim_destroy(sim_t *h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  release(h);
+  delete h;
+}
+
+extern "C" const char *sim_last_error(const sim_t *h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+extern "C" const char *sim_error_string(int code) {
+  switch (code) {
+    case SIM_OK: return "ok";
+    case SIM_EINVAL: return "invalid argument";
+    case SIM_ENOMEM: return "out of device memory";
+    case SIM_ECUDA: return "CUDA error";
+    case SIM_EUNSTABLE: return "unstable (non-finite field)";
+    case SIM_ETIMEOUT: return "device wait timed out";
+    case SIM_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown error";
+}
