@@ -187,6 +187,7 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nz", type=int, default=8192, help="interior z cells (8192 = the 20 m well; smaller for profiling)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
@@ -208,7 +209,7 @@ def main():
     from paper_2302_13907_gb300 import workloads as W
     from paper_2302_13907_gb300.binding import Simulation
 
-    sc = W.config2()
+    sc = W.config2(nz=args.nz)
     g = sc.grid
     cells = g.nth * g.NR * g.NZ
     K, Wm, T = args.steps, args.warmup, args.chunk

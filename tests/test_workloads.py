@@ -116,3 +116,19 @@ def test_case_draw_ranges():
         assert 0 <= p["ramp"] <= 0.5 and 0 <= p["top_frac"] <= 1
         assert 0.008 <= p["casing_t"] <= 0.012
         assert 0.9 * 1700 <= p["cement_vs"] <= 1.1 * 1700 and 0.9 * 2300 <= p["rock_vs"] <= 1.1 * 2300
+
+
+def test_full_scale_well_medium_is_valid():
+    """A shortened variant of the 20 m well (same radial grid, noise and
+    grading): every cell ID indexes the table; noisy rock spans +-5 %."""
+    sc = W.config2(nz=256)
+    med = sc.medium
+    assert med.cell_id.max() < med.n_mat
+    g = sc.grid
+    rock = med.cell_id[:, int(0.15 / g.dr) + 1:, :]
+    vp = med.vp[rock]
+    # normalised by max|g|: one extreme reaches exactly 5 %, none exceeds it
+    assert np.abs(vp / 4000 - 1).max() == pytest.approx(0.05, rel=1e-9)
+    assert len(np.unique(rock)) > 500
+    full = W.config2.__doc__
+    assert "20000 steps" in full
