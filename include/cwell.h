@@ -147,9 +147,15 @@ double sim_dt(const sim_t *h);
 int sim_steps_done(const sim_t *h);
 size_t sim_device_bytes(const sim_t *h);
 
+/* Path the handle runs: *kernel = SIM_KERNEL_SPLIT or SIM_KERNEL_FUSED;
+ * *tile_rows = r rows per block of the fused kernel chosen by the autotuner
+ * (0 for the split path). */
+int sim_config(const sim_t *h, int *kernel, int *tile_rows);
+
 /* Kernel timings gathered with opts.timing = 1: for kernel slot q
- * (0 = main update kernel, 1 = stress kernel of the split path, 2 = receivers),
- * total milliseconds and launch count so far.  Synchronises. */
+ * (0 = fused kernel or velocity kernel of the split path, 1 = stress kernel of
+ * the split path, 2 = receivers), total milliseconds and launch count so far.
+ * Synchronises. */
 int sim_kernel_time(sim_t *h, int q, double *ms, long *launches);
 
 /* Checkpoint: write / read fields, PML memory variables, step counter and

@@ -79,6 +79,8 @@ def lib(path: str | None = None):
         L.sim_steps_done.restype = i
         L.sim_device_bytes.argtypes = [p]
         L.sim_device_bytes.restype = sz
+        L.sim_config.argtypes = [p, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.sim_config.restype = i
         L.sim_kernel_time.argtypes = [p, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_long)]
         L.sim_kernel_time.restype = i
         L.sim_save.argtypes = [p, ctypes.c_char_p]
@@ -202,6 +204,12 @@ class Simulation:
         assert a.shape == self.grid.shape
         _check(self.L, self.h, self.L.sim_write_field(self.h, FIELDS.index(name),
                                                       a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
+
+    def config(self):
+        """(kernel, tile_rows): kernel 1 = split, 2 = fused; tile rows chosen by the autotuner."""
+        k, t = ctypes.c_int(), ctypes.c_int()
+        _check(self.L, self.h, self.L.sim_config(self.h, ctypes.byref(k), ctypes.byref(t)))
+        return k.value, t.value
 
     def kernel_time(self, q: int):
         ms, n = ctypes.c_double(), ctypes.c_long()

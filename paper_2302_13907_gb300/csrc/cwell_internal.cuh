@@ -14,6 +14,7 @@
 //    slab [6][nth][NR][2 pml_z], FP32.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -140,8 +141,28 @@ __device__ __forceinline__ float stretch(float *psi, float a, float b, float D) 
 
 }  // namespace cwell
 
-// launchers implemented in the .cu files (host side)
 namespace cwell {
+// TMA descriptors of the fused kernel: the six stresses of the buffer being
+// read, and the material IDs; 3-D [nth][NR][NZp] tensors.
+struct FusedMaps {
+  CUtensorMap sig[6];
+  CUtensorMap id;
+};
+// Fused kernel parameters: k.f / k.psr / k.psz are the buffers read (step n),
+// fo / psr_o / psz_o the buffers written (step n + 1).
+struct FusedParams {
+  KParams k;
+  void *fo[NF];
+  float *psr_o[NPR];
+  float *psz_o[NPZ];
+  int *status;  // bit 1: a bounded wait gave up
+};
+
+// launchers implemented in the .cu files (host side)
 cudaError_t launch_split(int storage, const KParams &p, cudaStream_t s, cudaEvent_t *ev);
 cudaError_t launch_receivers(int storage, const RParams &p, cudaStream_t s);
+cudaError_t launch_fused(int storage, int rt, const FusedMaps &maps, const FusedParams &fp, cudaStream_t s);
+size_t fused_smem_bytes(int storage, int rt);
+int fused_box_x(int storage);
+int fused_pad_x(int storage);
 }  // namespace cwell

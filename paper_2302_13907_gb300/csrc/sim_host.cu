@@ -6,8 +6,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "../../include/cwell.h"
 #include "cwell_internal.cuh"
@@ -34,6 +39,15 @@ struct sim_s {
   int n_wav = 0;
   KParams kp{};
   RParams rp{};
+  // fused path: second buffer set, TMA descriptors and parameters per step parity
+  bool fused = false;
+  int tile_rt = 0;
+  void *f2[NF] = {};
+  float *psr2[NPR] = {};
+  float *psz2[NPZ] = {};
+  FusedMaps maps[2];
+  FusedParams fp[2];
+  RParams rp2[2];
   int steps_done = 0;
   size_t bytes = 0, mem_cap = 0, psr_elems = 0, psz_elems = 0;
   std::vector<void *> allocs;
@@ -143,6 +157,109 @@ static void release(sim_t *h) {
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
+// ---------------------------------------------------------------- TMA descriptors
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// 3-D tiled descriptor of an [nth][NR][NZp] array, box {bx, rows, 1}; loads
+// outside the array read zeros.
+static int make_map(sim_t *h, CUtensorMap *m, void *base, CUtensorMapDataType dt, int elem, int bx, int rows) {
+  auto enc = tmap_encoder();
+  if (!enc) return fail(h, SIM_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  cuuint64_t dims[3] = {(cuuint64_t)h->NZp, (cuuint64_t)h->NR, (cuuint64_t)h->grid.nth};
+  cuuint64_t strides[2] = {(cuuint64_t)h->NZp * elem, (cuuint64_t)h->NZp * h->NR * elem};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(h, SIM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return SIM_OK;
+}
+
+static int build_maps(sim_t *h, int rt) {
+  const CUtensorMapDataType dt = h->storage == 0   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : h->storage == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  for (int par = 0; par < 2; par++) {
+    void **src = par == 0 ? h->f : h->f2;
+    for (int q = 0; q < 6; q++) {
+      int rc = make_map(h, &h->maps[par].sig[q], src[F_SRR + q], dt, (int)h->elem, fused_box_x(h->storage), rt + 2);
+      if (rc) return rc;
+    }
+    int rc = make_map(h, &h->maps[par].id, h->id, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, 64 + 16, rt + 2);
+    if (rc) return rc;
+  }
+  return SIM_OK;
+}
+
+// Autotuner: time each tile height on the still-zero state with the source
+// disabled (the state stays zero), keep the fastest; cached per grid shape.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int, int, int>, int> g_tune;
+
+static int autotune(sim_t *h, int *best_rt) {
+  int dev = h->device, maxsm = 0;
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  auto key = std::make_tuple(dev, h->grid.nth, h->NR, h->NZ, h->storage, h->kp.pml_r > 0 ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *best_rt = it->second;
+      return SIM_OK;
+    }
+  }
+  const int cand[3] = {4, 8, 12};
+  cudaEvent_t a, b;
+  CK(h, cudaEventCreate(&a));
+  CK(h, cudaEventCreate(&b));
+  float best = INFINITY;
+  int pick = 0;
+  for (int rt : cand) {
+    if (fused_smem_bytes(h->storage, rt) > (size_t)maxsm) continue;
+    int rc = build_maps(h, rt);
+    if (rc) return rc;
+    FusedParams dry = h->fp[0];
+    dry.k.src_i = -1;  // no source: zero state stays zero
+    cudaError_t e = cudaSuccess;
+    for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_fused(h->storage, rt, h->maps[0], dry, h->stream);
+    cudaEventRecord(a, h->stream);
+    for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_fused(h->storage, rt, h->maps[0], dry, h->stream);
+    cudaEventRecord(b, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      return cuda_fail(h, e, "autotune launch");
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best) {
+      best = ms;
+      pick = rt;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (!pick) return fail(h, SIM_EUNSUPPORTED, "no fused tile fits in shared memory");
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[key] = pick;
+  }
+  *best_rt = pick;
+  return SIM_OK;
+}
+
 extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, const sim_source_t *source,
                           const sim_receivers_t *receivers, const sim_opts_t *opts, sim_t **out) {
   if (!out) return fail(nullptr, SIM_EINVAL, "out is null");
@@ -169,7 +286,8 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   h->NZp = NZp;
   h->storage = opts->storage;
   h->elem = opts->storage == 0 ? 4 : 2;
-  h->kernel = SIM_KERNEL_SPLIT;
+  h->kernel = opts->kernel == SIM_KERNEL_SPLIT ? SIM_KERNEL_SPLIT : SIM_KERNEL_FUSED;
+  h->fused = h->kernel == SIM_KERNEL_FUSED;
   h->graph_chunk = opts->graph_chunk == 0 ? 64 : opts->graph_chunk;
   h->timing = opts->timing;
   h->mem_cap = opts->mem_cap;
@@ -294,6 +412,16 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
     for (int q = 0; q < NPZ; q++)
       if ((rc = dev_alloc(h, (void **)&h->psz[q], h->psz_elems * 4))) return bail(rc);
   }
+  if (h->fused) {
+    for (int q = 0; q < NF; q++)
+      if ((rc = dev_alloc(h, &h->f2[q], fbytes))) return bail(rc);
+    if (pml) {
+      for (int q = 0; q < NPR; q++)
+        if ((rc = dev_alloc(h, (void **)&h->psr2[q], h->psr_elems * 4))) return bail(rc);
+      for (int q = 0; q < NPZ; q++)
+        if ((rc = dev_alloc(h, (void **)&h->psz2[q], h->psz_elems * 4))) return bail(rc);
+    }
+  }
   if ((rc = dev_alloc(h, (void **)&h->id, (size_t)nth * NR * NZp * 2))) return bail(rc);
   if ((rc = dev_alloc(h, (void **)&h->mat, mat.size() * sizeof(float4)))) return bail(rc);
   if ((rc = dev_alloc(h, (void **)&h->ab_r, NR * sizeof(float4)))) return bail(rc);
@@ -371,6 +499,37 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   r.traces = h->traces;
   r.step = h->step;
   r.status = h->status;
+  if (h->fused) {
+    for (int par = 0; par < 2; par++) {
+      FusedParams &f = h->fp[par];
+      f.k = p;
+      void **cur = par == 0 ? h->f : h->f2, **nxt = par == 0 ? h->f2 : h->f;
+      float **pc = par == 0 ? h->psr : h->psr2, **pn = par == 0 ? h->psr2 : h->psr;
+      float **zc = par == 0 ? h->psz : h->psz2, **zn = par == 0 ? h->psz2 : h->psz;
+      for (int q = 0; q < NF; q++) {
+        f.k.f[q] = cur[q];
+        f.fo[q] = nxt[q];
+      }
+      for (int q = 0; q < NPR; q++) {
+        f.k.psr[q] = pc[q];
+        f.psr_o[q] = pn[q];
+      }
+      for (int q = 0; q < NPZ; q++) {
+        f.k.psz[q] = zc[q];
+        f.psz_o[q] = zn[q];
+      }
+      f.status = h->status;
+      // the stresses of step n + 1 are in the buffer this parity writes
+      h->rp2[par] = r;
+      h->rp2[par].srr = nxt[F_SRR];
+      h->rp2[par].spp = nxt[F_SPP];
+      h->rp2[par].szz = nxt[F_SZZ];
+    }
+    if ((rc = autotune(h, &h->tile_rt))) return bail(rc);
+    if ((rc = build_maps(h, h->tile_rt))) return bail(rc);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "autotune"));
+  }
   if (h->timing)
     for (auto &ev : h->ev)
       if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(cuda_fail(h, e, "cudaEventCreate"));
@@ -378,10 +537,23 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   return SIM_OK;
 }
 
-static cudaError_t enqueue_step(sim_t *h, bool timed) {
-  cudaError_t e = launch_split(h->storage, h->kp, h->stream, timed ? h->ev : nullptr);
-  if (e != cudaSuccess) return e;
-  e = launch_receivers(h->storage, h->rp, h->stream);
+// Enqueue one step; `parity` = index of the step mod 2 (fused path buffers).
+static cudaError_t enqueue_step(sim_t *h, int parity, bool timed) {
+  cudaError_t e;
+  if (h->fused) {
+    if (timed) cudaEventRecord(h->ev[0], h->stream);
+    e = launch_fused(h->storage, h->tile_rt, h->maps[parity], h->fp[parity], h->stream);
+    if (e != cudaSuccess) return e;
+    if (timed) {
+      cudaEventRecord(h->ev[1], h->stream);
+      cudaEventRecord(h->ev[2], h->stream);
+    }
+    e = launch_receivers(h->storage, h->rp2[parity], h->stream);
+  } else {
+    e = launch_split(h->storage, h->kp, h->stream, timed ? h->ev : nullptr);
+    if (e != cudaSuccess) return e;
+    e = launch_receivers(h->storage, h->rp, h->stream);
+  }
   if (e != cudaSuccess) return e;
   if (timed) {
     cudaEventRecord(h->ev[3], h->stream);
@@ -406,19 +578,33 @@ extern "C" int sim_step(sim_t *h, int nsteps) {
   if (nsteps < 0) return fail(h, SIM_EINVAL, "nsteps < 0");
   CK(h, cudaSetDevice(h->device));
   int left = nsteps;
-  if (!h->timing && h->graph_chunk > 0 && left >= h->graph_chunk) {
+  auto direct = [&]() -> int {
+    cudaError_t e = enqueue_step(h, h->steps_done & 1, h->timing != 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+    h->steps_done++;
+    left--;
+    return SIM_OK;
+  };
+  // a captured chunk starts on an even step (fused buffers alternate) and has even length
+  int chunk = h->graph_chunk;
+  if (h->fused && chunk > 0 && (chunk & 1)) chunk++;
+  if (!h->timing && chunk > 0 && left >= chunk + (h->steps_done & 1)) {
+    if (h->steps_done & 1) {
+      int rc = direct();
+      if (rc) return rc;
+    }
     if (!h->gexec) {
       cudaGraph_t graph;
       CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
       cudaError_t e = cudaSuccess;
-      for (int q = 0; q < h->graph_chunk && e == cudaSuccess; q++) e = enqueue_step(h, false);
+      for (int q = 0; q < chunk && e == cudaSuccess; q++) e = enqueue_step(h, q & 1, false);
       cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
       if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch during capture");
       if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
       e = cudaGraphInstantiate(&h->gexec, graph, 0);
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
-      h->gsteps = h->graph_chunk;
+      h->gsteps = chunk;
     }
     while (left >= h->gsteps) {
       CK(h, cudaGraphLaunch(h->gexec, h->stream));
@@ -426,13 +612,17 @@ extern "C" int sim_step(sim_t *h, int nsteps) {
       h->steps_done += h->gsteps;
     }
   }
-  for (; left > 0; left--) {
-    cudaError_t e = enqueue_step(h, h->timing != 0);
-    if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
-    h->steps_done++;
+  while (left > 0) {
+    int rc = direct();
+    if (rc) return rc;
   }
   return SIM_OK;
 }
+
+// buffers holding the current state (the fused path alternates two sets)
+static void **cur_fields(sim_t *h) { return (h->fused && (h->steps_done & 1)) ? h->f2 : h->f; }
+static float **cur_psr(sim_t *h) { return (h->fused && (h->steps_done & 1)) ? h->psr2 : h->psr; }
+static float **cur_psz(sim_t *h) { return (h->fused && (h->steps_done & 1)) ? h->psz2 : h->psz; }
 
 extern "C" int sim_sync(sim_t *h) {
   if (!h) return SIM_EINVAL;
@@ -498,9 +688,9 @@ extern "C" int sim_read_field(sim_t *h, int which, float *out, size_t n) {
   const float sc = (float)(1.0 / field_scale(h, which));
   int blocks = (int)((tot + 255) / 256);
   switch (h->storage) {
-    case 0: to_f32<float><<<blocks, 256, 0, h->stream>>>((const float *)h->f[which], tmp, tot, sc); break;
-    case 1: to_f32<__nv_bfloat16><<<blocks, 256, 0, h->stream>>>((const __nv_bfloat16 *)h->f[which], tmp, tot, sc); break;
-    default: to_f32<__half><<<blocks, 256, 0, h->stream>>>((const __half *)h->f[which], tmp, tot, sc); break;
+    case 0: to_f32<float><<<blocks, 256, 0, h->stream>>>((const float *)cur_fields(h)[which], tmp, tot, sc); break;
+    case 1: to_f32<__nv_bfloat16><<<blocks, 256, 0, h->stream>>>((const __nv_bfloat16 *)cur_fields(h)[which], tmp, tot, sc); break;
+    default: to_f32<__half><<<blocks, 256, 0, h->stream>>>((const __half *)cur_fields(h)[which], tmp, tot, sc); break;
   }
   cudaError_t e = cudaMemcpy2DAsync(out, h->NZ * 4, tmp, h->NZp * 4, h->NZ * 4, rows, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -525,9 +715,9 @@ extern "C" int sim_write_field(sim_t *h, int which, const float *in, size_t n) {
     const float sc = (float)field_scale(h, which);
     int blocks = (int)((tot + 255) / 256);
     switch (h->storage) {
-      case 0: from_f32<float><<<blocks, 256, 0, h->stream>>>(tmp, (float *)h->f[which], tot, sc); break;
-      case 1: from_f32<__nv_bfloat16><<<blocks, 256, 0, h->stream>>>(tmp, (__nv_bfloat16 *)h->f[which], tot, sc); break;
-      default: from_f32<__half><<<blocks, 256, 0, h->stream>>>(tmp, (__half *)h->f[which], tot, sc); break;
+      case 0: from_f32<float><<<blocks, 256, 0, h->stream>>>(tmp, (float *)cur_fields(h)[which], tot, sc); break;
+      case 1: from_f32<__nv_bfloat16><<<blocks, 256, 0, h->stream>>>(tmp, (__nv_bfloat16 *)cur_fields(h)[which], tot, sc); break;
+      default: from_f32<__half><<<blocks, 256, 0, h->stream>>>(tmp, (__half *)cur_fields(h)[which], tot, sc); break;
     }
     e = cudaGetLastError();
   }
@@ -540,6 +730,13 @@ extern "C" int sim_write_field(sim_t *h, int which, const float *in, size_t n) {
 extern "C" double sim_dt(const sim_t *h) { return h ? h->dt : 0.0; }
 extern "C" int sim_steps_done(const sim_t *h) { return h ? h->steps_done : -1; }
 extern "C" size_t sim_device_bytes(const sim_t *h) { return h ? h->bytes : 0; }
+
+extern "C" int sim_config(const sim_t *h, int *kernel, int *tile_rows) {
+  if (!h) return SIM_EINVAL;
+  if (kernel) *kernel = h->kernel;
+  if (tile_rows) *tile_rows = h->fused ? h->tile_rt : 0;
+  return SIM_OK;
+}
 
 extern "C" int sim_kernel_time(sim_t *h, int q, double *ms, long *launches) {
   if (!h) return SIM_EINVAL;
@@ -572,9 +769,9 @@ extern "C" int sim_save(sim_t *h, const char *path) {
          fwrite(buf.data(), 1, bytes, fp) == bytes;
   };
   const size_t fbytes = (size_t)h->grid.nth * h->NR * h->NZp * h->elem;
-  for (int q = 0; q < NF; q++) dump(h->f[q], fbytes);
-  for (int q = 0; q < NPR; q++) dump(h->psr[q], h->psr_elems * 4);
-  for (int q = 0; q < NPZ; q++) dump(h->psz[q], h->psz_elems * 4);
+  for (int q = 0; q < NF; q++) dump(cur_fields(h)[q], fbytes);
+  for (int q = 0; q < NPR; q++) dump(cur_psr(h)[q], h->psr_elems * 4);
+  for (int q = 0; q < NPZ; q++) dump(cur_psz(h)[q], h->psz_elems * 4);
   dump(h->traces, (size_t)h->n_rec * h->cap * 4);
   dump(h->step, 4);
   if (fclose(fp) != 0) ok = false;
@@ -598,6 +795,8 @@ extern "C" int sim_load(sim_t *h, const char *path) {
     fclose(fp);
     return fail(h, SIM_EINVAL, "checkpoint does not match this handle");
   }
+  const int prev_steps = h->steps_done;
+  h->steps_done = (int)hdr[6];
   std::vector<char> buf;
   auto load = [&](void *dptr, size_t bytes) {
     if (!ok || !dptr) return;
@@ -606,14 +805,16 @@ extern "C" int sim_load(sim_t *h, const char *path) {
          cudaMemcpy(dptr, buf.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
   };
   const size_t fbytes = (size_t)h->grid.nth * h->NR * h->NZp * h->elem;
-  for (int q = 0; q < NF; q++) load(h->f[q], fbytes);
-  for (int q = 0; q < NPR; q++) load(h->psr[q], h->psr_elems * 4);
-  for (int q = 0; q < NPZ; q++) load(h->psz[q], h->psz_elems * 4);
+  for (int q = 0; q < NF; q++) load(cur_fields(h)[q], fbytes);
+  for (int q = 0; q < NPR; q++) load(cur_psr(h)[q], h->psr_elems * 4);
+  for (int q = 0; q < NPZ; q++) load(cur_psz(h)[q], h->psz_elems * 4);
   load(h->traces, (size_t)h->n_rec * h->cap * 4);
   load(h->step, 4);
   fclose(fp);
-  if (!ok) return fail(h, SIM_EINVAL, "checkpoint read failed");
-  h->steps_done = (int)hdr[6];
+  if (!ok) {
+    h->steps_done = prev_steps;
+    return fail(h, SIM_EINVAL, "checkpoint read failed");
+  }
   return SIM_OK;
 }
 

@@ -26,9 +26,10 @@ namespace cwell {
 
 constexpr int SB_X = 32;  // z-quads per block
 constexpr int SB_Y = 4;   // r rows per block
+constexpr int SB_MINB = 6;  // resident blocks per SM asked of the register allocator
 
 template <typename T>
-__global__ void __launch_bounds__(SB_X *SB_Y) vel_split(const KParams p) {
+__global__ void __launch_bounds__(SB_X *SB_Y, SB_MINB) vel_split(const KParams p) {
   const int j = blockIdx.x;
   const int i = blockIdx.y * SB_Y + threadIdx.y;
   const int k0 = (blockIdx.z * SB_X + threadIdx.x) * 4;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(SB_X *SB_Y) vel_split(const KParams p) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SB_X *SB_Y) str_split(const KParams p) {
+__global__ void __launch_bounds__(SB_X *SB_Y, SB_MINB) str_split(const KParams p) {
   const int j = blockIdx.x;
   const int i = blockIdx.y * SB_Y + threadIdx.y;
   const int k0 = (blockIdx.z * SB_X + threadIdx.x) * 4;

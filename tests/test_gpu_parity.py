@@ -39,7 +39,7 @@ def _ragged_scenario(seed=0, nth=6, nr=9, pml_r=3, nz=37, pml_z=3):
     return W.Scenario("ragged", med, W.Source(r=0.014, theta=2.0, z=0.06, f0=60e3), rec, steps=200)
 
 
-@pytest.mark.parametrize("kernel", ["split", "auto"])
+@pytest.mark.parametrize("kernel", ["split", "fused"])
 def test_config1_traces_match_oracle(kernel):
     sc = W.config1()
     o = oracle.Oracle(sc)
@@ -71,8 +71,9 @@ def test_config1_long_window_traces_match_oracle():
             assert rel_l2(got[q], ref[q]) <= 10 * TRACE_TOL, q
 
 
-@pytest.mark.parametrize("kernel", ["split", "auto"])
-@pytest.mark.parametrize("seed,nth,nr,nz", [(0, 6, 9, 37), (1, 4, 5, 70), (2, 8, 13, 2), (3, 4, 40, 131)])
+@pytest.mark.parametrize("kernel", ["split", "fused"])
+@pytest.mark.parametrize("seed,nth,nr,nz", [(0, 6, 9, 37), (1, 4, 5, 70), (2, 8, 13, 2), (3, 4, 40, 131),
+                                            (4, 10, 29, 190)])
 def test_ragged_grid_fields_elementwise(kernel, seed, nth, nr, nz):
     sc = _ragged_scenario(seed=seed, nth=nth, nr=nr, nz=nz)
     if nz < 20:  # tiny z: keep source / receivers inside
@@ -226,4 +227,26 @@ def test_full_size_well_sampled_against_oracle_crop():
         sub = a[:, :, lo + 8:hi - 8]
         ref = b[:, :, 8:-8]
         assert np.abs(a[:, :, : lo]).max() == 0 and np.abs(a[:, :, hi:]).max() == 0, q
+        if np.abs(ref).max() == 0:  # e.g. shear stress next to the source, all liquid
+            assert np.abs(sub).max() == 0, q
+            continue
         assert rel_l2(sub, ref) <= TRACE_TOL, (q, rel_l2(sub, ref))
+
+
+def test_fused_matches_split_and_autotuner_choice():
+    """The fused (time-skewed, TMA-staged) kernel and the split kernels
+    compute the same scheme: traces agree to FP32 rounding; every tile
+    height the autotuner may pick gives the same answer."""
+    sc = W.config1(steps=400)
+    with sim(sc, kernel="split") as a:
+        a.step(400)
+        ta = a.traces()
+        fa = {n: a.field(n) for n in ("vr", "srr", "srz")}
+    with sim(sc, kernel="fused") as b:
+        kind, tile = b.config()
+        assert kind == 2 and tile in (4, 8, 12)
+        b.step(400)
+        tb = b.traces()
+        assert rel_l2(tb, ta) <= 1e-6
+        for n, x in fa.items():
+            assert rel_l2(b.field(n), x) <= 1e-6, n
