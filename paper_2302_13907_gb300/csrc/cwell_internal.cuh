@@ -40,6 +40,9 @@ struct KParams {
   const float4 *ab_q;   // [NR] the same for the 1/r group (integrated profile)
   const float4 *ab_z;   // [NZ] {a, b} at the cell centre, {a, b} at the half node
   const float4 *mat;    // [n_mat] {rho, lambda, mu, 1/mu}
+  const float *m_rho;   // [n_mat] rho
+  const float *m_imu;   // [n_mat] 1/mu (+inf for a liquid)
+  const float2 *m_lam;  // [n_mat] {lambda, lambda + 2 mu}
   const uint16_t *id;   // [nth][NR][NZp]
   void *f[NF];          // field storage (type set by the kernel template)
   float *psr[NPR];      // [nth][pml_r][NZp]
@@ -142,10 +145,11 @@ __device__ __forceinline__ float stretch(float *psi, float a, float b, float D) 
 }  // namespace cwell
 
 namespace cwell {
-// TMA descriptors of the fused kernel: the six stresses of the buffer being
-// read, and the material IDs; 3-D [nth][NR][NZp] tensors.
+// TMA descriptors of the fused kernel: the nine fields of the buffer being
+// read (field order F_*), and the material IDs; 4-D [case][nth][NR][NZp]
+// tensors (one case for a single well).
 struct FusedMaps {
-  CUtensorMap sig[6];
+  CUtensorMap f[NF];
   CUtensorMap id;
 };
 // Fused kernel parameters: k.f / k.psr / k.psz are the buffers read (step n),

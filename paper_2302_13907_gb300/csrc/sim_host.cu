@@ -34,6 +34,8 @@ struct sim_s {
   float *psz[NPZ] = {};
   uint16_t *id = nullptr;
   float4 *mat = nullptr, *ab_r = nullptr, *ab_q = nullptr, *ab_z = nullptr;
+  float *m_rho = nullptr, *m_imu = nullptr;
+  float2 *m_lam = nullptr;
   float *inv_ri = nullptr, *inv_rh = nullptr, *wav = nullptr, *traces = nullptr;
   int *rec = nullptr, *step = nullptr, *status = nullptr;
   int n_wav = 0;
@@ -171,16 +173,17 @@ static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
   return fn;
 }
 
-// 3-D tiled descriptor of an [nth][NR][NZp] array, box {bx, rows, 1}; loads
-// outside the array read zeros.
+// 4-D tiled descriptor of an [1][nth][NR][NZp] array, box {bx, rows, 1, 1};
+// loads outside the array read zeros.
 static int make_map(sim_t *h, CUtensorMap *m, void *base, CUtensorMapDataType dt, int elem, int bx, int rows) {
   auto enc = tmap_encoder();
   if (!enc) return fail(h, SIM_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-  cuuint64_t dims[3] = {(cuuint64_t)h->NZp, (cuuint64_t)h->NR, (cuuint64_t)h->grid.nth};
-  cuuint64_t strides[2] = {(cuuint64_t)h->NZp * elem, (cuuint64_t)h->NZp * h->NR * elem};
-  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)rows, 1};
-  cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = enc(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+  cuuint64_t dims[4] = {(cuuint64_t)h->NZp, (cuuint64_t)h->NR, (cuuint64_t)h->grid.nth, 1};
+  cuuint64_t strides[3] = {(cuuint64_t)h->NZp * elem, (cuuint64_t)h->NZp * h->NR * elem,
+                           (cuuint64_t)h->NZp * h->NR * h->grid.nth * elem};
+  cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)rows, 1, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, dt, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(h, SIM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   return SIM_OK;
@@ -192,8 +195,8 @@ static int build_maps(sim_t *h, int rt) {
                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   for (int par = 0; par < 2; par++) {
     void **src = par == 0 ? h->f : h->f2;
-    for (int q = 0; q < 6; q++) {
-      int rc = make_map(h, &h->maps[par].sig[q], src[F_SRR + q], dt, (int)h->elem, fused_box_x(h->storage), rt + 2);
+    for (int q = 0; q < NF; q++) {
+      int rc = make_map(h, &h->maps[par].f[q], src[q], dt, (int)h->elem, fused_box_x(h->storage), rt + 2);
       if (rc) return rc;
     }
     int rc = make_map(h, &h->maps[par].id, h->id, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, 64 + 16, rt + 2);
@@ -219,7 +222,7 @@ static int autotune(sim_t *h, int *best_rt) {
       return SIM_OK;
     }
   }
-  const int cand[3] = {4, 8, 12};
+  const int cand[4] = {2, 4, 6, 8};
   cudaEvent_t a, b;
   CK(h, cudaEventCreate(&a));
   CK(h, cudaEventCreate(&b));
@@ -345,11 +348,16 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
 
   // --- material table {rho, lambda, mu, 1/mu}; Lame from the cell-centre values
   std::vector<float4> mat(h->n_mat);
+  std::vector<float> m_rho(h->n_mat), m_imu(h->n_mat);
+  std::vector<float2> m_lam(h->n_mat);
   double vpmax = 0;
   for (int q = 0; q < h->n_mat; q++) {
     double rho = medium->rho[q], mu = rho * medium->vs[q] * medium->vs[q];
     double lam = rho * medium->vp[q] * medium->vp[q] - 2.0 * mu;
     mat[q] = make_float4((float)rho, (float)lam, (float)mu, mu > 0 ? (float)(1.0 / mu) : INFINITY);
+    m_rho[q] = mat[q].x;
+    m_imu[q] = mat[q].w;
+    m_lam[q] = make_float2(mat[q].y, mat[q].y + 2.f * mat[q].z);
     vpmax = std::max(vpmax, medium->vp[q]);
   }
   // --- radius tables
@@ -424,6 +432,9 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   }
   if ((rc = dev_alloc(h, (void **)&h->id, (size_t)nth * NR * NZp * 2))) return bail(rc);
   if ((rc = dev_alloc(h, (void **)&h->mat, mat.size() * sizeof(float4)))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->m_rho, mat.size() * 4))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->m_imu, mat.size() * 4))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->m_lam, mat.size() * 8))) return bail(rc);
   if ((rc = dev_alloc(h, (void **)&h->ab_r, NR * sizeof(float4)))) return bail(rc);
   if ((rc = dev_alloc(h, (void **)&h->ab_q, NR * sizeof(float4)))) return bail(rc);
   if ((rc = dev_alloc(h, (void **)&h->ab_z, NZ * sizeof(float4)))) return bail(rc);
@@ -441,6 +452,9 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   e = cudaMemcpy2DAsync(h->id, NZp * 2, cid, NZ * 2, NZ * 2, (size_t)nth * NR, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return bail(cuda_fail(h, e, "upload cell_id"));
   UP(h->mat, mat.data(), mat.size() * sizeof(float4));
+  UP(h->m_rho, m_rho.data(), mat.size() * 4);
+  UP(h->m_imu, m_imu.data(), mat.size() * 4);
+  UP(h->m_lam, m_lam.data(), mat.size() * 8);
   UP(h->ab_r, ab_r.data(), NR * sizeof(float4));
   UP(h->ab_q, ab_q.data(), NR * sizeof(float4));
   UP(h->ab_z, ab_z.data(), NZ * sizeof(float4));
@@ -474,6 +488,9 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   p.ab_q = h->ab_q;
   p.ab_z = h->ab_z;
   p.mat = h->mat;
+  p.m_rho = h->m_rho;
+  p.m_imu = h->m_imu;
+  p.m_lam = h->m_lam;
   p.id = h->id;
   for (int q = 0; q < NF; q++) p.f[q] = h->f[q];
   for (int q = 0; q < NPR; q++) p.psr[q] = h->psr[q];
