@@ -168,6 +168,40 @@ void sim_destroy(sim_t *h);
 const char *sim_last_error(const sim_t *h);
 const char *sim_error_string(int code);
 
+/* ------------------------------------------------------------------------
+ * Batched scenarios: n independent wells (e.g. cement-hardening cases of
+ * uneven length) advanced together, one launch per kernel per step for all
+ * of them.  Each case is defined exactly as for sim_create (grid, medium,
+ * source, receivers; shapes may differ between cases); opts is shared
+ * (storage, stream, device, mem_cap applied to the batch total, graph_chunk,
+ * max_steps).  The cases run the split kernels driven by persistent blocks
+ * that walk a work list of (case, theta, r tile, z tile) items; the number of
+ * persistent blocks is chosen by timing candidates at create time.  A case
+ * computes exactly what its own sim_create handle would.
+ * ------------------------------------------------------------------------ */
+typedef struct simb_s simb_t;
+
+/* Arrays hold n entries.  On failure *out is NULL and simb_last_error(NULL)
+ * names the failing case. */
+int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *media, const sim_source_t *sources,
+                const sim_receivers_t *receivers, const sim_opts_t *opts, simb_t **out);
+
+/* Enqueue nsteps leapfrog steps of every case (nsteps >= 0). */
+int simb_run(simb_t *b, int nsteps);
+
+/* Wait for the batch; reports device-side failures of any case. */
+int simb_sync(simb_t *b);
+
+/* Traces of case `which` as sim_traces; field of case `which` as sim_read_field. */
+int simb_traces(simb_t *b, int which, float *out, size_t cap, int *n_rec, int *n_steps);
+int simb_read_field(simb_t *b, int which, int field, float *out, size_t n);
+
+/* Number of cases, work items per kernel launch, persistent blocks per launch. */
+int simb_config(const simb_t *b, int *n_cases, long long *work_items, int *grid_blocks);
+
+void simb_destroy(simb_t *b);
+const char *simb_last_error(const simb_t *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,6 +93,23 @@ def lib(path: str | None = None):
         L.sim_last_error.restype = ctypes.c_char_p
         L.sim_error_string.argtypes = [i]
         L.sim_error_string.restype = ctypes.c_char_p
+        L.simb_create.argtypes = [i, ctypes.POINTER(SimGrid), ctypes.POINTER(SimMedium), ctypes.POINTER(SimSource),
+                                  ctypes.POINTER(SimReceivers), ctypes.POINTER(SimOpts), ctypes.POINTER(p)]
+        L.simb_create.restype = i
+        L.simb_run.argtypes = [p, i]
+        L.simb_run.restype = i
+        L.simb_sync.argtypes = [p]
+        L.simb_sync.restype = i
+        L.simb_traces.argtypes = [p, i, ctypes.POINTER(ctypes.c_float), sz, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.simb_traces.restype = i
+        L.simb_read_field.argtypes = [p, i, i, ctypes.POINTER(ctypes.c_float), sz]
+        L.simb_read_field.restype = i
+        L.simb_config.argtypes = [p, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i)]
+        L.simb_config.restype = i
+        L.simb_destroy.argtypes = [p]
+        L.simb_destroy.restype = None
+        L.simb_last_error.argtypes = [p]
+        L.simb_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -221,3 +238,73 @@ class Simulation:
 
     def load(self, path: str):
         _check(self.L, self.h, self.L.sim_load(self.h, path.encode()))
+
+
+class BatchSimulation:
+    """Many wells advanced together (simb_create ... simb_destroy)."""
+
+    def __init__(self, scenarios, **kw):
+        self.L = lib()
+        n = len(scenarios)
+        if n == 0:
+            raise SimError(SIM_EINVAL, "a batch needs at least one scenario")
+        parts = [make_structs(sc, **kw) for sc in scenarios]
+        self._keep = [k for _, k in parts]
+        G = (SimGrid * n)(*[p[0][0] for p in parts])
+        M = (SimMedium * n)(*[p[0][1] for p in parts])
+        S = (SimSource * n)(*[p[0][2] for p in parts])
+        R = (SimReceivers * n)(*[p[0][3] for p in parts])
+        opts = parts[0][0][4]
+        self._arrays = (G, M, S, R, opts)
+        self.grids = [sc.medium.grid for sc in scenarios]
+        h = ctypes.c_void_p()
+        rc = self.L.simb_create(n, G, M, S, R, ctypes.byref(opts), ctypes.byref(h))
+        if rc != SIM_OK:
+            raise SimError(rc, self.L.simb_last_error(None).decode())
+        self.h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.simb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _chk(self, rc):
+        if rc != SIM_OK:
+            raise SimError(rc, self.L.simb_last_error(self.h).decode())
+
+    def run(self, n: int):
+        self._chk(self.L.simb_run(self.h, int(n)))
+        return self
+
+    def sync(self):
+        self._chk(self.L.simb_sync(self.h))
+
+    def traces(self, which: int) -> np.ndarray:
+        nr, ns = ctypes.c_int(), ctypes.c_int()
+        self._chk(self.L.simb_traces(self.h, int(which), None, 0, ctypes.byref(nr), ctypes.byref(ns)))
+        out = np.zeros((nr.value, ns.value), np.float32)
+        self._chk(self.L.simb_traces(self.h, int(which), out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size,
+                                     ctypes.byref(nr), ctypes.byref(ns)))
+        return out
+
+    def field(self, which: int, name: str) -> np.ndarray:
+        out = np.zeros(self.grids[which].shape, np.float32)
+        self._chk(self.L.simb_read_field(self.h, int(which), FIELDS.index(name),
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size))
+        return out
+
+    def config(self):
+        """(cases, work items per launch, persistent blocks per launch)."""
+        n, w, g = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
+        self._chk(self.L.simb_config(self.h, ctypes.byref(n), ctypes.byref(w), ctypes.byref(g)))
+        return n.value, w.value, g.value

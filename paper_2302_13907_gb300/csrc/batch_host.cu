@@ -1,0 +1,250 @@
+// Batched scenarios: many wells advanced by one persistent launch per kernel
+// per step.  Every case is a regular simulator handle (same validation and
+// set-up as sim_create, split kernels, buffers updated in place); the batch
+// holds device arrays of their kernel parameters and a prefix sum of their
+// work items, and captures its steps in a CUDA graph.
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "sim_state.cuh"
+
+struct simb_s {
+  int device = 0, storage = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<sim_t *> cases;
+  KParams *d_cases = nullptr;
+  RParams *d_rp = nullptr;
+  long long *d_start = nullptr;
+  long long total = 0;
+  int grid = 0, graph_chunk = 64, steps_done = 0;
+  cudaGraphExec_t gexec = nullptr;
+  int gsteps = 0;
+  std::string err;
+};
+
+static thread_local std::string g_batch_err;
+
+static int bfail(simb_t *b, int code, const std::string &msg) {
+  if (b) b->err = msg;
+  else g_batch_err = msg;
+  return code;
+}
+
+static int bcuda(simb_t *b, cudaError_t e, const char *what) {
+  return bfail(b, SIM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static void brelease(simb_t *b) {
+  if (!b) return;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (sim_t *h : b->cases) sim_destroy(h);
+  b->cases.clear();
+  if (b->d_cases) cudaFree(b->d_cases);
+  if (b->d_rp) cudaFree(b->d_rp);
+  if (b->d_start) cudaFree(b->d_start);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+static cudaError_t batch_step(simb_t *b, const KParams *cases) {
+  const int n = (int)b->cases.size();
+  cudaError_t e = launch_batch_split(b->storage, true, cases, b->d_start, n, b->total, b->grid, b->stream);
+  if (e == cudaSuccess) e = launch_batch_split(b->storage, false, cases, b->d_start, n, b->total, b->grid, b->stream);
+  return e;
+}
+
+// time persistent grids of several sizes (and one block per item) on the
+// still-zero state with every source disabled; keep the fastest
+static int tune_grid(simb_t *b) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  const int n = (int)b->cases.size();
+  std::vector<KParams> dry(n);
+  for (int c = 0; c < n; c++) {
+    dry[c] = b->cases[c]->kp;
+    dry[c].src_i = -1;
+  }
+  KParams *d_dry = nullptr;
+  cudaError_t e = cudaMalloc(&d_dry, n * sizeof(KParams));
+  if (e != cudaSuccess) return bcuda(b, e, "cudaMalloc");
+  e = cudaMemcpy(d_dry, dry.data(), n * sizeof(KParams), cudaMemcpyHostToDevice);
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  const long long cand[5] = {(long long)sms * 6, (long long)sms * 12, (long long)sms * 24, (long long)sms * 48,
+                             b->total};
+  float best = INFINITY;
+  int pick = (int)std::min<long long>(b->total, (long long)sms * 12);
+  for (long long g : cand) {
+    if (e != cudaSuccess) break;
+    b->grid = (int)std::max<long long>(1, std::min<long long>(g, std::min<long long>(b->total, 1LL << 30)));
+    e = batch_step(b, d_dry);
+    cudaEventRecord(t0, b->stream);
+    for (int w = 0; w < 3 && e == cudaSuccess; w++) e = batch_step(b, d_dry);
+    cudaEventRecord(t1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, t0, t1);
+    if (e == cudaSuccess && ms < best) {
+      best = ms;
+      pick = b->grid;
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  cudaFree(d_dry);
+  if (e != cudaSuccess) return bcuda(b, e, "batch autotune");
+  b->grid = pick;
+  return SIM_OK;
+}
+
+extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *media, const sim_source_t *sources,
+                           const sim_receivers_t *receivers, const sim_opts_t *opts, simb_t **out) {
+  if (!out) return bfail(nullptr, SIM_EINVAL, "out is null");
+  *out = nullptr;
+  if (n < 1 || !grids || !media || !sources || !receivers || !opts)
+    return bfail(nullptr, SIM_EINVAL, "need n >= 1 and non-null arrays");
+  for (int c = 0; c < n; c++) {  // host-side checks of every case before any device work
+    int rc = validate_inputs(&grids[c], &media[c], &sources[c], &receivers[c], opts);
+    if (rc) return bfail(nullptr, rc, "case " + std::to_string(c) + ": " + g_create_err);
+  }
+  simb_t *b = new simb_t();
+  b->device = opts->device;
+  b->storage = opts->storage;
+  b->graph_chunk = opts->graph_chunk == 0 ? 64 : opts->graph_chunk;
+  auto bail = [&](int code) {
+    g_batch_err = b->err;
+    brelease(b);
+    delete b;
+    return code;
+  };
+  cudaError_t e = cudaSetDevice(b->device);
+  if (e != cudaSuccess) return bail(bcuda(b, e, "cudaSetDevice"));
+  if (opts->cuda_stream) {
+    b->stream = (cudaStream_t)opts->cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(bcuda(b, e, "cudaStreamCreate"));
+    b->own_stream = true;
+  }
+  sim_opts_t o = *opts;
+  o.kernel = SIM_KERNEL_SPLIT;
+  o.cuda_stream = b->stream;
+  o.graph_chunk = -1;
+  o.timing = 0;
+  size_t used = 0;
+  std::vector<long long> start(n + 1, 0);
+  for (int c = 0; c < n; c++) {
+    if (opts->mem_cap) o.mem_cap = opts->mem_cap > used ? opts->mem_cap - used : 1;
+    sim_t *h = nullptr;
+    int rc = sim_create(&grids[c], &media[c], &sources[c], &receivers[c], &o, &h);
+    if (rc) return bail(bfail(b, rc, "case " + std::to_string(c) + ": " + sim_last_error(nullptr)));
+    b->cases.push_back(h);
+    used += sim_device_bytes(h);
+    start[c + 1] = start[c] + split_items(grids[c].nth, grids[c].nr + grids[c].pml_r, grids[c].nz + 2 * grids[c].pml_z);
+  }
+  b->total = start[n];
+  std::vector<KParams> kp(n);
+  std::vector<RParams> rp(n);
+  for (int c = 0; c < n; c++) {
+    kp[c] = b->cases[c]->kp;
+    rp[c] = b->cases[c]->rp;
+  }
+  if ((e = cudaMalloc(&b->d_cases, n * sizeof(KParams))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_rp, n * sizeof(RParams))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_start, (n + 1) * sizeof(long long))) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(bfail(b, SIM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)));
+  }
+  if ((e = cudaMemcpy(b->d_cases, kp.data(), n * sizeof(KParams), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_rp, rp.data(), n * sizeof(RParams), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_start, start.data(), (n + 1) * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(bcuda(b, e, "upload batch tables"));
+  int rc = tune_grid(b);
+  if (rc) return bail(rc);
+  *out = b;
+  return SIM_OK;
+}
+
+static cudaError_t enqueue_batch_step(simb_t *b) {
+  cudaError_t e = batch_step(b, b->d_cases);
+  if (e == cudaSuccess) e = launch_batch_receivers(b->storage, b->d_rp, (int)b->cases.size(), b->stream);
+  return e;
+}
+
+extern "C" int simb_run(simb_t *b, int nsteps) {
+  if (!b) return SIM_EINVAL;
+  if (nsteps < 0) return bfail(b, SIM_EINVAL, "nsteps < 0");
+  cudaError_t e = cudaSetDevice(b->device);
+  if (e != cudaSuccess) return bcuda(b, e, "cudaSetDevice");
+  int left = nsteps;
+  if (b->graph_chunk > 0 && left >= b->graph_chunk) {
+    if (!b->gexec) {
+      cudaGraph_t graph;
+      if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bcuda(b, e, "cudaStreamBeginCapture");
+      cudaError_t e1 = cudaSuccess;
+      for (int q = 0; q < b->graph_chunk && e1 == cudaSuccess; q++) e1 = enqueue_batch_step(b);
+      e = cudaStreamEndCapture(b->stream, &graph);
+      if (e1 != cudaSuccess) return bcuda(b, e1, "kernel launch during capture");
+      if (e != cudaSuccess) return bcuda(b, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&b->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return bcuda(b, e, "cudaGraphInstantiate");
+      b->gsteps = b->graph_chunk;
+    }
+    while (left >= b->gsteps) {
+      if ((e = cudaGraphLaunch(b->gexec, b->stream)) != cudaSuccess) return bcuda(b, e, "cudaGraphLaunch");
+      left -= b->gsteps;
+    }
+  }
+  for (; left > 0; left--)
+    if ((e = enqueue_batch_step(b)) != cudaSuccess) return bcuda(b, e, "kernel launch");
+  b->steps_done += nsteps;
+  for (sim_t *h : b->cases) sim_advance(h, nsteps);
+  return SIM_OK;
+}
+
+extern "C" int simb_sync(simb_t *b) {
+  if (!b) return SIM_EINVAL;
+  for (size_t c = 0; c < b->cases.size(); c++) {
+    int rc = sim_sync(b->cases[c]);
+    if (rc) return bfail(b, rc, "case " + std::to_string(c) + ": " + sim_last_error(b->cases[c]));
+  }
+  return SIM_OK;
+}
+
+extern "C" int simb_traces(simb_t *b, int which, float *out, size_t cap, int *n_rec, int *n_steps) {
+  if (!b) return SIM_EINVAL;
+  if (which < 0 || which >= (int)b->cases.size()) return bfail(b, SIM_EINVAL, "case index out of range");
+  int rc = sim_traces(b->cases[which], out, cap, n_rec, n_steps);
+  if (rc) bfail(b, rc, sim_last_error(b->cases[which]));
+  return rc;
+}
+
+extern "C" int simb_read_field(simb_t *b, int which, int field, float *out, size_t n) {
+  if (!b) return SIM_EINVAL;
+  if (which < 0 || which >= (int)b->cases.size()) return bfail(b, SIM_EINVAL, "case index out of range");
+  int rc = sim_read_field(b->cases[which], field, out, n);
+  if (rc) bfail(b, rc, sim_last_error(b->cases[which]));
+  return rc;
+}
+
+extern "C" int simb_config(const simb_t *b, int *n_cases, long long *work_items, int *grid_blocks) {
+  if (!b) return SIM_EINVAL;
+  if (n_cases) *n_cases = (int)b->cases.size();
+  if (work_items) *work_items = b->total;
+  if (grid_blocks) *grid_blocks = b->grid;
+  return SIM_OK;
+}
+
+extern "C" void simb_destroy(simb_t *b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  brelease(b);
+  delete b;
+}
+
+extern "C" const char *simb_last_error(const simb_t *b) { return b ? b->err.c_str() : g_batch_err.c_str(); }

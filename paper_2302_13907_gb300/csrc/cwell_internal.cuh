@@ -167,6 +167,10 @@ cudaError_t launch_split(int storage, const KParams &p, cudaStream_t s, cudaEven
 cudaError_t launch_receivers(int storage, const RParams &p, cudaStream_t s);
 cudaError_t launch_fused(int storage, int rt, const FusedMaps &maps, const FusedParams &fp, cudaStream_t s);
 size_t fused_smem_bytes(int storage, int rt);
+long long split_items(int nth, int NR, int NZ);
+cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, const long long *start, int n_cases,
+                               long long total, int grid, cudaStream_t s);
+cudaError_t launch_batch_receivers(int storage, const RParams *rp, int n_cases, cudaStream_t s);
 int fused_box_x(int storage);
 int fused_pad_x(int storage);
 }  // namespace cwell

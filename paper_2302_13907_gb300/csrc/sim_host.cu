@@ -12,72 +12,11 @@
 #include <tuple>
 #include <vector>
 
-#include <cudaTypedefs.h>
-
-#include "../../include/cwell.h"
-#include "cwell_internal.cuh"
+#include "sim_state.cuh"
 
 using namespace cwell;
 
-struct sim_s {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  sim_grid_t grid{};
-  int NR = 0, NZ = 0, NZp = 0;
-  double dt = 0, vscale = 1, sscale = 1;
-  int storage = 0, kernel = SIM_KERNEL_SPLIT, graph_chunk = 64, timing = 0;
-  int n_mat = 0, n_rec = 0, cap = 0;
-  size_t elem = 4;
-  void *f[NF] = {};
-  float *psr[NPR] = {};
-  float *psz[NPZ] = {};
-  uint16_t *id = nullptr;
-  float4 *mat = nullptr, *ab_r = nullptr, *ab_q = nullptr, *ab_z = nullptr;
-  float *m_rho = nullptr, *m_imu = nullptr;
-  float2 *m_lam = nullptr;
-  float *inv_ri = nullptr, *inv_rh = nullptr, *wav = nullptr, *traces = nullptr;
-  int *rec = nullptr, *step = nullptr, *status = nullptr;
-  int n_wav = 0;
-  KParams kp{};
-  RParams rp{};
-  // fused path: second buffer set, TMA descriptors and parameters per step parity
-  bool fused = false;
-  int tile_rt = 0;
-  void *f2[NF] = {};
-  float *psr2[NPR] = {};
-  float *psz2[NPZ] = {};
-  FusedMaps maps[2];
-  FusedParams fp[2];
-  RParams rp2[2];
-  int steps_done = 0;
-  size_t bytes = 0, mem_cap = 0, psr_elems = 0, psz_elems = 0;
-  std::vector<void *> allocs;
-  cudaGraphExec_t gexec = nullptr;
-  int gsteps = 0;
-  cudaEvent_t ev[4] = {};
-  double kms[3] = {0, 0, 0};
-  long kcount[3] = {0, 0, 0};
-  std::string err;
-};
-
-static thread_local std::string g_create_err;
-
-static int fail(sim_t *h, int code, const std::string &msg) {
-  if (h) h->err = msg;
-  else g_create_err = msg;
-  return code;
-}
-
-static int cuda_fail(sim_t *h, cudaError_t e, const char *what) {
-  return fail(h, SIM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
-
-#define CK(h, call)                                  \
-  do {                                               \
-    cudaError_t e_ = (call);                         \
-    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
-  } while (0)
+thread_local std::string cwell::g_create_err;
 
 static int dev_alloc(sim_t *h, void **p, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -115,8 +54,8 @@ static void cpml(double d, double al, double dt, float *a, float *b) {
   *a = (float)(d * (bb - 1.0) / (d + al));
 }
 
-static int validate(const sim_grid_t *g, const sim_medium_t *m, const sim_source_t *s, const sim_receivers_t *r,
-                    const sim_opts_t *o) {
+int cwell::validate_inputs(const sim_grid_t *g, const sim_medium_t *m, const sim_source_t *s,
+                           const sim_receivers_t *r, const sim_opts_t *o) {
   if (!g || !m || !s || !r || !o) return fail(nullptr, SIM_EINVAL, "null argument");
   if (g->nr < 2 || g->nth < 4 || (g->nth & 1) || g->nz < 2 || g->pml_r < 0 || g->pml_z < 0)
     return fail(nullptr, SIM_EINVAL, "grid: need nr >= 2, nth >= 4 and even, nz >= 2, pml >= 0");
@@ -210,10 +149,13 @@ static int build_maps(sim_t *h, int rt) {
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int, int, int, int>, int> g_tune;
 
-static int autotune(sim_t *h, int *best_rt) {
+// Candidates: the fused kernel with each tile height that fits in shared
+// memory and, when allowed, the split kernels (returned as tile height 0).
+static int autotune(sim_t *h, bool allow_split, int *best_rt) {
   int dev = h->device, maxsm = 0;
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  auto key = std::make_tuple(dev, h->grid.nth, h->NR, h->NZ, h->storage, h->kp.pml_r > 0 ? 1 : 0);
+  auto key = std::make_tuple(dev, h->grid.nth, h->NR, h->NZ, h->storage * 2 + (allow_split ? 1 : 0),
+                             h->kp.pml_r > 0 ? 1 : 0);
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tune.find(key);
@@ -222,23 +164,33 @@ static int autotune(sim_t *h, int *best_rt) {
       return SIM_OK;
     }
   }
-  const int cand[4] = {2, 4, 6, 8};
+  const int cand[5] = {2, 4, 6, 8, 0};
   cudaEvent_t a, b;
   CK(h, cudaEventCreate(&a));
   CK(h, cudaEventCreate(&b));
   float best = INFINITY;
-  int pick = 0;
+  int pick = -1;
   for (int rt : cand) {
-    if (fused_smem_bytes(h->storage, rt) > (size_t)maxsm) continue;
-    int rc = build_maps(h, rt);
-    if (rc) return rc;
-    FusedParams dry = h->fp[0];
-    dry.k.src_i = -1;  // no source: zero state stays zero
     cudaError_t e = cudaSuccess;
-    for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_fused(h->storage, rt, h->maps[0], dry, h->stream);
-    cudaEventRecord(a, h->stream);
-    for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_fused(h->storage, rt, h->maps[0], dry, h->stream);
-    cudaEventRecord(b, h->stream);
+    if (rt == 0) {
+      if (!allow_split) continue;
+      KParams dry = h->kp;
+      dry.src_i = -1;  // no source: zero state stays zero
+      for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_split(h->storage, dry, h->stream, nullptr);
+      cudaEventRecord(a, h->stream);
+      for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_split(h->storage, dry, h->stream, nullptr);
+      cudaEventRecord(b, h->stream);
+    } else {
+      if (fused_smem_bytes(h->storage, rt) > (size_t)maxsm) continue;
+      int rc = build_maps(h, rt);
+      if (rc) return rc;
+      FusedParams dry = h->fp[0];
+      dry.k.src_i = -1;
+      for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_fused(h->storage, rt, h->maps[0], dry, h->stream);
+      cudaEventRecord(a, h->stream);
+      for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_fused(h->storage, rt, h->maps[0], dry, h->stream);
+      cudaEventRecord(b, h->stream);
+    }
     if (e == cudaSuccess) e = cudaEventSynchronize(b);
     if (e != cudaSuccess) {
       cudaEventDestroy(a);
@@ -254,7 +206,7 @@ static int autotune(sim_t *h, int *best_rt) {
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  if (!pick) return fail(h, SIM_EUNSUPPORTED, "no fused tile fits in shared memory");
+  if (pick < 0) return fail(h, SIM_EUNSUPPORTED, "no fused tile fits in shared memory");
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_tune[key] = pick;
@@ -267,7 +219,7 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
                           const sim_receivers_t *receivers, const sim_opts_t *opts, sim_t **out) {
   if (!out) return fail(nullptr, SIM_EINVAL, "out is null");
   *out = nullptr;
-  int rc = validate(grid, medium, source, receivers, opts);
+  int rc = validate_inputs(grid, medium, source, receivers, opts);
   if (rc) return rc;
   const sim_grid_t &g = *grid;
   const int NR = g.nr + g.pml_r, NZ = g.nz + 2 * g.pml_z, nth = g.nth;
@@ -289,8 +241,10 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   h->NZp = NZp;
   h->storage = opts->storage;
   h->elem = opts->storage == 0 ? 4 : 2;
+  // AUTO prepares the fused path and lets the autotuner fall back to the split kernels
   h->kernel = opts->kernel == SIM_KERNEL_SPLIT ? SIM_KERNEL_SPLIT : SIM_KERNEL_FUSED;
   h->fused = h->kernel == SIM_KERNEL_FUSED;
+  const bool allow_split = opts->kernel == SIM_KERNEL_AUTO;
   h->graph_chunk = opts->graph_chunk == 0 ? 64 : opts->graph_chunk;
   h->timing = opts->timing;
   h->mem_cap = opts->mem_cap;
@@ -542,8 +496,13 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
       h->rp2[par].spp = nxt[F_SPP];
       h->rp2[par].szz = nxt[F_SZZ];
     }
-    if ((rc = autotune(h, &h->tile_rt))) return bail(rc);
-    if ((rc = build_maps(h, h->tile_rt))) return bail(rc);
+    if ((rc = autotune(h, allow_split, &h->tile_rt))) return bail(rc);
+    if (h->tile_rt == 0) {  // the split kernels won: run in place on the first buffer set
+      h->fused = false;
+      h->kernel = SIM_KERNEL_SPLIT;
+    } else if ((rc = build_maps(h, h->tile_rt))) {
+      return bail(rc);
+    }
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "autotune"));
   }

@@ -1,0 +1,85 @@
+// Internal state of a simulator handle, shared by the single-well and batch
+// host code.
+#pragma once
+
+#include <cudaTypedefs.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cwell.h"
+#include "cwell_internal.cuh"
+
+// the handle type is declared at global scope by cwell.h
+using namespace cwell;
+
+struct sim_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  sim_grid_t grid{};
+  int NR = 0, NZ = 0, NZp = 0;
+  double dt = 0, vscale = 1, sscale = 1;
+  int storage = 0, kernel = SIM_KERNEL_SPLIT, graph_chunk = 64, timing = 0;
+  int n_mat = 0, n_rec = 0, cap = 0;
+  size_t elem = 4;
+  void *f[NF] = {};
+  float *psr[NPR] = {};
+  float *psz[NPZ] = {};
+  uint16_t *id = nullptr;
+  float4 *mat = nullptr, *ab_r = nullptr, *ab_q = nullptr, *ab_z = nullptr;
+  float *m_rho = nullptr, *m_imu = nullptr;
+  float2 *m_lam = nullptr;
+  float *inv_ri = nullptr, *inv_rh = nullptr, *wav = nullptr, *traces = nullptr;
+  int *rec = nullptr, *step = nullptr, *status = nullptr;
+  int n_wav = 0;
+  KParams kp{};
+  RParams rp{};
+  // fused path: second buffer set, TMA descriptors and parameters per step parity
+  bool fused = false;
+  int tile_rt = 0;
+  void *f2[NF] = {};
+  float *psr2[NPR] = {};
+  float *psz2[NPZ] = {};
+  FusedMaps maps[2];
+  FusedParams fp[2];
+  RParams rp2[2];
+  int steps_done = 0;
+  size_t bytes = 0, mem_cap = 0, psr_elems = 0, psz_elems = 0;
+  std::vector<void *> allocs;
+  cudaGraphExec_t gexec = nullptr;
+  int gsteps = 0;
+  cudaEvent_t ev[4] = {};
+  double kms[3] = {0, 0, 0};
+  long kcount[3] = {0, 0, 0};
+  std::string err;
+};
+
+namespace cwell {
+extern thread_local std::string g_create_err;
+
+inline int fail(sim_t *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+inline int cuda_fail(sim_t *h, cudaError_t e, const char *what) {
+  return fail(h, SIM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                  \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+
+// host-only argument checks of sim_create (no device call); message in g_create_err
+int validate_inputs(const sim_grid_t *g, const sim_medium_t *m, const sim_source_t *s, const sim_receivers_t *r,
+                    const sim_opts_t *o);
+
+// steps enqueued on the handle (the batch advances its cases directly)
+inline void sim_advance(sim_t *h, int n) { h->steps_done += n; }
+
+}  // namespace cwell

@@ -28,12 +28,9 @@ constexpr int SB_X = 32;  // z-quads per block
 constexpr int SB_Y = 4;   // r rows per block
 constexpr int SB_MINB = 6;  // resident blocks per SM asked of the register allocator
 
+// velocity half-step of the four z cells k0 .. k0+3 of row (j, i)
 template <typename T>
-__global__ void __launch_bounds__(SB_X *SB_Y, SB_MINB) vel_split(const KParams p) {
-  const int j = blockIdx.x;
-  const int i = blockIdx.y * SB_Y + threadIdx.y;
-  const int k0 = (blockIdx.z * SB_X + threadIdx.x) * 4;
-  if (i >= p.NR || k0 >= p.NZ) return;
+__device__ __forceinline__ void vel_body(const KParams &p, const int j, const int i, const int k0) {
   const int nth = p.nth, NR = p.NR, NZ = p.NZ;
   const long long NZp = p.NZp, pl = p.plane;
   const int jm = j == 0 ? nth - 1 : j - 1, jp = j == nth - 1 ? 0 : j + 1;
@@ -166,12 +163,9 @@ __global__ void __launch_bounds__(SB_X *SB_Y, SB_MINB) vel_split(const KParams p
   }
 }
 
+// stress step of the four z cells k0 .. k0+3 of row (j, i)
 template <typename T>
-__global__ void __launch_bounds__(SB_X *SB_Y, SB_MINB) str_split(const KParams p) {
-  const int j = blockIdx.x;
-  const int i = blockIdx.y * SB_Y + threadIdx.y;
-  const int k0 = (blockIdx.z * SB_X + threadIdx.x) * 4;
-  if (i >= p.NR || k0 >= p.NZ) return;
+__device__ __forceinline__ void str_body(const KParams &p, const int j, const int i, const int k0) {
   const int nth = p.nth, NR = p.NR, NZ = p.NZ;
   const long long NZp = p.NZp, pl = p.plane;
   const int jm = j == 0 ? nth - 1 : j - 1, jp = j == nth - 1 ? 0 : j + 1;
@@ -344,12 +338,63 @@ __global__ void __launch_bounds__(SB_X *SB_Y, SB_MINB) str_split(const KParams p
     St<T>::st4(spz + c, make_float4(o[0], o[1], o[2], o[3]));
   }
   (void)cjm;
+  (void)nth;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SB_X *SB_Y, SB_MINB) vel_split(const KParams p) {
+  const int i = blockIdx.y * SB_Y + threadIdx.y, k0 = (blockIdx.z * SB_X + threadIdx.x) * 4;
+  if (i < p.NR && k0 < p.NZ) vel_body<T>(p, blockIdx.x, i, k0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SB_X *SB_Y, SB_MINB) str_split(const KParams p) {
+  const int i = blockIdx.y * SB_Y + threadIdx.y, k0 = (blockIdx.z * SB_X + threadIdx.x) * 4;
+  if (i < p.NR && k0 < p.NZ) str_body<T>(p, blockIdx.x, i, k0);
+}
+
+// Batched scenarios: persistent blocks walk the work list of all cases,
+// item = (case, theta, r tile, z tile), theta fastest inside a case so the
+// theta neighbours a block reads are read by co-resident blocks too.
+// start[c] = first item of case c (start[n] = total); cases[c] holds the
+// case's geometry and buffers.
+__device__ __forceinline__ int find_case(const long long *start, int n, long long item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, bool VEL>
+__global__ void __launch_bounds__(SB_X *SB_Y, SB_MINB) batch_split(const KParams *cases, const long long *start,
+                                                                   int n_cases, long long total) {
+  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    const int c = find_case(start, n_cases, item);
+    const KParams &p = cases[c];
+    long long q = item - __ldg(start + c);
+    const int nth = p.nth, nrt = (p.NR + SB_Y - 1) / SB_Y;
+    const int j = (int)(q % nth);
+    q /= nth;
+    const int rt = (int)(q % nrt), zt = (int)(q / nrt);
+    const int i = rt * SB_Y + threadIdx.y, k0 = (zt * SB_X + threadIdx.x) * 4;
+    if (i < p.NR && k0 < p.NZ) {
+      if (VEL) vel_body<T>(p, j, i, k0);
+      else str_body<T>(p, j, i, k0);
+    }
+  }
+}
+
+long long split_items(int nth, int NR, int NZ) {
+  return (long long)nth * ((NR + SB_Y - 1) / SB_Y) * ((NZ + 4 * SB_X - 1) / (4 * SB_X));
 }
 
 // Pressure at the receivers after the stress update; one block, fixed
 // summation order over theta; advances the device step counter.
 template <typename T>
-__global__ void __launch_bounds__(256) receivers_kernel(const RParams p) {
+__device__ __forceinline__ void receivers_body(const RParams &p) {
   const int n = *p.step;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const T *srr = (const T *)p.srr, *spp = (const T *)p.spp, *szz = (const T *)p.szz;
@@ -374,6 +419,17 @@ __global__ void __launch_bounds__(256) receivers_kernel(const RParams p) {
 }
 
 template <typename T>
+__global__ void __launch_bounds__(256) receivers_kernel(const RParams p) {
+  receivers_body<T>(p);
+}
+
+// one block per case
+template <typename T>
+__global__ void __launch_bounds__(256) receivers_batch(const RParams *rp) {
+  receivers_body<T>(rp[blockIdx.x]);
+}
+
+template <typename T>
 static cudaError_t launch_split_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev) {
   dim3 blk(SB_X, SB_Y);
   dim3 grd(p.nth, (p.NR + SB_Y - 1) / SB_Y, (p.NZ + 4 * SB_X - 1) / (4 * SB_X));
@@ -392,6 +448,31 @@ cudaError_t launch_split(int storage, const KParams &p, cudaStream_t s, cudaEven
     case 2: return launch_split_t<__half>(p, s, ev);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, const long long *start, int n_cases,
+                               long long total, int grid, cudaStream_t s) {
+  dim3 blk(SB_X, SB_Y);
+  switch (storage * 2 + (vel ? 1 : 0)) {
+    case 0: batch_split<float, false><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
+    case 1: batch_split<float, true><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
+    case 2: batch_split<__nv_bfloat16, false><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
+    case 3: batch_split<__nv_bfloat16, true><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
+    case 4: batch_split<__half, false><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
+    case 5: batch_split<__half, true><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_receivers(int storage, const RParams *rp, int n_cases, cudaStream_t s) {
+  switch (storage) {
+    case 0: receivers_batch<float><<<n_cases, 256, 0, s>>>(rp); break;
+    case 1: receivers_batch<__nv_bfloat16><<<n_cases, 256, 0, s>>>(rp); break;
+    case 2: receivers_batch<__half><<<n_cases, 256, 0, s>>>(rp); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_receivers(int storage, const RParams &p, cudaStream_t s) {

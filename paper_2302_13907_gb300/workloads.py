@@ -325,27 +325,23 @@ def cased_well(grid: Grid, *, z_top: float, ramp: float = 0.0, top_frac: float =
                 rock_i0 = i
             id2[i, :] = reg.id(rock)
             continue
-        # annulus material per depth (fluid above the top, graded cement below)
-        outer_ids = {}
-        for k in range(NZ):
-            if in_cement_zone[k]:
-                key = ("c", float(level[k]))
-                mat_out = graded_cement(cement, float(level[k]), top_frac)
-            else:
-                key = ("f",)
-                mat_out = fluid
-            if ra < casing_out < rb:  # straddling cell: volume fraction by int r dr
-                fr = (casing_out ** 2 - ra ** 2) / (rb ** 2 - ra ** 2)
+        # annulus material per depth (fluid above the top, graded cement below):
+        # one ID per distinct (zone, level), assigned to all depths sharing it
+        zone_key = np.where(in_cement_zone, level, -1.0)
+        keys, inv = np.unique(zone_key, return_inverse=True)
+        straddle = ra < casing_out < rb
+        fr = (casing_out ** 2 - ra ** 2) / (rb ** 2 - ra ** 2) if straddle else 0.0
+        lut = np.empty(len(keys), dtype=np.uint16)
+        for q, key in enumerate(keys):
+            mat_out = fluid if key < 0 else graded_cement(cement, float(key), top_frac)
+            if straddle:  # cell cut by the casing's outer radius: volume fraction by int r dr
                 mat = straddle_material(steel, mat_out, fr)
             elif r < casing_out:
                 mat = steel
             else:
                 mat = mat_out
-            cached = outer_ids.get(key)
-            if cached is None:
-                cached = reg.id(mat)
-                outer_ids[key] = cached
-            id2[i, k] = cached
+            lut[q] = reg.id(mat)
+        id2[i, :] = lut[inv]
     cell_id = np.broadcast_to(id2, (nth, NR, NZ)).copy()
     if noise is not None and rock_i0 is not None:
         d = rock_noise(grid, rock_i0, noise)
