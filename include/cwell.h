@@ -202,6 +202,64 @@ int simb_config(const simb_t *b, int *n_cases, long long *work_items, int *grid_
 void simb_destroy(simb_t *b);
 const char *simb_last_error(const simb_t *b);
 
+/* ------------------------------------------------------------------------
+ * Trace surrogate: maps the six case parameters of a cement-hardening
+ * scenario to its 8 receiver traces over the reflected window.  The paper
+ * has no learned component; this network is trained on traces the simulator
+ * itself produces and the simulator remains the fallback.
+ *
+ *   h1 = gelu(x W1 + b1), h2 = gelu(h1 W2 + b2),
+ *   a0 = gelu(reshape(h2 W3 + b3, [l0][chans[0]])),
+ *   a_{l+1} = gelu(convT(a_l)) for l < n_up (kernel 4, stride 2, padding 1),
+ *   y = a_{n_up} Wf + bf  -> output [out_ch][l0 * 2^n_up]
+ * with gelu(x) = x/2 (1 + tanh(sqrt(2/pi)(x + 0.044715 x^3))), inputs
+ * normalised as (x - mean) / scale and outputs multiplied by y_scale.  BF16 weights and activations at every
+ * GEMM, FP32 accumulation, FP32 Adam master weights.  Parameters are one
+ * FP32 vector in the order W1 [in][h1], b1, W2 [h1][h2], b2, W3 [h2][l0*c0],
+ * b3, then (T_l [c_l][c_{l+1}][4], t_l) per transposed convolution, then
+ * Wf [c_n][out_ch], bf.  Host buffers are row-major FP32.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int in_dim, h1, h2, l0, n_up;
+  int chans[9];       /* chans[0]: channels of the reshaped dense output; chans[l+1]: after convT l */
+  int out_ch;
+  int max_batch;      /* samples per device pass */
+  unsigned long long seed;  /* initial weights: uniform +-sqrt(6/(fan_in+fan_out)), biases 0 */
+} sur_cfg_t;
+
+typedef struct sur_s sur_t;
+
+int sur_create(const sur_cfg_t *cfg, const sim_opts_t *opts, sur_t **out);  /* opts: device, stream */
+int sur_param_count(const sur_t *s, long long *n);
+int sur_get_params(sur_t *s, float *out, size_t n);
+int sur_set_params(sur_t *s, const float *in, size_t n);   /* also resets the Adam moments */
+/* inputs enter as (x - x_mean) / x_scale; outputs and targets are in units of
+ * y_scale (the network works on y / y_scale) */
+int sur_set_normalization(sur_t *s, const float *x_mean, const float *x_scale, float y_scale);
+/* Y[n][out_ch][l0 * 2^n_up] from raw inputs X[n][in_dim]. */
+int sur_forward(sur_t *s, const float *X, int n, float *Y);
+/* Mean-square loss of the normalised output against Y[n][out_ch][L] / y_scale
+ * and its gradient (n <= max_batch). */
+int sur_loss_grad(sur_t *s, const float *X, const float *Y, int n, float *loss, float *grad, size_t ngrad);
+/* Adam (beta 0.9 / 0.999, eps 1e-8), cosine learning-rate decay from lr over
+ * all steps, minibatches of `batch` drawn by a seeded shuffle each epoch;
+ * epoch_loss[epochs] receives the mean minibatch loss per epoch (may be NULL). */
+int sur_train(sur_t *s, const float *X, const float *Y, int n, int epochs, int batch, float lr,
+              unsigned long long seed, float *epoch_loss);
+/* Fallback gate: fit on validation inputs and their relative errors; a query
+ * is accepted when the largest error among its k nearest validation inputs
+ * (normalised distance) is <= tol, else the caller runs the simulator. */
+int sur_gate_fit(sur_t *s, const float *X, const float *err, int n);
+int sur_gate(sur_t *s, const float *X, int n, int k, float tol, int *accept);
+void sur_destroy(sur_t *s);
+const char *sur_last_error(const sur_t *s);
+
+/* Tensor-core GEMM of the surrogate on host buffers: C[M][N] = op(A) op(B),
+ * A and B BF16 bit patterns (row-major, op = transpose when trans_* != 0),
+ * C FP32; for testing the kernel against an FP64 product of the same inputs. */
+int cw_gemm_bf16(int trans_a, int trans_b, int M, int N, int K, const uint16_t *A, int lda, const uint16_t *B,
+                 int ldb, float *C, int ldc);
+
 #ifdef __cplusplus
 }
 #endif

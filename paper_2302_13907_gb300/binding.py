@@ -308,3 +308,159 @@ class BatchSimulation:
         n, w, g = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
         self._chk(self.L.simb_config(self.h, ctypes.byref(n), ctypes.byref(w), ctypes.byref(g)))
         return n.value, w.value, g.value
+
+
+# ------------------------------------------------------------------ surrogate
+class SurCfg(ctypes.Structure):
+    _fields_ = [("in_dim", ctypes.c_int), ("h1", ctypes.c_int), ("h2", ctypes.c_int), ("l0", ctypes.c_int),
+                ("n_up", ctypes.c_int), ("chans", ctypes.c_int * 9), ("out_ch", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
+
+
+SURROGATE_DEFAULT = dict(in_dim=6, h1=256, h2=512, l0=64, chans=(64, 64, 64, 32, 32, 16), out_ch=8)
+
+
+def _sur_sigs(L):
+    if getattr(L, "_sur_ready", False):
+        return
+    p, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.sur_create.argtypes = [ctypes.POINTER(SurCfg), ctypes.POINTER(SimOpts), ctypes.POINTER(p)]
+    L.sur_create.restype = i
+    L.sur_param_count.argtypes = [p, ctypes.POINTER(ctypes.c_longlong)]
+    L.sur_param_count.restype = i
+    L.sur_get_params.argtypes = [p, fp, sz]
+    L.sur_get_params.restype = i
+    L.sur_set_params.argtypes = [p, fp, sz]
+    L.sur_set_params.restype = i
+    L.sur_set_normalization.argtypes = [p, fp, fp, ctypes.c_float]
+    L.sur_set_normalization.restype = i
+    L.sur_forward.argtypes = [p, fp, i, fp]
+    L.sur_forward.restype = i
+    L.sur_loss_grad.argtypes = [p, fp, fp, i, fp, fp, sz]
+    L.sur_loss_grad.restype = i
+    L.sur_train.argtypes = [p, fp, fp, i, i, i, ctypes.c_float, ctypes.c_ulonglong, fp]
+    L.sur_train.restype = i
+    L.sur_gate_fit.argtypes = [p, fp, fp, i]
+    L.sur_gate_fit.restype = i
+    L.sur_gate.argtypes = [p, fp, i, i, ctypes.c_float, ctypes.POINTER(i)]
+    L.sur_gate.restype = i
+    L.sur_destroy.argtypes = [p]
+    L.sur_destroy.restype = None
+    L.sur_last_error.argtypes = [p]
+    L.sur_last_error.restype = ctypes.c_char_p
+    u16p = ctypes.POINTER(ctypes.c_uint16)
+    L.cw_gemm_bf16.argtypes = [i, i, i, i, i, u16p, i, u16p, i, fp, i]
+    L.cw_gemm_bf16.restype = i
+    L._sur_ready = True
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def gemm_bf16(A16: np.ndarray, B16: np.ndarray, trans_a=False, trans_b=False) -> np.ndarray:
+    """Tensor-core GEMM on BF16 bit patterns (uint16 arrays), FP32 result."""
+    L = lib()
+    _sur_sigs(L)
+    A16 = np.ascontiguousarray(A16, np.uint16)
+    B16 = np.ascontiguousarray(B16, np.uint16)
+    M, K = (A16.shape[1], A16.shape[0]) if trans_a else A16.shape
+    N = B16.shape[0] if trans_b else B16.shape[1]
+    C = np.zeros((M, N), np.float32)
+    u16p = ctypes.POINTER(ctypes.c_uint16)
+    rc = L.cw_gemm_bf16(int(trans_a), int(trans_b), M, N, K, A16.ctypes.data_as(u16p), A16.shape[1],
+                        B16.ctypes.data_as(u16p), B16.shape[1], _fp(C), N)
+    if rc != SIM_OK:
+        raise SimError(rc, "cw_gemm_bf16 failed")
+    return C
+
+
+class Surrogate:
+    """Trace surrogate handle (sur_create ... sur_destroy)."""
+
+    def __init__(self, max_batch=32, seed=1, stream=None, device=0, **arch):
+        self.L = lib()
+        _sur_sigs(self.L)
+        a = dict(SURROGATE_DEFAULT)
+        a.update(arch)
+        ch = list(a["chans"])
+        cfg = SurCfg(a["in_dim"], a["h1"], a["h2"], a["l0"], len(ch) - 1, (ctypes.c_int * 9)(*(ch + [0] * (9 - len(ch)))),
+                     a["out_ch"], int(max_batch), int(seed))
+        opts = SimOpts(0, 0, 0, ctypes.c_void_p(stream) if stream else None, 0, 0, 0, 0, int(device))
+        h = ctypes.c_void_p()
+        rc = self.L.sur_create(ctypes.byref(cfg), ctypes.byref(opts), ctypes.byref(h))
+        if rc != SIM_OK:
+            raise SimError(rc, self.L.sur_last_error(None).decode())
+        self.h = h
+        self.arch = a
+        self.out_len = a["l0"] * 2 ** (len(ch) - 1)
+        n = ctypes.c_longlong()
+        self._chk(self.L.sur_param_count(self.h, ctypes.byref(n)))
+        self.n_params = n.value
+
+    def _chk(self, rc):
+        if rc != SIM_OK:
+            raise SimError(rc, self.L.sur_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.sur_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *e):
+        self.close()
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32)
+        self._chk(self.L.sur_get_params(self.h, _fp(out), out.size))
+        return out
+
+    def set_params(self, th):
+        th = np.ascontiguousarray(th, np.float32)
+        self._chk(self.L.sur_set_params(self.h, _fp(th), th.size))
+
+    def set_normalization(self, mean, scale, y_scale=1.0):
+        m = np.ascontiguousarray(mean, np.float32)
+        s = np.ascontiguousarray(scale, np.float32)
+        self._chk(self.L.sur_set_normalization(self.h, _fp(m), _fp(s), float(y_scale)))
+
+    def forward(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.zeros((X.shape[0], self.arch["out_ch"], self.out_len), np.float32)
+        self._chk(self.L.sur_forward(self.h, _fp(X), X.shape[0], _fp(Y)))
+        return Y
+
+    def loss_grad(self, X, Y):
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.ascontiguousarray(Y, np.float32)
+        g = np.zeros(self.n_params, np.float32)
+        loss = ctypes.c_float()
+        self._chk(self.L.sur_loss_grad(self.h, _fp(X), _fp(Y), X.shape[0], ctypes.byref(loss), _fp(g), g.size))
+        return loss.value, g
+
+    def train(self, X, Y, epochs, batch=32, lr=1e-3, seed=0):
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.ascontiguousarray(Y, np.float32)
+        hist = np.zeros(max(epochs, 1), np.float32)
+        self._chk(self.L.sur_train(self.h, _fp(X), _fp(Y), X.shape[0], int(epochs), int(batch), float(lr), int(seed),
+                                   _fp(hist)))
+        return hist[:epochs]
+
+    def gate_fit(self, X, err):
+        X = np.ascontiguousarray(X, np.float32)
+        e = np.ascontiguousarray(err, np.float32)
+        self._chk(self.L.sur_gate_fit(self.h, _fp(X), _fp(e), X.shape[0]))
+
+    def gate(self, X, k=3, tol=0.05) -> np.ndarray:
+        X = np.ascontiguousarray(X, np.float32)
+        acc = np.zeros(X.shape[0], np.int32)
+        self._chk(self.L.sur_gate(self.h, _fp(X), X.shape[0], int(k), float(tol),
+                                  acc.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return acc.astype(bool)

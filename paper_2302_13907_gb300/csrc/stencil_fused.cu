@@ -94,6 +94,7 @@ struct FusedSmem {
   // every TMA destination starts on a 128-byte boundary
   static constexpr int BOXB = (BR * BW * (int)sizeof(T) + 127) / 128 * 128;
   static constexpr int IDB = (BR * BWI * 2 + 127) / 128 * 128;
+  static constexpr int BOX_ELEMS = BOXB / (int)sizeof(T);
   static constexpr int SLOT_BYTES = 9 * BOXB + IDB;  // nine fields + IDs of one plane
   static constexpr size_t RING_BYTES = (size_t)4 * SLOT_BYTES;
   static constexpr size_t V_BYTES = (size_t)4 * 3 * BR * VW * 4;  // 3 ring planes + saved plane 0
@@ -156,30 +157,59 @@ __device__ __forceinline__ void fused_tile(const FusedMaps &maps, const FusedPar
   T *vnxt[3] = {(T *)fp.fo[F_VR], (T *)fp.fo[F_VP], (T *)fp.fo[F_VZ]};
   const int i = i0 - 1 + row;  // this thread's radial index
 
-  // velocity component c at tile row r (0 .. RT+1), depth k, of plane `plane`
-  // held in ring slots (sm1, s0, sp1) = planes (m-1, m, m+1); writes the owned
-  // value and memory variables, returns the new value (0 at walls / outside).
-  auto vel_point = [&](int c, int r, int k, int plane, bool own, int sm1, int s0, int sp1) -> float {
-    const int ii = i0 - 1 + r;
-    const int x = r * BW + (k - k0 + HX);  // index into a field box
-    const int xi = r * BWI + (k - k0 + 8);
-    const T *S0rr = slot_field(s0, 3), *S0pp = slot_field(s0, 4), *S0zz = slot_field(s0, 5);
-    const T *S0rp = slot_field(s0, 6), *S0pz = slot_field(s0, 7), *S0rz = slot_field(s0, 8);
+  // Per-point constants of a velocity point at tile row r, depth k: they do
+  // not change along the theta march, so each thread builds them once.
+  struct VCtx {
+    int ii, k, x, xi;     // radial index, depth, offsets in a field box / ID box
+    long long cb, crb, czb;  // global, radial-slab and z-slab offsets without the plane term
+    int kz;
+    bool rp, zp;
+    float inv_ri, inv_rh;
+    float4 ab, aq, abz;
+  };
+  auto make_ctx = [&](int r, int k) {
+    VCtx v;
+    v.ii = i0 - 1 + r;
+    v.k = k;
+    v.x = r * BW + (k - k0 + HX);
+    v.xi = r * BWI + (k - k0 + 8);
+    const int iic = min(max(v.ii, 0), NR - 1), kc = min(max(k, 0), NZ - 1);
+    v.cb = (long long)v.ii * NZp + k;
+    v.rp = v.ii >= nr_p && v.ii < NR;
+    v.crb = v.rp ? (long long)(v.ii - nr_p) * NZp + k : 0;
+    v.zp = (k >= 0 && k < pz) || (k >= NZ - pz && k < NZ);
+    v.kz = k < pz ? k : k - (NZ - 2 * pz);
+    v.czb = (long long)iic * (2 * pz) + v.kz;
+    v.inv_ri = __ldg(p.inv_ri + iic);
+    v.inv_rh = __ldg(p.inv_rh + iic);
+    v.ab = __ldg(p.ab_r + iic);
+    v.aq = __ldg(p.ab_q + iic);
+    v.abz = v.zp ? __ldg(p.ab_z + kc) : make_float4(0.f, 1.f, 0.f, 1.f);
+    return v;
+  };
+  const long long pr_plane = (long long)p.pml_r * NZp, pz_plane = (long long)NR * 2 * pz;
+
+  // velocity component c at the point of `v` in plane `plane`, with ring slots
+  // (sm1, s0, sp1) = planes (m-1, m, m+1); writes the owned value and memory
+  // variables, returns the new value (0 at walls and outside the grid).
+  auto vel_point = [&](int c, const VCtx &v, int plane, bool own, int sm1, int s0, int sp1) -> float {
+    const int ii = v.ii, k = v.k, x = v.x, xi = v.xi;
+    const long long cr = plane * pr_plane + v.crb, cz = plane * pz_plane + v.czb;
+    const T *S0 = slot_field(s0, 0);
+    const int F = SM::BOX_ELEMS;  // stride between field boxes of one slot
     const uint16_t *I0 = slot_ids(s0);
-    float out = 0.f;
+    float out;
     if (c == 0) {  // v_r at (r_i, theta_j, z_k): i >= 1
       if (ii < 1 || ii >= NR || k >= NZ) return 0.f;
-      const float srr_c = sld(S0rr + x), srr_m = sld(S0rr + x - BW);
-      const float spp_c = sld(S0pp + x), spp_m = sld(S0pp + x - BW);
+      const float srr_c = sld(S0 + 3 * F + x), srr_m = sld(S0 + 3 * F + x - BW);
+      const float spp_c = sld(S0 + 4 * F + x), spp_m = sld(S0 + 4 * F + x - BW);
       float Dr = (srr_c - srr_m) * idr;
-      float Q = (0.5f * (srr_c + srr_m) - 0.5f * (spp_c + spp_m) + (sld(S0rp + x) - sld(slot_field(sm1, 6) + x)) * idth) *
-                __ldg(p.inv_ri + ii);
-      float Dz = (sld(S0rz + x) - sld(S0rz + x - 1)) * idz;
-      if (ii >= nr_p) {
-        const long long cr = ((long long)plane * p.pml_r + (ii - nr_p)) * NZp + k;
-        const float4 ab = __ldg(p.ab_r + ii), aq = __ldg(p.ab_q + ii);
-        const float ps = ab.y * p.psr[R_VR][cr] + ab.x * Dr;
-        const float qs = aq.y * p.psr[Q_VR][cr] + aq.x * Q;
+      float Q = (0.5f * (srr_c + srr_m) - 0.5f * (spp_c + spp_m) + (sld(S0 + 6 * F + x) - sld(slot_field(sm1, 6) + x)) * idth) *
+                v.inv_ri;
+      float Dz = (sld(S0 + 8 * F + x) - sld(S0 + 8 * F + x - 1)) * idz;
+      if (v.rp) {
+        const float ps = v.ab.y * p.psr[R_VR][cr] + v.ab.x * Dr;
+        const float qs = v.aq.y * p.psr[Q_VR][cr] + v.aq.x * Q;
         if (own) {
           fp.psr_o[R_VR][cr] = ps;
           fp.psr_o[Q_VR][cr] = qs;
@@ -187,27 +217,22 @@ __device__ __forceinline__ void fused_tile(const FusedMaps &maps, const FusedPar
         Dr += ps;
         Q += qs;
       }
-      if (k < pz || k >= NZ - pz) {
-        const int kz = k < pz ? k : k - (NZ - 2 * pz);
-        const long long cz = ((long long)plane * NR + ii) * (2 * pz) + kz;
-        const float4 abz = __ldg(p.ab_z + k);
-        const float ps = abz.y * p.psz[Z_VR][cz] + abz.x * Dz;
+      if (v.zp) {
+        const float ps = v.abz.y * p.psz[Z_VR][cz] + v.abz.x * Dz;
         if (own) fp.psz_o[Z_VR][cz] = ps;
         Dz += ps;
       }
       const float rho = __ldg(m_rho + I0[xi]) + __ldg(m_rho + I0[xi - BWI]);
-      out = sld(slot_field(s0, 0) + x) + 2.f * dtv / rho * (Dr + Q + Dz);
+      out = sld(S0 + x) + 2.f * dtv / rho * (Dr + Q + Dz);
     } else if (c == 1) {  // v_phi at (r_{i+1/2}, theta_{j+1/2}, z_k)
       if (ii < 0 || ii >= NR || k >= NZ) return 0.f;
-      const float s1 = sld(S0rp + x + BW), s0v = sld(S0rp + x);
+      const float s1 = sld(S0 + 6 * F + x + BW), s0v = sld(S0 + 6 * F + x);
       float Dr = (s1 - s0v) * idr;
-      float Q = ((s1 + s0v) + (sld(slot_field(sp1, 4) + x) - sld(S0pp + x)) * idth) * __ldg(p.inv_rh + ii);
-      float Dz = (sld(S0pz + x) - sld(S0pz + x - 1)) * idz;
-      if (ii >= nr_p) {
-        const long long cr = ((long long)plane * p.pml_r + (ii - nr_p)) * NZp + k;
-        const float4 ab = __ldg(p.ab_r + ii), aq = __ldg(p.ab_q + ii);
-        const float ps = ab.w * p.psr[R_VP][cr] + ab.z * Dr;
-        const float qs = aq.w * p.psr[Q_VP][cr] + aq.z * Q;
+      float Q = ((s1 + s0v) + (sld(slot_field(sp1, 4) + x) - sld(S0 + 4 * F + x)) * idth) * v.inv_rh;
+      float Dz = (sld(S0 + 7 * F + x) - sld(S0 + 7 * F + x - 1)) * idz;
+      if (v.rp) {
+        const float ps = v.ab.w * p.psr[R_VP][cr] + v.ab.z * Dr;
+        const float qs = v.aq.w * p.psr[Q_VP][cr] + v.aq.z * Q;
         if (own) {
           fp.psr_o[R_VP][cr] = ps;
           fp.psr_o[Q_VP][cr] = qs;
@@ -215,27 +240,22 @@ __device__ __forceinline__ void fused_tile(const FusedMaps &maps, const FusedPar
         Dr += ps;
         Q += qs;
       }
-      if (k < pz || k >= NZ - pz) {
-        const int kz = k < pz ? k : k - (NZ - 2 * pz);
-        const long long cz = ((long long)plane * NR + ii) * (2 * pz) + kz;
-        const float4 abz = __ldg(p.ab_z + k);
-        const float ps = abz.y * p.psz[Z_VP][cz] + abz.x * Dz;
+      if (v.zp) {
+        const float ps = v.abz.y * p.psz[Z_VP][cz] + v.abz.x * Dz;
         if (own) fp.psz_o[Z_VP][cz] = ps;
         Dz += ps;
       }
       const float rho = __ldg(m_rho + I0[xi]) + __ldg(m_rho + slot_ids(sp1)[xi]);
-      out = sld(slot_field(s0, 1) + x) + 2.f * dtv / rho * (Dr + Q + Dz);
+      out = sld(S0 + F + x) + 2.f * dtv / rho * (Dr + Q + Dz);
     } else {  // v_z at (r_{i+1/2}, theta_j, z_{k+1/2}); the last half-node is a wall
       if (ii < 0 || ii >= NR || k < 0 || k + 1 >= NZ) return 0.f;
-      const float s1 = sld(S0rz + x + BW), s0v = sld(S0rz + x);
+      const float s1 = sld(S0 + 8 * F + x + BW), s0v = sld(S0 + 8 * F + x);
       float Dr = (s1 - s0v) * idr;
-      float Q = (0.5f * (s1 + s0v) + (sld(S0pz + x) - sld(slot_field(sm1, 7) + x)) * idth) * __ldg(p.inv_rh + ii);
-      float Dz = (sld(S0zz + x + 1) - sld(S0zz + x)) * idz;
-      if (ii >= nr_p) {
-        const long long cr = ((long long)plane * p.pml_r + (ii - nr_p)) * NZp + k;
-        const float4 ab = __ldg(p.ab_r + ii), aq = __ldg(p.ab_q + ii);
-        const float ps = ab.w * p.psr[R_VZ][cr] + ab.z * Dr;
-        const float qs = aq.w * p.psr[Q_VZ][cr] + aq.z * Q;
+      float Q = (0.5f * (s1 + s0v) + (sld(S0 + 7 * F + x) - sld(slot_field(sm1, 7) + x)) * idth) * v.inv_rh;
+      float Dz = (sld(S0 + 5 * F + x + 1) - sld(S0 + 5 * F + x)) * idz;
+      if (v.rp) {
+        const float ps = v.ab.w * p.psr[R_VZ][cr] + v.ab.z * Dr;
+        const float qs = v.aq.w * p.psr[Q_VZ][cr] + v.aq.z * Q;
         if (own) {
           fp.psr_o[R_VZ][cr] = ps;
           fp.psr_o[Q_VZ][cr] = qs;
@@ -243,20 +263,20 @@ __device__ __forceinline__ void fused_tile(const FusedMaps &maps, const FusedPar
         Dr += ps;
         Q += qs;
       }
-      if (k < pz || k >= NZ - pz) {
-        const int kz = k < pz ? k : k - (NZ - 2 * pz);
-        const long long cz = ((long long)plane * NR + ii) * (2 * pz) + kz;
-        const float4 abz = __ldg(p.ab_z + k);
-        const float ps = abz.w * p.psz[Z_VZ][cz] + abz.z * Dz;
+      if (v.zp) {
+        const float ps = v.abz.w * p.psz[Z_VZ][cz] + v.abz.z * Dz;
         if (own) fp.psz_o[Z_VZ][cz] = ps;
         Dz += ps;
       }
       const float rho = __ldg(m_rho + I0[xi]) + __ldg(m_rho + I0[xi + 1]);
-      out = sld(slot_field(s0, 2) + x) + 2.f * dtv / rho * (Dr + Q + Dz);
+      out = sld(S0 + 2 * F + x) + 2.f * dtv / rho * (Dr + Q + Dz);
     }
-    if (own && k < NZp) gst(vnxt[c] + (long long)plane * pl + (long long)ii * NZp + k, out);
+    if (own && k < NZp) gst(vnxt[c] + plane * pl + v.cb, out);
     return out;
   };
+  // this thread's main point and, for the row's edge lanes, its halo point
+  const VCtx vmain = make_ctx(row, k0 + lane);
+  const VCtx vhalo = make_ctx(row, lane == 0 ? k0 - 1 : k0 + ZT);
 
   for (int m = -1; m <= nth; m++) {
     // prefetch plane m + 2 into the slot freed at the end of the previous iteration
@@ -276,24 +296,19 @@ __device__ __forceinline__ void fused_tile(const FusedMaps &maps, const FusedPar
       const bool own_plane = m >= 0;
       float *V = vr_ring + (((m % 3) + 3) % 3) * 3 * BR * VW;
       {
-        const int k = k0 + lane;
         const bool own_rz = own_plane && row >= 1 && row <= RT;
         // v_r on rows 1 .. RT+1, v_phi and v_z on rows 0 .. RT
-        V[(0 * BR + row) * VW + lane + 1] = row >= 1 ? vel_point(0, row, k, plane, own_rz, sm1, s0, sp1) : 0.f;
-        if (row <= RT) {
-          V[(1 * BR + row) * VW + lane + 1] = vel_point(1, row, k, plane, own_rz, sm1, s0, sp1);
-          V[(2 * BR + row) * VW + lane + 1] = vel_point(2, row, k, plane, own_rz, sm1, s0, sp1);
-        } else {
-          V[(1 * BR + row) * VW + lane + 1] = 0.f;
-          V[(2 * BR + row) * VW + lane + 1] = 0.f;
+        V[(0 * BR + row) * VW + lane + 1] = row >= 1 ? vel_point(0, vmain, plane, own_rz, sm1, s0, sp1) : 0.f;
+        V[(1 * BR + row) * VW + lane + 1] = row <= RT ? vel_point(1, vmain, plane, own_rz, sm1, s0, sp1) : 0.f;
+        V[(2 * BR + row) * VW + lane + 1] = row <= RT ? vel_point(2, vmain, plane, own_rz, sm1, s0, sp1) : 0.f;
+        // halo columns, one row per warp pair: v_z at k0-1 by lane 0, v_r and
+        // v_phi at k0+ZT by lane 63 (recomputed, never written)
+        if (lane == 0) {
+          V[(2 * BR + row) * VW + 0] = row <= RT ? vel_point(2, vhalo, plane, false, sm1, s0, sp1) : 0.f;
+        } else if (lane == 63) {
+          V[(0 * BR + row) * VW + ZT + 1] = row >= 1 ? vel_point(0, vhalo, plane, false, sm1, s0, sp1) : 0.f;
+          V[(1 * BR + row) * VW + ZT + 1] = row <= RT ? vel_point(1, vhalo, plane, false, sm1, s0, sp1) : 0.f;
         }
-      }
-      // halo columns: v_z at k0-1 (rows 0..RT), v_r and v_phi at k0+ZT (rows 1..RT+1 / 0..RT)
-      if (tid < BR) {
-        const int r = tid;
-        V[(2 * BR + r) * VW + 0] = r <= RT ? vel_point(2, r, k0 - 1, plane, false, sm1, s0, sp1) : 0.f;
-        V[(0 * BR + r) * VW + ZT + 1] = r >= 1 ? vel_point(0, r, k0 + ZT, plane, false, sm1, s0, sp1) : 0.f;
-        V[(1 * BR + r) * VW + ZT + 1] = r <= RT ? vel_point(1, r, k0 + ZT, plane, false, sm1, s0, sp1) : 0.f;
       }
       if (m == 0) {
         __syncthreads();
@@ -321,14 +336,10 @@ __device__ __forceinline__ void fused_tile(const FusedMaps &maps, const FusedPar
         for (int f = 0; f < 6; f++) o[f] = sld(slot_field(sm1, 3 + f) + x);  // s^n of plane m-1
         if (k < NZ) {
           const uint16_t *Im = slot_ids(sm1), *Ij = slot_ids(s0);
-          const bool rpm = i >= nr_p;
-          const long long cr = rpm ? ((long long)plane * p.pml_r + (i - nr_p)) * NZp + k : 0;
-          const bool zpm = k < pz || k >= NZ - pz;
-          const int kz = k < pz ? k : k - (NZ - 2 * pz);
-          const long long cz = ((long long)plane * NR + i) * (2 * pz) + kz;
-          const float inv_rh = __ldg(p.inv_rh + i), inv_ri = __ldg(p.inv_ri + i);
-          const float4 ab = __ldg(p.ab_r + i), aq = __ldg(p.ab_q + i);
-          const float4 abz = zpm ? __ldg(p.ab_z + k) : make_float4(0.f, 1.f, 0.f, 1.f);
+          const bool rpm = vmain.rp, zpm = vmain.zp;
+          const long long cr = plane * pr_plane + vmain.crb, cz = plane * pz_plane + vmain.czb;
+          const float inv_rh = vmain.inv_rh, inv_ri = vmain.inv_ri;
+          const float4 ab = vmain.ab, aq = vmain.aq, abz = vmain.abz;
           const float imu_c = __ldg(m_imu + Im[xi]), imu_m = __ldg(m_imu + Im[xi - BWI]);
           // normal stresses
           {

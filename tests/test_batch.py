@@ -49,6 +49,7 @@ def test_batch_equals_single_runs_and_oracle():
         b.sync()
         got = [b.traces(c) for c in range(5)]
         got_f = [b.field(c, "srr") for c in range(5)]
+        got_vz = b.field(0, "vz")
     for c, sc in enumerate(cases):
         with Simulation(sc, kernel="split") as s:
             s.step(160)
@@ -56,9 +57,12 @@ def test_batch_equals_single_runs_and_oracle():
             assert got[c].shape == ref.shape
             assert rel_l2(got[c], ref) <= 1e-6, c
             assert rel_l2(got_f[c], s.field("srr")) <= 1e-6, c
+    # against the oracle element by element (the receivers of this small case
+    # may still see only the exponentially small tail ahead of the wavefront)
     o = oracle.Oracle(cases[0])
     o.step(160)
-    assert rel_l2(got[0], o.traces()) <= 1e-4
+    for a, ref in ((got_f[0], o.field("srr")), (got_vz, o.field("vz"))):
+        assert np.abs(a - ref).max() <= 2e-5 * np.abs(ref).max()
 
 
 @pytest.mark.gpu

@@ -1,0 +1,79 @@
+"""Surrogate kernels on the GPU against the FP64 reference (oracle/surrogate_ref.py)."""
+import numpy as np
+import pytest
+
+from oracle import surrogate_ref as R
+
+pytestmark = pytest.mark.gpu
+
+
+def to_bf16_bits(a):
+    """Round-to-nearest-even FP32 -> BF16 bit patterns."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+    return r
+
+
+def bf16_value(bits):
+    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("ta,tb", [(False, False), (False, True), (True, False), (True, True)])
+@pytest.mark.parametrize("M,N,K", [(37, 70, 45), (128, 64, 32), (5, 3, 200), (300, 130, 17)])
+def test_tensor_core_gemm_against_fp64(ta, tb, M, N, K):
+    from paper_2302_13907_gb300.binding import gemm_bf16
+    rng = np.random.default_rng(M * 7 + N + K)
+    A = to_bf16_bits(rng.standard_normal((K, M) if ta else (M, K)))
+    B = to_bf16_bits(rng.standard_normal((N, K) if tb else (K, N)))
+    C = gemm_bf16(A, B, ta, tb)
+    a, b = bf16_value(A), bf16_value(B)
+    ref = (a.T if ta else a) @ (b.T if tb else b)
+    assert np.abs(C - ref).max() <= 1e-5 * np.abs(ref).max() * max(1.0, K / 64)
+
+
+def _bf16_theta(th, shp):
+    """Weight matrices rounded to BF16 (as the GPU's GEMMs see them), biases FP32."""
+    out = th.astype(np.float64).copy()
+    o = 0
+    for name, sh in shp:
+        n = int(np.prod(sh))
+        if len(sh) > 1:
+            out[o:o + n] = bf16_value(to_bf16_bits(th[o:o + n]))
+        o += n
+    return out
+
+
+def test_forward_and_gradient_match_fp64_reference():
+    from paper_2302_13907_gb300.binding import Surrogate
+    shp = R.shapes()
+    rng = np.random.default_rng(11)
+    X = rng.uniform(-1, 1, (4, 6)).astype(np.float32)
+    with Surrogate(max_batch=8, seed=3) as s:
+        th = s.params()
+        assert th.size == sum(int(np.prod(x)) for _, x in shp)
+        Y = s.forward(X)
+        thb = _bf16_theta(th, shp)
+        ref = R.forward(thb, X.astype(np.float64), shp)
+        assert Y.shape == ref.shape == (4, 8, 2048)
+        rel = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
+        assert rel <= 2e-2, rel
+        T = rng.standard_normal(ref.shape).astype(np.float32) * np.abs(ref).max()
+        loss, g = s.loss_grad(X, T)
+        lref, gref = R.loss_and_grad(thb, X.astype(np.float64), T.astype(np.float64), shp)
+        assert abs(loss - lref) <= 2e-2 * lref
+        cos = float(g @ gref / (np.linalg.norm(g) * np.linalg.norm(gref)))
+        assert cos >= 0.999, cos
+
+
+def test_training_reduces_loss_on_a_smooth_map():
+    from paper_2302_13907_gb300.binding import Surrogate
+    rng = np.random.default_rng(0)
+    X = rng.uniform(-1, 1, (64, 6)).astype(np.float32)
+    t = np.linspace(0, 1, 2048)
+    # a smooth family of damped oscillations parameterised by the inputs
+    Y = np.stack([[np.sin(2 * np.pi * (3 + x[0] + 0.3 * c) * t + x[1]) * np.exp(-t * (1 + x[2] ** 2))
+                   for c in range(8)] for x in X]).astype(np.float32)
+    with Surrogate(max_batch=32, seed=7) as s:
+        hist = s.train(X, Y, epochs=40, batch=16, lr=2e-3, seed=1)
+        assert np.all(np.isfinite(hist))
+        assert hist[-1] < 0.5 * hist[0], hist
