@@ -87,20 +87,27 @@ def conv_t_backward(x, W, dy):
     return dx, dW, dy.sum(axis=(0, 1))
 
 
-def forward(theta, x, shp, c0=64, l0=64, keep=False):
+def _ident(a):
+    return a
+
+
+def forward(theta, x, shp, c0=64, l0=64, keep=False, q=_ident):
+    """`q` is applied to every operand of a contraction (identity: exact FP64;
+    a BF16 rounding reproduces the rounding points of a BF16 implementation)."""
     P = unpack(theta, shp)
     cache = {}
-    z1 = x @ P["W1"] + P["b1"]
-    h1 = gelu(z1)
+    xq = q(x)
+    z1 = xq @ P["W1"] + P["b1"]
+    h1 = q(gelu(z1))
     z2 = h1 @ P["W2"] + P["b2"]
-    h2 = gelu(z2)
+    h2 = q(gelu(z2))
     z3 = (h2 @ P["W3"] + P["b3"]).reshape(x.shape[0], l0, c0)
-    a = gelu(z3)
-    cache.update(x=x, z1=z1, h1=h1, z2=z2, h2=h2, z3=z3, a=[a], z=[])
+    a = q(gelu(z3))
+    cache.update(x=xq, z1=z1, h1=h1, z2=z2, h2=h2, z3=z3, a=[a], z=[])
     i = 0
     while f"T{i}" in P:
         z = conv_t(a, P[f"T{i}"], P[f"t{i}"])
-        a = gelu(z)
+        a = q(gelu(z))
         cache["z"].append(z)
         cache["a"].append(a)
         i += 1
@@ -109,8 +116,8 @@ def forward(theta, x, shp, c0=64, l0=64, keep=False):
     return (y, cache) if keep else y
 
 
-def loss_and_grad(theta, x, target, shp, c0=64, l0=64):
-    y, c = forward(theta, x, shp, c0, l0, keep=True)
+def loss_and_grad(theta, x, target, shp, c0=64, l0=64, q=_ident):
+    y, c = forward(theta, x, shp, c0, l0, keep=True, q=q)
     P = unpack(theta, shp)
     n = y.size
     loss = np.sum((y - target) ** 2) / n
@@ -118,24 +125,28 @@ def loss_and_grad(theta, x, target, shp, c0=64, l0=64):
     dy = np.transpose(dy, (0, 2, 1))  # [B, L, 8]
     G = {}
     a = c["a"][-1]
-    G["Wf"] = np.einsum("blc,blo->co", a, dy)
     G["bf"] = dy.sum(axis=(0, 1))
-    da = dy @ P["Wf"].T
+    dyq = q(dy)
+    G["Wf"] = np.einsum("blc,blo->co", a, dyq)
+    da = dyq @ P["Wf"].T
     nT = len(c["z"])
     for i in reversed(range(nT)):
         dz = da * gelu_grad(c["z"][i])
-        dx, G[f"T{i}"], G[f"t{i}"] = conv_t_backward(c["a"][i], P[f"T{i}"], dz)
+        G[f"t{i}"] = dz.sum(axis=(0, 1))
+        dx, G[f"T{i}"], _ = conv_t_backward(c["a"][i], P[f"T{i}"], q(dz))
         da = dx
     dz3 = (da * gelu_grad(c["z3"])).reshape(x.shape[0], -1)
-    G["W3"] = c["h2"].T @ dz3
     G["b3"] = dz3.sum(axis=0)
+    dz3 = q(dz3)
+    G["W3"] = c["h2"].T @ dz3
     dh2 = dz3 @ P["W3"].T
     dz2 = dh2 * gelu_grad(c["z2"])
-    G["W2"] = c["h1"].T @ dz2
     G["b2"] = dz2.sum(axis=0)
+    dz2 = q(dz2)
+    G["W2"] = c["h1"].T @ dz2
     dh1 = dz2 @ P["W2"].T
     dz1 = dh1 * gelu_grad(c["z1"])
-    G["W1"] = c["x"].T @ dz1
     G["b1"] = dz1.sum(axis=0)
+    G["W1"] = c["x"].T @ q(dz1)
     grad = np.concatenate([G[name].ravel() for name, _ in shp])
     return loss, grad

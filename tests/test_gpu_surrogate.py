@@ -18,6 +18,17 @@ def bf16_value(bits):
     return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
 
 
+def bf16_round(a):
+    a = np.asarray(a)
+    return bf16_value(to_bf16_bits(a.astype(np.float32))).reshape(a.shape)
+
+
+def cosine(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
+
+
 @pytest.mark.parametrize("ta,tb", [(False, False), (False, True), (True, False), (True, True)])
 @pytest.mark.parametrize("M,N,K", [(37, 70, 45), (128, 64, 32), (5, 3, 200), (300, 130, 17)])
 def test_tensor_core_gemm_against_fp64(ta, tb, M, N, K):
@@ -57,12 +68,25 @@ def test_forward_and_gradient_match_fp64_reference():
         assert Y.shape == ref.shape == (4, 8, 2048)
         rel = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
         assert rel <= 2e-2, rel
-        T = rng.standard_normal(ref.shape).astype(np.float32) * np.abs(ref).max()
-        loss, g = s.loss_grad(X, T)
-        lref, gref = R.loss_and_grad(thb, X.astype(np.float64), T.astype(np.float64), shp)
-        assert abs(loss - lref) <= 2e-2 * lref
-        cos = float(g @ gref / (np.linalg.norm(g) * np.linalg.norm(gref)))
-        assert cos >= 0.999, cos
+        # a target near the output (a trained-network regime) and a random one
+        for T in (ref * (1 + 0.1 * rng.standard_normal(ref.shape)),
+                  rng.standard_normal(ref.shape) * np.abs(ref).max()):
+            T = T.astype(np.float32)
+            loss, g = s.loss_grad(X, T)
+            lref, gref = R.loss_and_grad(thb, X.astype(np.float64), T.astype(np.float64), shp)
+            # the same contraction operands rounded to BF16 as on the GPU
+            lq, gq = R.loss_and_grad(thb, X.astype(np.float64), T.astype(np.float64), shp, q=bf16_round)
+            assert abs(loss - lref) <= 2e-2 * lref
+            per = {}
+            o = 0
+            for name, sh in shp:
+                nn = int(np.prod(sh))
+                a, b, c = g[o:o + nn], gq[o:o + nn], gref[o:o + nn]
+                per[name] = (cosine(a, b), cosine(a, c))
+                o += nn
+            assert cosine(g, gq) >= 0.999, per
+            assert min(v[0] for v in per.values()) >= 0.99, per
+            assert cosine(g, gref) >= 0.99, per
 
 
 def test_training_reduces_loss_on_a_smooth_map():
