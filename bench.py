@@ -237,7 +237,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--chunk", type=int, default=200, help="leapfrog steps per bench step")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused", "fused4"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nz", type=int, default=8192, help="interior z cells (8192 = the 20 m well; smaller for profiling)")
@@ -323,7 +323,7 @@ def main():
     tsim.close()
     avg = [(kt[q][0] - base[q][0]) / max(1, kt[q][1] - base[q][1]) for q in range(3)]
     if kind == 2:
-        names = ["fused_step", "-", "receivers"]
+        names = ["fused4_step" if tile >= 100 else "fused_step", "-", "receivers"]
         qd, per_cell = 0, b_fused
     else:
         names = ["vel_split", "str_split", "receivers"]
@@ -386,7 +386,7 @@ def main():
                 "config": {"workload": f"{sc.name}: Nr=180+16 PML, Ntheta=64, Nz=8192+2x16 PML, dr=dz=2.5 mm, "
                                        f"graded cement top, rock noise, 8 kHz monopole, 16 receivers",
                            "cells": cells, "leapfrog_steps_per_bench_step": T,
-                           "kernel": "fused" if kind == 2 else "split",
+                           "kernel": ("fused4" if tile >= 100 else "fused") if kind == 2 else "split",
                            "storage": args.storage, "parallelism": f"replicas x{ws}",
                            "l2": f"inputs larger than L2 ({bytes_held / 1e9:.1f} GB resident)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batch": batch,

@@ -64,7 +64,8 @@ extern "C" {
 
 #define SIM_KERNEL_AUTO 0     /* fastest path for the storage type */
 #define SIM_KERNEL_SPLIT 1    /* separate velocity and stress kernels */
-#define SIM_KERNEL_FUSED 2    /* one time-skewed kernel per step */
+#define SIM_KERNEL_FUSED 2    /* one time-skewed kernel per step, one cell per thread */
+#define SIM_KERNEL_FUSED_VEC 3 /* the time-skewed kernel with four z cells per thread */
 
 /* Grid (Sec. 3): interior cell counts, PML widths in cells, steps in metres.
  * nth must be even and >= 4; nr >= 2; nz >= 2.  dt > 0 fixes the time step;

@@ -17,7 +17,7 @@ from . import build as _build
 SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_EUNSTABLE, SIM_ETIMEOUT, SIM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 FIELDS = ("vr", "vp", "vz", "srr", "spp", "szz", "srp", "spz", "srz")
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
-KERNEL = {"auto": 0, "split": 1, "fused": 2}
+KERNEL = {"auto": 0, "split": 1, "fused": 2, "fused4": 3}
 
 
 class SimGrid(ctypes.Structure):

@@ -172,5 +172,10 @@ cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, cons
                                long long total, int grid, cudaStream_t s);
 cudaError_t launch_batch_receivers(int storage, const RParams *rp, int n_cases, cudaStream_t s);
 int fused_box_x(int storage);
+cudaError_t launch_fused4(int storage, int rt, const FusedMaps &maps, const FusedParams &fp, cudaStream_t s);
+size_t fused4_smem_bytes(int storage, int rt);
+// fused path tile code: rt < 100 = scalar fused kernel with rt rows, rt >= 100 =
+// vector fused kernel with rt - 100 rows
+inline int tile_rows(int code) { return code % 100; }
 int fused_pad_x(int storage);
 }  // namespace cwell

@@ -83,7 +83,7 @@ int cwell::validate_inputs(const sim_grid_t *g, const sim_medium_t *m, const sim
       return fail(nullptr, SIM_EINVAL, "receiver " + std::to_string(q) + " outside the interior");
   }
   if (o->storage < 0 || o->storage > 2) return fail(nullptr, SIM_EINVAL, "opts: storage must be 0, 1 or 2");
-  if (o->kernel < 0 || o->kernel > 2) return fail(nullptr, SIM_EINVAL, "opts: kernel must be 0, 1 or 2");
+  if (o->kernel < 0 || o->kernel > 3) return fail(nullptr, SIM_EINVAL, "opts: kernel must be 0, 1, 2 or 3");
   if (o->max_steps < 0) return fail(nullptr, SIM_EINVAL, "opts: max_steps < 0");
   return SIM_OK;
 }
@@ -128,7 +128,8 @@ static int make_map(sim_t *h, CUtensorMap *m, void *base, CUtensorMapDataType dt
   return SIM_OK;
 }
 
-static int build_maps(sim_t *h, int rt) {
+static int build_maps(sim_t *h, int code) {
+  const int rt = tile_rows(code);
   const CUtensorMapDataType dt = h->storage == 0   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                  : h->storage == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
@@ -149,12 +150,18 @@ static int build_maps(sim_t *h, int rt) {
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int, int, int, int>, int> g_tune;
 
+static cudaError_t launch_fused_any(int storage, int code, const FusedMaps &maps, const FusedParams &fp,
+                                    cudaStream_t s) {
+  return code >= 100 ? launch_fused4(storage, code - 100, maps, fp, s) : launch_fused(storage, code, maps, fp, s);
+}
+
 // Candidates: the fused kernel with each tile height that fits in shared
 // memory and, when allowed, the split kernels (returned as tile height 0).
-static int autotune(sim_t *h, bool allow_split, int *best_rt) {
+static int autotune(sim_t *h, int kernel, int *best_rt) {
+  const bool allow_split = kernel == SIM_KERNEL_AUTO;
   int dev = h->device, maxsm = 0;
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  auto key = std::make_tuple(dev, h->grid.nth, h->NR, h->NZ, h->storage * 2 + (allow_split ? 1 : 0),
+  auto key = std::make_tuple(dev, h->grid.nth, h->NR, h->NZ, h->storage * 4 + kernel,
                              h->kp.pml_r > 0 ? 1 : 0);
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
@@ -164,7 +171,7 @@ static int autotune(sim_t *h, bool allow_split, int *best_rt) {
       return SIM_OK;
     }
   }
-  const int cand[5] = {2, 4, 6, 8, 0};
+  const int cand[8] = {2, 4, 6, 8, 106, 110, 114, 0};
   cudaEvent_t a, b;
   CK(h, cudaEventCreate(&a));
   CK(h, cudaEventCreate(&b));
@@ -172,6 +179,8 @@ static int autotune(sim_t *h, bool allow_split, int *best_rt) {
   int pick = -1;
   for (int rt : cand) {
     cudaError_t e = cudaSuccess;
+    if (kernel == SIM_KERNEL_FUSED && rt >= 100) continue;
+    if (kernel == SIM_KERNEL_FUSED_VEC && rt < 100) continue;
     if (rt == 0) {
       if (!allow_split) continue;
       KParams dry = h->kp;
@@ -181,14 +190,15 @@ static int autotune(sim_t *h, bool allow_split, int *best_rt) {
       for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_split(h->storage, dry, h->stream, nullptr);
       cudaEventRecord(b, h->stream);
     } else {
-      if (fused_smem_bytes(h->storage, rt) > (size_t)maxsm) continue;
+      const size_t need = rt >= 100 ? fused4_smem_bytes(h->storage, rt - 100) : fused_smem_bytes(h->storage, rt);
+      if (need == 0 || need > (size_t)maxsm) continue;
       int rc = build_maps(h, rt);
       if (rc) return rc;
       FusedParams dry = h->fp[0];
       dry.k.src_i = -1;
-      for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_fused(h->storage, rt, h->maps[0], dry, h->stream);
+      for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_fused_any(h->storage, rt, h->maps[0], dry, h->stream);
       cudaEventRecord(a, h->stream);
-      for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_fused(h->storage, rt, h->maps[0], dry, h->stream);
+      for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_fused_any(h->storage, rt, h->maps[0], dry, h->stream);
       cudaEventRecord(b, h->stream);
     }
     if (e == cudaSuccess) e = cudaEventSynchronize(b);
@@ -244,7 +254,7 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   // AUTO prepares the fused path and lets the autotuner fall back to the split kernels
   h->kernel = opts->kernel == SIM_KERNEL_SPLIT ? SIM_KERNEL_SPLIT : SIM_KERNEL_FUSED;
   h->fused = h->kernel == SIM_KERNEL_FUSED;
-  const bool allow_split = opts->kernel == SIM_KERNEL_AUTO;
+
   h->graph_chunk = opts->graph_chunk == 0 ? 64 : opts->graph_chunk;
   h->timing = opts->timing;
   h->mem_cap = opts->mem_cap;
@@ -496,7 +506,7 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
       h->rp2[par].spp = nxt[F_SPP];
       h->rp2[par].szz = nxt[F_SZZ];
     }
-    if ((rc = autotune(h, allow_split, &h->tile_rt))) return bail(rc);
+    if ((rc = autotune(h, opts->kernel, &h->tile_rt))) return bail(rc);
     if (h->tile_rt == 0) {  // the split kernels won: run in place on the first buffer set
       h->fused = false;
       h->kernel = SIM_KERNEL_SPLIT;
@@ -518,7 +528,7 @@ static cudaError_t enqueue_step(sim_t *h, int parity, bool timed) {
   cudaError_t e;
   if (h->fused) {
     if (timed) cudaEventRecord(h->ev[0], h->stream);
-    e = launch_fused(h->storage, h->tile_rt, h->maps[parity], h->fp[parity], h->stream);
+    e = launch_fused_any(h->storage, h->tile_rt, h->maps[parity], h->fp[parity], h->stream);
     if (e != cudaSuccess) return e;
     if (timed) {
       cudaEventRecord(h->ev[1], h->stream);
@@ -710,7 +720,7 @@ extern "C" size_t sim_device_bytes(const sim_t *h) { return h ? h->bytes : 0; }
 extern "C" int sim_config(const sim_t *h, int *kernel, int *tile_rows) {
   if (!h) return SIM_EINVAL;
   if (kernel) *kernel = h->kernel;
-  if (tile_rows) *tile_rows = h->fused ? h->tile_rt : 0;
+  if (tile_rows) *tile_rows = h->fused ? h->tile_rt : 0;  // >= 100: vector variant with tile_rows - 100 rows
   return SIM_OK;
 }
 

@@ -39,7 +39,7 @@ def _ragged_scenario(seed=0, nth=6, nr=9, pml_r=3, nz=37, pml_z=3):
     return W.Scenario("ragged", med, W.Source(r=0.014, theta=2.0, z=0.06, f0=60e3), rec, steps=200)
 
 
-@pytest.mark.parametrize("kernel", ["split", "fused"])
+@pytest.mark.parametrize("kernel", ["split", "fused", "fused4"])
 def test_config1_traces_match_oracle(kernel):
     sc = W.config1()
     o = oracle.Oracle(sc)
@@ -71,7 +71,7 @@ def test_config1_long_window_traces_match_oracle():
             assert rel_l2(got[q], ref[q]) <= 10 * TRACE_TOL, q
 
 
-@pytest.mark.parametrize("kernel", ["split", "fused"])
+@pytest.mark.parametrize("kernel", ["split", "fused", "fused4"])
 @pytest.mark.parametrize("seed,nth,nr,nz", [(0, 6, 9, 37), (1, 4, 5, 70), (2, 8, 13, 2), (3, 4, 40, 131),
                                             (4, 10, 29, 190)])
 def test_ragged_grid_fields_elementwise(kernel, seed, nth, nr, nz):
@@ -242,11 +242,12 @@ def test_fused_matches_split_and_autotuner_choice():
         a.step(400)
         ta = a.traces()
         fa = {n: a.field(n) for n in ("vr", "srr", "srz")}
-    with sim(sc, kernel="fused") as b:
-        kind, tile = b.config()
-        assert kind == 2 and tile in (2, 4, 6, 8)
-        b.step(400)
-        tb = b.traces()
-        assert rel_l2(tb, ta) <= 1e-6
-        for n, x in fa.items():
-            assert rel_l2(b.field(n), x) <= 1e-6, n
+    for kern, tiles in (("fused", (2, 4, 6, 8)), ("fused4", (106, 110, 114))):
+        with sim(sc, kernel=kern) as b:
+            kind, tile = b.config()
+            assert kind == 2 and tile in tiles
+            b.step(400)
+            tb = b.traces()
+            assert rel_l2(tb, ta) <= 1e-6, kern
+            for n, x in fa.items():
+                assert rel_l2(b.field(n), x) <= 1e-6, (kern, n)
