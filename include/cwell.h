@@ -140,6 +140,20 @@ int sim_traces(sim_t *h, float *out, size_t cap, int *n_rec, int *n_steps);
 /* Host copy of field `which` (SIM_FIELD_*) as FP32 [nth][NR][NZ]; n = capacity. */
 int sim_read_field(sim_t *h, int which, float *out, size_t n);
 
+/* The same read-back as sim_read_field with no device allocation, for callers
+ * that cannot call cudaMalloc / cudaFree: a process whose device memory is
+ * fully reserved by a caching allocator (a new cudaMalloc would fail), or a
+ * monitoring thread beside running graph replays (cudaFree synchronises the
+ * whole device).  The paper has no counterpart; this is a library service.
+ * The FP32 conversion is staged in one fixed device array of 4 Mi floats
+ * (16 MiB) that every GPU loading the library holds until the process exits;
+ * a field of more than 4 Mi padded cells (nth * NR * NZ rounded up to 32 in z)
+ * is rejected with SIM_EINVAL.  The first call on a device looks up the
+ * array's device address, so make it before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (two threads, two handles
+ * at once) race; serialise them.  Synchronises the handle's stream. */
+int sim_read_field_noalloc(sim_t *h, int which, float *out, size_t n);
+
 /* Overwrite field `which` from host FP32 [nth][NR][NZ] (initial conditions). */
 int sim_write_field(sim_t *h, int which, const float *in, size_t n);
 

@@ -71,6 +71,8 @@ def lib(path: str | None = None):
         L.sim_traces.restype = i
         L.sim_read_field.argtypes = [p, i, ctypes.POINTER(ctypes.c_float), sz]
         L.sim_read_field.restype = i
+        L.sim_read_field_noalloc.argtypes = [p, i, ctypes.POINTER(ctypes.c_float), sz]
+        L.sim_read_field_noalloc.restype = i
         L.sim_write_field.argtypes = [p, i, ctypes.POINTER(ctypes.c_float), sz]
         L.sim_write_field.restype = i
         L.sim_dt.argtypes = [p]
@@ -214,6 +216,14 @@ class Simulation:
         out = np.zeros(self.grid.shape, np.float32)
         _check(self.L, self.h, self.L.sim_read_field(self.h, FIELDS.index(name),
                                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size))
+        return out
+
+    def field_noalloc(self, name: str) -> np.ndarray:
+        """As field(), staged in the library's fixed device scratch (no device allocation)."""
+        out = np.zeros(self.grid.shape, np.float32)
+        _check(self.L, self.h, self.L.sim_read_field_noalloc(self.h, FIELDS.index(name),
+                                                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                             out.size))
         return out
 
     def set_field(self, name: str, a: np.ndarray):

@@ -685,6 +685,59 @@ extern "C" int sim_read_field(sim_t *h, int which, float *out, size_t n) {
   return SIM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Field read-back without allocation.  Same result as sim_read_field, but the
+// storage-to-FP32 conversion is staged in this fixed device array instead of a
+// buffer obtained from cudaMalloc.  The array lives in device memory of every
+// GPU that loads the library, until the process exits.  In host code its name
+// is only a stand-in for the symbol: the kernel gets the device address that
+// cudaGetSymbolAddress returns for the current device.
+#define SIM_NOALLOC_SCRATCH_FLOATS (4u << 20) /* 16 MiB: fields of up to 4 Mi padded cells */
+static __device__ __align__(256) float g_field_scratch[SIM_NOALLOC_SCRATCH_FLOATS];
+static std::mutex g_scratch_mu;
+static float *g_scratch_addr[64] = {};
+
+// device address of the scratch array on the current device, looked up once per device
+static int scratch_address(sim_t *h, float **out) {
+  std::lock_guard<std::mutex> g(g_scratch_mu);
+  if (h->device < 0 || h->device >= 64) return fail(h, SIM_EINVAL, "device ordinal out of range for the scratch table");
+  if (!g_scratch_addr[h->device]) {
+    float *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void **)&p, g_field_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(h, e, "cudaGetSymbolAddress(g_field_scratch)");
+    g_scratch_addr[h->device] = p;
+  }
+  *out = g_scratch_addr[h->device];
+  return SIM_OK;
+}
+
+extern "C" int sim_read_field_noalloc(sim_t *h, int which, float *out, size_t n) {
+  if (!h) return SIM_EINVAL;
+  if (which < 0 || which >= NF || !out) return fail(h, SIM_EINVAL, "bad field index or buffer");
+  const size_t rows = (size_t)h->grid.nth * h->NR, need = rows * h->NZ;
+  if (n < need) return fail(h, SIM_EINVAL, "output buffer too small");
+  const long long tot = (long long)rows * h->NZp;
+  if (tot > (long long)SIM_NOALLOC_SCRATCH_FLOATS)
+    return fail(h, SIM_EINVAL, "field of " + std::to_string(tot) + " padded cells exceeds the " +
+                                   std::to_string(SIM_NOALLOC_SCRATCH_FLOATS) + "-float scratch of sim_read_field_noalloc");
+  CK(h, cudaSetDevice(h->device));
+  float *tmp = nullptr;
+  int rc = scratch_address(h, &tmp);
+  if (rc) return rc;
+  CK(h, cudaStreamSynchronize(h->stream));
+  const float sc = (float)(1.0 / field_scale(h, which));
+  const int blocks = (int)((tot + 255) / 256);
+  switch (h->storage) {  // every element the copy reads is written here: nothing needs clearing
+    case 0: to_f32<float><<<blocks, 256, 0, h->stream>>>((const float *)cur_fields(h)[which], tmp, tot, sc); break;
+    case 1: to_f32<__nv_bfloat16><<<blocks, 256, 0, h->stream>>>((const __nv_bfloat16 *)cur_fields(h)[which], tmp, tot, sc); break;
+    default: to_f32<__half><<<blocks, 256, 0, h->stream>>>((const __half *)cur_fields(h)[which], tmp, tot, sc); break;
+  }
+  CK(h, cudaGetLastError());
+  CK(h, cudaMemcpy2DAsync(out, h->NZ * 4, tmp, h->NZp * 4, h->NZ * 4, rows, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
 extern "C" int sim_write_field(sim_t *h, int which, const float *in, size_t n) {
   if (!h) return SIM_EINVAL;
   if (which < 0 || which >= NF || !in) return fail(h, SIM_EINVAL, "bad field index or buffer");
