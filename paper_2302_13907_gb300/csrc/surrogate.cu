@@ -569,6 +569,7 @@ extern "C" int sur_set_normalization(sur_t *s, const float *x_mean, const float 
   if (!s || !x_mean || !x_scale) return SIM_EINVAL;
   if (!(y_scale > 0) || !isfinite(y_scale)) return sfail(s, SIM_EINVAL, "output scale must be positive and finite");
   s->y_scale = y_scale;
+  SCK(s, cudaStreamSynchronize(s->stream));
   for (int q = 0; q < s->cfg.in_dim; q++)
     if (!(x_scale[q] != 0.f) || !isfinite(x_scale[q]) || !isfinite(x_mean[q]))
       return sfail(s, SIM_EINVAL, "normalisation scales must be finite and non-zero");
@@ -609,7 +610,9 @@ extern "C" int sur_loss_grad(sur_t *s, const float *X, const float *Y, int n, fl
   float l = 0.f;
   SCK(s, backward(s, n, &l));
   if (loss) *loss = l;
-  if (grad) SCK(s, cudaMemcpy(grad, s->g, s->nparam * 4, cudaMemcpyDeviceToHost));
+  // the gradient kernels run on the handle's (non-blocking) stream: copy on it and wait
+  if (grad) SCK(s, cudaMemcpyAsync(grad, s->g, s->nparam * 4, cudaMemcpyDeviceToHost, s->stream));
+  SCK(s, cudaStreamSynchronize(s->stream));
   return SIM_OK;
 }
 
@@ -680,6 +683,7 @@ extern "C" int sur_gate_fit(sur_t *s, const float *X, const float *err, int n) {
   if (!s || n < 1 || !X || !err) return s ? sfail(s, SIM_EINVAL, "bad gate data") : SIM_EINVAL;
   const int d = s->cfg.in_dim;
   std::vector<float> mean(d), scale(d);
+  SCK(s, cudaStreamSynchronize(s->stream));
   SCK(s, cudaMemcpy(mean.data(), s->x_mean, d * 4, cudaMemcpyDeviceToHost));
   SCK(s, cudaMemcpy(scale.data(), s->x_scale, d * 4, cudaMemcpyDeviceToHost));
   s->gate_x.resize((size_t)n * d);
