@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(F4Smem<T, RT>::NT) fused4_step(const __grid_co
                                                                   const __grid_constant__ FusedParams fp) {
   using SM = F4Smem<T, RT>;
   constexpr int ZT = SM::ZT, HX = SM::HX, BR = SM::BR, BW = SM::BW, BWI = SM::BWI, VW = SM::VW, NT = SM::NT,
-                VPL = SM::VPL, FB = SM::BOX_ELEMS;
+                VPL = SM::VPL;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char *smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
   float *vring = reinterpret_cast<float *>(smem + SM::RING_BYTES);
