@@ -101,6 +101,15 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_label(kind, tile):
+    """Name of the path sim_config reports (kernel kind, tile code)."""
+    if kind == 2:
+        return "fused4" if tile >= 100 else "fused"
+    if kind == 4:
+        return "march"
+    return "split"
+
+
 def alg_bytes_split(g, elem=4):
     """Algorithmic bytes per cell-update of the split kernels: each field read
     once and written once where updated, the material ID read once, PML memory
@@ -237,7 +246,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--chunk", type=int, default=200, help="leapfrog steps per bench step")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused", "fused4"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused", "fused4", "march"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nz", type=int, default=8192, help="interior z cells (8192 = the 20 m well; smaller for profiling)")
@@ -329,7 +338,8 @@ def main():
         names = ["fused4_step" if tile >= 100 else "fused_step", "-", "receivers"]
         qd, per_cell = 0, b_fused
     else:
-        names = ["vel_split", "str_split", "receivers"]
+        names = ["march_step(velocity)", "march_step(stress)", "receivers"] if kind == 4 else \
+            ["vel_split", "str_split", "receivers"]
         qd = 0 if avg[0] >= avg[1] else 1
         per_cell = b_vel if qd == 0 else b_str
     alg = per_cell * cells
@@ -389,7 +399,7 @@ def main():
                 "config": {"workload": f"{sc.name}: Nr=180+16 PML, Ntheta=64, Nz=8192+2x16 PML, dr=dz=2.5 mm, "
                                        f"graded cement top, rock noise, 8 kHz monopole, 16 receivers",
                            "cells": cells, "leapfrog_steps_per_bench_step": T,
-                           "kernel": ("fused4" if tile >= 100 else "fused") if kind == 2 else "split",
+                           "kernel": kernel_label(kind, tile),
                            "storage": args.storage, "parallelism": f"replicas x{ws}",
                            "l2": f"inputs larger than L2 ({bytes_held / 1e9:.1f} GB resident)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batch": batch,

@@ -66,6 +66,7 @@ extern "C" {
 #define SIM_KERNEL_SPLIT 1    /* separate velocity and stress kernels */
 #define SIM_KERNEL_FUSED 2    /* one time-skewed kernel per step, one cell per thread */
 #define SIM_KERNEL_FUSED_VEC 3 /* the time-skewed kernel with four z cells per thread */
+#define SIM_KERNEL_MARCH 4     /* velocity and stress kernels marching theta over TMA-staged planes */
 
 /* Grid (Sec. 3): interior cell counts, PML widths in cells, steps in metres.
  * nth must be even and >= 4; nr >= 2; nz >= 2.  dt > 0 fixes the time step;
@@ -115,6 +116,10 @@ typedef struct {
   int kernel;         /* SIM_KERNEL_* */
   int timing;         /* 1: bracket each kernel launch with CUDA events (no graph) */
   int device;         /* CUDA device ordinal */
+  int tile;           /* 0: the autotuner picks the tile; otherwise the tile code
+                         (see sim_config) of the requested kernel to run,
+                         SIM_EINVAL if that kernel has no such tile or it does
+                         not fit in shared memory */
 } sim_opts_t;
 
 typedef struct sim_s sim_t;
@@ -162,14 +167,16 @@ double sim_dt(const sim_t *h);
 int sim_steps_done(const sim_t *h);
 size_t sim_device_bytes(const sim_t *h);
 
-/* Path the handle runs: *kernel = SIM_KERNEL_SPLIT or SIM_KERNEL_FUSED;
- * *tile_rows = r rows per block of the fused kernel chosen by the autotuner
- * (0 for the split path). */
+/* Path the handle runs: *kernel = SIM_KERNEL_SPLIT, SIM_KERNEL_FUSED or
+ * SIM_KERNEL_MARCH; *tile_rows = the tile code chosen by the autotuner: 0 for
+ * the split path; r (< 100) for the fused kernel with r rows per block, 100 + r
+ * for its four-cells-per-thread variant; 1000 + 100 r + J for the marching
+ * kernels with r rows per block and runs of J theta planes. */
 int sim_config(const sim_t *h, int *kernel, int *tile_rows);
 
 /* Kernel timings gathered with opts.timing = 1: for kernel slot q
- * (0 = fused kernel or velocity kernel of the split path, 1 = stress kernel of
- * the split path, 2 = receivers), total milliseconds and launch count so far.
+ * (0 = fused kernel or velocity kernel of the split and marching paths,
+ * 1 = their stress kernel, 2 = receivers), total milliseconds and launch count so far.
  * Synchronises. */
 int sim_kernel_time(sim_t *h, int q, double *ms, long *launches);
 

@@ -17,7 +17,7 @@ from . import build as _build
 SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_EUNSTABLE, SIM_ETIMEOUT, SIM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 FIELDS = ("vr", "vp", "vz", "srr", "spp", "szz", "srp", "spz", "srz")
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
-KERNEL = {"auto": 0, "split": 1, "fused": 2, "fused4": 3}
+KERNEL = {"auto": 0, "split": 1, "fused": 2, "fused4": 3, "march": 4}
 
 
 class SimGrid(ctypes.Structure):
@@ -45,7 +45,7 @@ class SimReceivers(ctypes.Structure):
 class SimOpts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("pml_off", ctypes.c_int), ("graph_chunk", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("mem_cap", ctypes.c_size_t), ("max_steps", ctypes.c_int),
-                ("kernel", ctypes.c_int), ("timing", ctypes.c_int), ("device", ctypes.c_int)]
+                ("kernel", ctypes.c_int), ("timing", ctypes.c_int), ("device", ctypes.c_int), ("tile", ctypes.c_int)]
 
 
 _lib = None
@@ -133,7 +133,7 @@ def _check(L, h, rc):
 
 
 def make_structs(scenario, *, storage="f32", pml_on=None, graph_chunk=0, stream=None, mem_cap=0, max_steps=None,
-                 kernel="auto", timing=False, device=0, dt=0.0):
+                 kernel="auto", timing=False, device=0, dt=0.0, tile=0):
     """C structs for a workload Scenario; returns (structs, keepalive)."""
     m = scenario.medium
     g = m.grid
@@ -152,7 +152,8 @@ def make_structs(scenario, *, storage="f32", pml_on=None, graph_chunk=0, stream=
     cap = scenario.steps if max_steps is None else max_steps
     opts = SimOpts(STORAGE[storage] if isinstance(storage, str) else int(storage), 0 if on else 1, int(graph_chunk),
                    ctypes.c_void_p(stream) if stream else None, int(mem_cap), int(cap),
-                   KERNEL[kernel] if isinstance(kernel, str) else int(kernel), int(bool(timing)), int(device))
+                   KERNEL[kernel] if isinstance(kernel, str) else int(kernel), int(bool(timing)), int(device),
+                   int(tile))
     return (grid, med, src, rec, opts), keep
 
 
@@ -233,7 +234,8 @@ class Simulation:
                                                       a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
 
     def config(self):
-        """(kernel, tile_rows): kernel 1 = split, 2 = fused; tile rows chosen by the autotuner."""
+        """(kernel, tile code): kernel 1 = split, 2 = fused, 4 = marching; the tile code
+        the autotuner chose (0 split; r or 100 + r fused; 1000 + 100 r + J marching)."""
         k, t = ctypes.c_int(), ctypes.c_int()
         _check(self.L, self.h, self.L.sim_config(self.h, ctypes.byref(k), ctypes.byref(t)))
         return k.value, t.value

@@ -130,6 +130,7 @@ extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *m
   }
   sim_opts_t o = *opts;
   o.kernel = SIM_KERNEL_SPLIT;
+  o.tile = 0;
   o.cuda_stream = b->stream;
   o.graph_chunk = -1;
   o.timing = 0;

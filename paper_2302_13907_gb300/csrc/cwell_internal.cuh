@@ -178,4 +178,24 @@ size_t fused4_smem_bytes(int storage, int rt);
 // vector fused kernel with rt - 100 rows
 inline int tile_rows(int code) { return code % 100; }
 int fused_pad_x(int storage);
+// marching split path: tile code = 1000 + 100 * rows + planes per block
+// (rows in {2, 4, 8}, planes 1 .. 99); TMA boxes {march_box_x, rows + 2} for
+// the fields and {march_box_id, rows + 2} for the IDs
+inline bool is_march(int code) { return code >= 1000; }
+inline int march_rows(int code) { return (code / 100) % 10; }
+inline int march_planes(int code) { return code % 100; }
+cudaError_t launch_march(int storage, int code, const FusedMaps &maps, const KParams &p, int *status, cudaStream_t s,
+                         cudaEvent_t *ev);
+size_t march_smem_bytes(int storage, int code);
+// batched marching kernels: one well's descriptors, parameters and status word
+struct MarchCase {
+  FusedMaps maps;
+  KParams k;
+  int *status;
+};
+long long march_items(int code, int nth, int NR, int NZ);
+cudaError_t launch_march_batch(int storage, int code, bool vel, const MarchCase *cases, const long long *start,
+                               int n_cases, long long total, cudaStream_t s);
+int march_box_x(int storage);
+int march_box_id();
 }  // namespace cwell

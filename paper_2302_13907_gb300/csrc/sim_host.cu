@@ -83,7 +83,9 @@ int cwell::validate_inputs(const sim_grid_t *g, const sim_medium_t *m, const sim
       return fail(nullptr, SIM_EINVAL, "receiver " + std::to_string(q) + " outside the interior");
   }
   if (o->storage < 0 || o->storage > 2) return fail(nullptr, SIM_EINVAL, "opts: storage must be 0, 1 or 2");
-  if (o->kernel < 0 || o->kernel > 3) return fail(nullptr, SIM_EINVAL, "opts: kernel must be 0, 1, 2 or 3");
+  if (o->kernel < 0 || o->kernel > 4) return fail(nullptr, SIM_EINVAL, "opts: kernel must be 0 .. 4");
+  if (o->tile < 0 || (o->tile != 0 && o->kernel == SIM_KERNEL_SPLIT))
+    return fail(nullptr, SIM_EINVAL, "opts: tile must be 0, or a tile code of a tiled kernel");
   if (o->max_steps < 0) return fail(nullptr, SIM_EINVAL, "opts: max_steps < 0");
   return SIM_OK;
 }
@@ -145,6 +147,20 @@ static int build_maps(sim_t *h, int code) {
   return SIM_OK;
 }
 
+// descriptors of the marching kernels: the nine fields of the first buffer
+// set (updated in place) and the IDs, boxes of rows + 2 rows
+static int build_march_maps(sim_t *h, int code) {
+  const int rt = march_rows(code);
+  const CUtensorMapDataType dt = h->storage == 0   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : h->storage == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  for (int q = 0; q < NF; q++) {
+    int rc = make_map(h, &h->mmaps.f[q], h->f[q], dt, (int)h->elem, march_box_x(h->storage), rt + 2);
+    if (rc) return rc;
+  }
+  return make_map(h, &h->mmaps.id, h->id, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, march_box_id(), rt + 2);
+}
+
 // Autotuner: time each tile height on the still-zero state with the source
 // disabled (the state stays zero), keep the fastest; cached per grid shape.
 static std::mutex g_tune_mu;
@@ -155,15 +171,16 @@ static cudaError_t launch_fused_any(int storage, int code, const FusedMaps &maps
   return code >= 100 ? launch_fused4(storage, code - 100, maps, fp, s) : launch_fused(storage, code, maps, fp, s);
 }
 
-// Candidates: the fused kernel with each tile height that fits in shared
-// memory and, when allowed, the split kernels (returned as tile height 0).
-static int autotune(sim_t *h, int kernel, int *best_rt) {
+// Candidates: the fused kernels with each tile height that fits in shared
+// memory, the marching split kernels with each tile height and theta run, and,
+// when allowed, the split kernels (returned as code 0).
+static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
   const bool allow_split = kernel == SIM_KERNEL_AUTO;
   int dev = h->device, maxsm = 0;
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  auto key = std::make_tuple(dev, h->grid.nth, h->NR, h->NZ, h->storage * 4 + kernel,
+  auto key = std::make_tuple(dev, h->grid.nth, h->NR, h->NZ, h->storage * 8 + kernel,
                              h->kp.pml_r > 0 ? 1 : 0);
-  {
+  if (!forced) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
@@ -171,7 +188,7 @@ static int autotune(sim_t *h, int kernel, int *best_rt) {
       return SIM_OK;
     }
   }
-  const int cand[8] = {2, 4, 6, 8, 106, 110, 114, 0};
+  const int cand[] = {2, 4, 6, 8, 106, 110, 114, 1216, 1232, 1264, 1416, 1432, 1464, 1816, 1832, 1864, 0};
   cudaEvent_t a, b;
   CK(h, cudaEventCreate(&a));
   CK(h, cudaEventCreate(&b));
@@ -179,8 +196,19 @@ static int autotune(sim_t *h, int kernel, int *best_rt) {
   int pick = -1;
   for (int rt : cand) {
     cudaError_t e = cudaSuccess;
-    if (kernel == SIM_KERNEL_FUSED && rt >= 100) continue;
-    if (kernel == SIM_KERNEL_FUSED_VEC && rt < 100) continue;
+    if (kernel == SIM_KERNEL_FUSED && (rt >= 100 || rt == 0)) continue;
+    if (kernel == SIM_KERNEL_FUSED_VEC && (rt < 100 || rt >= 1000)) continue;
+    if (kernel == SIM_KERNEL_MARCH && !is_march(rt)) continue;
+    if (!h->fused && rt != 0 && !is_march(rt)) continue;  // no second buffer set for the fused kernels
+    if (forced && rt != forced) continue;
+    if (forced) {  // a tile asked for by the caller: check that it fits, time nothing
+      const size_t need = is_march(rt) ? march_smem_bytes(h->storage, rt)
+                          : rt >= 100  ? fused4_smem_bytes(h->storage, rt - 100)
+                                       : fused_smem_bytes(h->storage, rt);
+      if (need == 0 || need > (size_t)maxsm) continue;
+      pick = rt;
+      break;
+    }
     if (rt == 0) {
       if (!allow_split) continue;
       KParams dry = h->kp;
@@ -188,6 +216,20 @@ static int autotune(sim_t *h, int kernel, int *best_rt) {
       for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_split(h->storage, dry, h->stream, nullptr);
       cudaEventRecord(a, h->stream);
       for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_split(h->storage, dry, h->stream, nullptr);
+      cudaEventRecord(b, h->stream);
+    } else if (is_march(rt)) {
+      const size_t need = march_smem_bytes(h->storage, rt);
+      if (need == 0 || need > (size_t)maxsm) continue;
+      if (march_planes(rt) > 16 && march_planes(rt) / 2 >= h->grid.nth) continue;  // same launch as a shorter run
+      int rc = build_march_maps(h, rt);
+      if (rc) return rc;
+      KParams dry = h->kp;
+      dry.src_i = -1;
+      for (int w = 0; w < 2 && e == cudaSuccess; w++)
+        e = launch_march(h->storage, rt, h->mmaps, dry, h->status, h->stream, nullptr);
+      cudaEventRecord(a, h->stream);
+      for (int w = 0; w < 3 && e == cudaSuccess; w++)
+        e = launch_march(h->storage, rt, h->mmaps, dry, h->status, h->stream, nullptr);
       cudaEventRecord(b, h->stream);
     } else {
       const size_t need = rt >= 100 ? fused4_smem_bytes(h->storage, rt - 100) : fused_smem_bytes(h->storage, rt);
@@ -216,8 +258,10 @@ static int autotune(sim_t *h, int kernel, int *best_rt) {
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  if (pick < 0) return fail(h, SIM_EUNSUPPORTED, "no fused tile fits in shared memory");
-  {
+  if (pick < 0 && forced)
+    return fail(h, SIM_EINVAL, "opts.tile " + std::to_string(forced) + " is not a tile of the requested kernel that fits");
+  if (pick < 0) return fail(h, SIM_EUNSUPPORTED, "no tile of the requested kernel fits in shared memory");
+  if (!forced) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_tune[key] = pick;
   }
@@ -251,8 +295,11 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   h->NZp = NZp;
   h->storage = opts->storage;
   h->elem = opts->storage == 0 ? 4 : 2;
-  // AUTO prepares the fused path and lets the autotuner fall back to the split kernels
-  h->kernel = opts->kernel == SIM_KERNEL_SPLIT ? SIM_KERNEL_SPLIT : SIM_KERNEL_FUSED;
+  // AUTO prepares the fused path and lets the autotuner fall back to the split
+  // or marching kernels; the split and marching paths update one buffer set in place
+  h->kernel = opts->kernel == SIM_KERNEL_SPLIT   ? SIM_KERNEL_SPLIT
+              : opts->kernel == SIM_KERNEL_MARCH ? SIM_KERNEL_MARCH
+                                                 : SIM_KERNEL_FUSED;
   h->fused = h->kernel == SIM_KERNEL_FUSED;
 
   h->graph_chunk = opts->graph_chunk == 0 ? 64 : opts->graph_chunk;
@@ -506,15 +553,26 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
       h->rp2[par].spp = nxt[F_SPP];
       h->rp2[par].szz = nxt[F_SZZ];
     }
-    if ((rc = autotune(h, opts->kernel, &h->tile_rt))) return bail(rc);
+    if ((rc = autotune(h, opts->kernel, opts->tile, &h->tile_rt))) return bail(rc);
     if (h->tile_rt == 0) {  // the split kernels won: run in place on the first buffer set
       h->fused = false;
       h->kernel = SIM_KERNEL_SPLIT;
+    } else if (is_march(h->tile_rt)) {  // the marching kernels won: in place as well
+      h->fused = false;
+      h->kernel = SIM_KERNEL_MARCH;
     } else if ((rc = build_maps(h, h->tile_rt))) {
       return bail(rc);
     }
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "autotune"));
+  } else if (h->kernel == SIM_KERNEL_MARCH) {
+    if ((rc = autotune(h, SIM_KERNEL_MARCH, opts->tile, &h->tile_rt))) return bail(rc);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "autotune"));
+  }
+  if (h->kernel == SIM_KERNEL_MARCH) {
+    h->march = true;
+    if ((rc = build_march_maps(h, h->tile_rt))) return bail(rc);
   }
   if (h->timing)
     for (auto &ev : h->ev)
@@ -535,6 +593,10 @@ static cudaError_t enqueue_step(sim_t *h, int parity, bool timed) {
       cudaEventRecord(h->ev[2], h->stream);
     }
     e = launch_receivers(h->storage, h->rp2[parity], h->stream);
+  } else if (h->march) {
+    e = launch_march(h->storage, h->tile_rt, h->mmaps, h->kp, h->status, h->stream, timed ? h->ev : nullptr);
+    if (e != cudaSuccess) return e;
+    e = launch_receivers(h->storage, h->rp, h->stream);
   } else {
     e = launch_split(h->storage, h->kp, h->stream, timed ? h->ev : nullptr);
     if (e != cudaSuccess) return e;
@@ -773,7 +835,7 @@ extern "C" size_t sim_device_bytes(const sim_t *h) { return h ? h->bytes : 0; }
 extern "C" int sim_config(const sim_t *h, int *kernel, int *tile_rows) {
   if (!h) return SIM_EINVAL;
   if (kernel) *kernel = h->kernel;
-  if (tile_rows) *tile_rows = h->fused ? h->tile_rt : 0;  // >= 100: vector variant with tile_rows - 100 rows
+  if (tile_rows) *tile_rows = (h->fused || h->march) ? h->tile_rt : 0;
   return SIM_OK;
 }
 

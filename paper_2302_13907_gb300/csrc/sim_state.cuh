@@ -42,6 +42,9 @@ struct sim_s {
   float *psr2[NPR] = {};
   float *psz2[NPZ] = {};
   FusedMaps maps[2];
+  // marching split path (in place on the first buffer set): TMA descriptors
+  bool march = false;
+  FusedMaps mmaps;
   FusedParams fp[2];
   RParams rp2[2];
   int steps_done = 0;

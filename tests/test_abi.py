@@ -67,6 +67,14 @@ def test_host_validation_rejects_bad_input(mutate, code):
     assert L.sim_last_error(None)
 
 
+@pytest.mark.parametrize("kw", [dict(kernel="split", tile=1416), dict(kernel="march", tile=-3), dict(kernel=7)])
+def test_host_validation_rejects_bad_kernel_options(kw):
+    """Kernel / tile options are checked on the host before any device call."""
+    rc, h, L = _create(_tiny(), **kw)
+    assert rc == B.SIM_EINVAL, L.sim_last_error(None)
+    assert not h.value
+
+
 def test_error_strings():
     L = B.lib()
     for c in (0, -1, -2, -3, -4, -5, -6):

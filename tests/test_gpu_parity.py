@@ -39,7 +39,7 @@ def _ragged_scenario(seed=0, nth=6, nr=9, pml_r=3, nz=37, pml_z=3):
     return W.Scenario("ragged", med, W.Source(r=0.014, theta=2.0, z=0.06, f0=60e3), rec, steps=200)
 
 
-@pytest.mark.parametrize("kernel", ["split", "fused", "fused4"])
+@pytest.mark.parametrize("kernel", ["split", "fused", "fused4", "march"])
 def test_config1_traces_match_oracle(kernel):
     sc = W.config1()
     o = oracle.Oracle(sc)
@@ -71,7 +71,7 @@ def test_config1_long_window_traces_match_oracle():
             assert rel_l2(got[q], ref[q]) <= 10 * TRACE_TOL, q
 
 
-@pytest.mark.parametrize("kernel", ["split", "fused", "fused4"])
+@pytest.mark.parametrize("kernel", ["split", "fused", "fused4", "march"])
 @pytest.mark.parametrize("seed,nth,nr,nz", [(0, 6, 9, 37), (1, 4, 5, 70), (2, 8, 13, 2), (3, 4, 40, 131),
                                             (4, 10, 29, 190)])
 def test_ragged_grid_fields_elementwise(kernel, seed, nth, nr, nz):
@@ -233,6 +233,36 @@ def test_full_size_well_sampled_against_oracle_crop():
         assert rel_l2(sub, ref) <= TRACE_TOL, (q, rel_l2(sub, ref))
 
 
+MARCH_TILES = (1216, 1232, 1264, 1416, 1432, 1464, 1816, 1832, 1864)
+
+
+@pytest.mark.parametrize("tile", MARCH_TILES)
+def test_march_every_tile_fields_elementwise(tile):
+    """The marching kernels at every tile code the autotuner may pick, on a
+    grid where neither Ntheta (runs of 16 / 32 / 64 planes), NR (tiles of
+    2 / 4 / 8 rows) nor NZ (tiles of 128) divides evenly, with an off-axis
+    source: every field against the oracle element by element."""
+    sc = _ragged_scenario(seed=5, nth=40, nr=14, nz=150)
+    o = oracle.Oracle(sc)
+    o.step(sc.steps)
+    with sim(sc, kernel="march", tile=tile) as s:
+        assert s.config() == (4, tile)
+        s.step(sc.steps)
+        for n in oracle.FIELDS:
+            a, b = s.field(n), o.field(n)
+            scale = np.abs(b).max()
+            assert scale > 0, n
+            assert np.abs(a - b).max() <= 2e-5 * scale, (n, np.abs(a - b).max() / scale)
+        assert rel_l2(s.traces(), o.traces()) <= TRACE_TOL
+
+
+def test_march_rejects_a_tile_it_does_not_have():
+    from paper_2302_13907_gb300.binding import SIM_EINVAL, SimError
+    with pytest.raises(SimError) as ei:
+        sim(W.config1(steps=4), kernel="march", tile=1234)
+    assert ei.value.code == SIM_EINVAL
+
+
 def test_fused_matches_split_and_autotuner_choice():
     """The fused (time-skewed, TMA-staged) kernel and the split kernels
     compute the same scheme: traces agree to FP32 rounding; every tile
@@ -242,10 +272,10 @@ def test_fused_matches_split_and_autotuner_choice():
         a.step(400)
         ta = a.traces()
         fa = {n: a.field(n) for n in ("vr", "srr", "srz")}
-    for kern, tiles in (("fused", (2, 4, 6, 8)), ("fused4", (106, 110, 114))):
+    for kern, tiles in (("fused", (2, 4, 6, 8)), ("fused4", (106, 110, 114)), ("march", MARCH_TILES)):
         with sim(sc, kernel=kern) as b:
             kind, tile = b.config()
-            assert kind == 2 and tile in tiles
+            assert kind == (4 if kern == "march" else 2) and tile in tiles
             b.step(400)
             tb = b.traces()
             assert rel_l2(tb, ta) <= 1e-6, kern
