@@ -107,7 +107,7 @@ def kernel_label(kind, tile):
         return "fused4" if tile >= 100 else "fused"
     if kind == 4:
         return "march"
-    return "split"
+    return "split (load-first)" if tile > 2000 else "split"
 
 
 def alg_bytes_split(g, elem=4):
@@ -339,7 +339,7 @@ def main():
         qd, per_cell = 0, b_fused
     else:
         names = ["march_step(velocity)", "march_step(stress)", "receivers"] if kind == 4 else \
-            ["vel_split", "str_split", "receivers"]
+            ["vel_hoist", "str_hoist", "receivers"] if tile > 2000 else ["vel_split", "str_split", "receivers"]
         qd = 0 if avg[0] >= avg[1] else 1
         per_cell = b_vel if qd == 0 else b_str
     alg = per_cell * cells

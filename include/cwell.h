@@ -168,10 +168,12 @@ int sim_steps_done(const sim_t *h);
 size_t sim_device_bytes(const sim_t *h);
 
 /* Path the handle runs: *kernel = SIM_KERNEL_SPLIT, SIM_KERNEL_FUSED or
- * SIM_KERNEL_MARCH; *tile_rows = the tile code chosen by the autotuner: 0 for
- * the split path; r (< 100) for the fused kernel with r rows per block, 100 + r
- * for its four-cells-per-thread variant; 1000 + 100 r + J for the marching
- * kernels with r rows per block and runs of J theta planes. */
+ * SIM_KERNEL_MARCH; *tile_rows = the tile code chosen by the autotuner (or
+ * forced by opts.tile): r (< 100) for the fused kernel with r rows per block,
+ * 100 + r for its four-cells-per-thread variant; 1000 + 100 r + J for the
+ * marching kernels with r rows per block and runs of J theta planes; 2000 for
+ * the split kernels, 2000 + b for their load-first variant compiled for b
+ * resident blocks per SM. */
 int sim_config(const sim_t *h, int *kernel, int *tile_rows);
 
 /* Kernel timings gathered with opts.timing = 1: for kernel slot q
@@ -196,10 +198,12 @@ const char *sim_error_string(int code);
  * of them.  Each case is defined exactly as for sim_create (grid, medium,
  * source, receivers; shapes may differ between cases); opts is shared
  * (storage, stream, device, mem_cap applied to the batch total, graph_chunk,
- * max_steps).  The cases run the split kernels driven by persistent blocks
- * that walk a work list of (case, theta, r tile, z tile) items; the number of
- * persistent blocks is chosen by timing candidates at create time.  A case
- * computes exactly what its own sim_create handle would.
+ * max_steps; opts.kernel and opts.tile are ignored).  The cases run the
+ * load-first split bodies (tile code 2004 of sim_config) driven by blocks that
+ * walk a work list of (case, theta, r tile, z tile) items; the number of
+ * blocks is chosen by timing candidates at create time.  A case computes
+ * exactly what its own sim_create handle with kernel SIM_KERNEL_SPLIT and
+ * tile 2004 computes.  SIM_EINVAL for a case of more than 2^31 - 1 items.
  * ------------------------------------------------------------------------ */
 typedef struct simb_s simb_t;
 

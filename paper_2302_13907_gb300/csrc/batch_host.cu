@@ -1,6 +1,6 @@
-// Batched scenarios: many wells advanced by one persistent launch per kernel
-// per step.  Every case is a regular simulator handle (same validation and
-// set-up as sim_create, split kernels, buffers updated in place); the batch
+// Batched scenarios: many wells advanced by one launch per kernel per step.
+// Every case is a regular simulator handle (same validation and set-up as
+// sim_create, buffers updated in place by the load-first split bodies); the batch
 // holds device arrays of their kernel parameters and a prefix sum of their
 // work items, and captures its steps in a CUDA graph.
 #include <algorithm>
@@ -130,7 +130,7 @@ extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *m
   }
   sim_opts_t o = *opts;
   o.kernel = SIM_KERNEL_SPLIT;
-  o.tile = 0;
+  o.tile = SPLIT_CODE;  // the batch drives the plain split bodies: no per-case tuning
   o.cuda_stream = b->stream;
   o.graph_chunk = -1;
   o.timing = 0;
@@ -143,7 +143,10 @@ extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *m
     if (rc) return bail(bfail(b, rc, "case " + std::to_string(c) + ": " + sim_last_error(nullptr)));
     b->cases.push_back(h);
     used += sim_device_bytes(h);
-    start[c + 1] = start[c] + split_items(grids[c].nth, grids[c].nr + grids[c].pml_r, grids[c].nz + 2 * grids[c].pml_z);
+    const long long items = split_items(grids[c].nth, grids[c].nr + grids[c].pml_r, grids[c].nz + 2 * grids[c].pml_z);
+    if (items > 0x7fffffffLL)
+      return bail(bfail(b, SIM_EINVAL, "case " + std::to_string(c) + ": more work items than a 32-bit index holds"));
+    start[c + 1] = start[c] + items;
   }
   b->total = start[n];
   std::vector<KParams> kp(n);

@@ -135,6 +135,13 @@ __device__ __forceinline__ void ld_ids(const uint16_t *p, int (&o)[4]) {
   o[3] = u.y >> 16;
 }
 
+// velocity coefficient 2 dt / (rho_a + rho_b) (two-cell mean density) and
+// four-cell harmonic shear modulus 4 / sum(1/mu), by the fast division
+// intrinsic (within 2 ulp; the coefficients need no more).  A liquid among the
+// four cells makes the sum +inf and the modulus exactly 0.
+__device__ __forceinline__ float vel_coef(float dtv, float rho_sum) { return __fdividef(2.f * dtv, rho_sum); }
+__device__ __forceinline__ float mu_harm(float imu_sum) { return __fdividef(4.f, imu_sum); }
+
 // convolutional memory variable: psi <- b psi + a D, returns D + psi
 __device__ __forceinline__ float stretch(float *psi, float a, float b, float D) {
   float p = b * (*psi) + a * D;
@@ -181,12 +188,20 @@ int fused_pad_x(int storage);
 // marching split path: tile code = 1000 + 100 * rows + planes per block
 // (rows in {2, 4, 8}, planes 1 .. 99); TMA boxes {march_box_x, rows + 2} for
 // the fields and {march_box_id, rows + 2} for the IDs
-inline bool is_march(int code) { return code >= 1000; }
+inline bool is_march(int code) { return code >= 1000 && code < 2000; }
 inline int march_rows(int code) { return (code / 100) % 10; }
 inline int march_planes(int code) { return code % 100; }
 cudaError_t launch_march(int storage, int code, const FusedMaps &maps, const KParams &p, int *status, cudaStream_t s,
                          cudaEvent_t *ev);
 size_t march_smem_bytes(int storage, int code);
+// split path: tile code 2000 = the kernels of stencil_split.cu; 2000 + b =
+// the load-first kernels of stencil_hoist.cu with b resident blocks per SM
+// asked of the register allocator (b = 3, 4 or 5)
+constexpr int SPLIT_CODE = 2000;
+inline bool is_split_family(int code) { return code >= 2000 && code < 3000; }
+inline bool is_hoist(int code) { return code > 2000 && code < 3000; }
+inline int hoist_blocks(int code) { return code - 2000; }
+cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev);
 // batched marching kernels: one well's descriptors, parameters and status word
 struct MarchCase {
   FusedMaps maps;

@@ -84,8 +84,15 @@ int cwell::validate_inputs(const sim_grid_t *g, const sim_medium_t *m, const sim
   }
   if (o->storage < 0 || o->storage > 2) return fail(nullptr, SIM_EINVAL, "opts: storage must be 0, 1 or 2");
   if (o->kernel < 0 || o->kernel > 4) return fail(nullptr, SIM_EINVAL, "opts: kernel must be 0 .. 4");
-  if (o->tile < 0 || (o->tile != 0 && o->kernel == SIM_KERNEL_SPLIT))
-    return fail(nullptr, SIM_EINVAL, "opts: tile must be 0, or a tile code of a tiled kernel");
+  if (o->tile != 0) {  // the family of the code must match the kernel asked for; the code itself is checked later
+    const int t = o->tile;
+    const bool ok = t > 0 && ((o->kernel == SIM_KERNEL_SPLIT && is_split_family(t)) ||
+                              (o->kernel == SIM_KERNEL_FUSED && t < 100) ||
+                              (o->kernel == SIM_KERNEL_FUSED_VEC && t >= 100 && t < 1000) ||
+                              (o->kernel == SIM_KERNEL_MARCH && is_march(t)) ||
+                              (o->kernel == SIM_KERNEL_AUTO && t < 3000));
+    if (!ok) return fail(nullptr, SIM_EINVAL, "opts: tile " + std::to_string(t) + " is not a tile code of the kernel asked for");
+  }
   if (o->max_steps < 0) return fail(nullptr, SIM_EINVAL, "opts: max_steps < 0");
   return SIM_OK;
 }
@@ -172,10 +179,14 @@ static cudaError_t launch_fused_any(int storage, int code, const FusedMaps &maps
 }
 
 // Candidates: the fused kernels with each tile height that fits in shared
-// memory, the marching split kernels with each tile height and theta run, and,
-// when allowed, the split kernels (returned as code 0).
+// memory, the marching split kernels with each tile height and theta run, and
+// the split kernels (plain and load-first), as far as the requested kernel allows.
+static cudaError_t launch_split_family(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev) {
+  return is_hoist(code) ? launch_hoist(storage, code, p, s, ev) : launch_split(storage, p, s, ev);
+}
+
 static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
-  const bool allow_split = kernel == SIM_KERNEL_AUTO;
+  const bool allow_split = kernel == SIM_KERNEL_AUTO || kernel == SIM_KERNEL_SPLIT;
   int dev = h->device, maxsm = 0;
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   auto key = std::make_tuple(dev, h->grid.nth, h->NR, h->NZ, h->storage * 8 + kernel,
@@ -188,7 +199,8 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
       return SIM_OK;
     }
   }
-  const int cand[] = {2, 4, 6, 8, 106, 110, 114, 1216, 1232, 1264, 1416, 1432, 1464, 1816, 1832, 1864, 0};
+  const int cand[] = {2,    4,    6,    8,    106,  110,  114,  1216, 1232, 1264,
+                      1416, 1432, 1464, 1816, 1832, 1864, 2003, 2004, 2005, SPLIT_CODE};
   cudaEvent_t a, b;
   CK(h, cudaEventCreate(&a));
   CK(h, cudaEventCreate(&b));
@@ -196,26 +208,29 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
   int pick = -1;
   for (int rt : cand) {
     cudaError_t e = cudaSuccess;
-    if (kernel == SIM_KERNEL_FUSED && (rt >= 100 || rt == 0)) continue;
-    if (kernel == SIM_KERNEL_FUSED_VEC && (rt < 100 || rt >= 1000)) continue;
+    const bool fused_code = rt < 1000;
+    if (kernel == SIM_KERNEL_FUSED && (!fused_code || rt >= 100)) continue;
+    if (kernel == SIM_KERNEL_FUSED_VEC && (!fused_code || rt < 100)) continue;
     if (kernel == SIM_KERNEL_MARCH && !is_march(rt)) continue;
-    if (!h->fused && rt != 0 && !is_march(rt)) continue;  // no second buffer set for the fused kernels
+    if (kernel == SIM_KERNEL_SPLIT && !is_split_family(rt)) continue;
+    if (is_split_family(rt) && !allow_split) continue;
+    if (!h->fused && fused_code) continue;  // no second buffer set for the fused kernels
     if (forced && rt != forced) continue;
     if (forced) {  // a tile asked for by the caller: check that it fits, time nothing
-      const size_t need = is_march(rt) ? march_smem_bytes(h->storage, rt)
-                          : rt >= 100  ? fused4_smem_bytes(h->storage, rt - 100)
-                                       : fused_smem_bytes(h->storage, rt);
+      const size_t need = is_split_family(rt) ? 1
+                          : is_march(rt)      ? march_smem_bytes(h->storage, rt)
+                          : rt >= 100         ? fused4_smem_bytes(h->storage, rt - 100)
+                                              : fused_smem_bytes(h->storage, rt);
       if (need == 0 || need > (size_t)maxsm) continue;
       pick = rt;
       break;
     }
-    if (rt == 0) {
-      if (!allow_split) continue;
+    if (is_split_family(rt)) {
       KParams dry = h->kp;
       dry.src_i = -1;  // no source: zero state stays zero
-      for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_split(h->storage, dry, h->stream, nullptr);
+      for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_split_family(h->storage, rt, dry, h->stream, nullptr);
       cudaEventRecord(a, h->stream);
-      for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_split(h->storage, dry, h->stream, nullptr);
+      for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_split_family(h->storage, rt, dry, h->stream, nullptr);
       cudaEventRecord(b, h->stream);
     } else if (is_march(rt)) {
       const size_t need = march_smem_bytes(h->storage, rt);
@@ -554,7 +569,7 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
       h->rp2[par].szz = nxt[F_SZZ];
     }
     if ((rc = autotune(h, opts->kernel, opts->tile, &h->tile_rt))) return bail(rc);
-    if (h->tile_rt == 0) {  // the split kernels won: run in place on the first buffer set
+    if (is_split_family(h->tile_rt)) {  // the split kernels won: run in place on the first buffer set
       h->fused = false;
       h->kernel = SIM_KERNEL_SPLIT;
     } else if (is_march(h->tile_rt)) {  // the marching kernels won: in place as well
@@ -565,8 +580,8 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
     }
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "autotune"));
-  } else if (h->kernel == SIM_KERNEL_MARCH) {
-    if ((rc = autotune(h, SIM_KERNEL_MARCH, opts->tile, &h->tile_rt))) return bail(rc);
+  } else {  // the marching or the split kernels, asked for by name
+    if ((rc = autotune(h, h->kernel, opts->tile, &h->tile_rt))) return bail(rc);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "autotune"));
   }
@@ -598,7 +613,7 @@ static cudaError_t enqueue_step(sim_t *h, int parity, bool timed) {
     if (e != cudaSuccess) return e;
     e = launch_receivers(h->storage, h->rp, h->stream);
   } else {
-    e = launch_split(h->storage, h->kp, h->stream, timed ? h->ev : nullptr);
+    e = launch_split_family(h->storage, h->tile_rt, h->kp, h->stream, timed ? h->ev : nullptr);
     if (e != cudaSuccess) return e;
     e = launch_receivers(h->storage, h->rp, h->stream);
   }
@@ -835,7 +850,7 @@ extern "C" size_t sim_device_bytes(const sim_t *h) { return h ? h->bytes : 0; }
 extern "C" int sim_config(const sim_t *h, int *kernel, int *tile_rows) {
   if (!h) return SIM_EINVAL;
   if (kernel) *kernel = h->kernel;
-  if (tile_rows) *tile_rows = (h->fused || h->march) ? h->tile_rt : 0;
+  if (tile_rows) *tile_rows = h->tile_rt;
   return SIM_OK;
 }
 

@@ -173,7 +173,7 @@ __device__ __forceinline__ void fused_tile(const FusedMaps &maps, const FusedPar
         Dz += ps;
       }
       const float rho = __ldg(m_rho + I0[xi]) + __ldg(m_rho + I0[xi - BWI]);
-      out = sld(S0 + x) + 2.f * dtv / rho * (Dr + Q + Dz);
+      out = sld(S0 + x) + vel_coef(dtv, rho) * (Dr + Q + Dz);
     } else if (c == 1) {  // v_phi at (r_{i+1/2}, theta_{j+1/2}, z_k)
       if (ii < 0 || ii >= NR || k >= NZ) return 0.f;
       const float s1 = sld(S0 + 6 * F + x + BW), s0v = sld(S0 + 6 * F + x);
@@ -196,7 +196,7 @@ __device__ __forceinline__ void fused_tile(const FusedMaps &maps, const FusedPar
         Dz += ps;
       }
       const float rho = __ldg(m_rho + I0[xi]) + __ldg(m_rho + slot_ids(sp1)[xi]);
-      out = sld(S0 + F + x) + 2.f * dtv / rho * (Dr + Q + Dz);
+      out = sld(S0 + F + x) + vel_coef(dtv, rho) * (Dr + Q + Dz);
     } else {  // v_z at (r_{i+1/2}, theta_j, z_{k+1/2}); the last half-node is a wall
       if (ii < 0 || ii >= NR || k < 0 || k + 1 >= NZ) return 0.f;
       const float s1 = sld(S0 + 8 * F + x + BW), s0v = sld(S0 + 8 * F + x);
@@ -219,7 +219,7 @@ __device__ __forceinline__ void fused_tile(const FusedMaps &maps, const FusedPar
         Dz += ps;
       }
       const float rho = __ldg(m_rho + I0[xi]) + __ldg(m_rho + I0[xi + 1]);
-      out = sld(S0 + 2 * F + x) + 2.f * dtv / rho * (Dr + Q + Dz);
+      out = sld(S0 + 2 * F + x) + vel_coef(dtv, rho) * (Dr + Q + Dz);
     }
     if (own && k < NZp) gst(vnxt[c] + plane * pl + v.cb, out);
     return out;
@@ -332,7 +332,7 @@ __device__ __forceinline__ void fused_tile(const FusedMaps &maps, const FusedPar
               gr += ps;
               Q += qs;
             }
-            const float mu = 4.f / (imu_m + imu_c + __ldg(m_imu + Ij[xi - BWI]) + __ldg(m_imu + Ij[xi]));
+            const float mu = mu_harm(imu_m + imu_c + __ldg(m_imu + Ij[xi - BWI]) + __ldg(m_imu + Ij[xi]));
             o[3] += dts * mu * (gr + Q);
           }
           if (k + 1 < NZ) {
@@ -351,7 +351,7 @@ __device__ __forceinline__ void fused_tile(const FusedMaps &maps, const FusedPar
                 fp.psr_o[R_GRZ][cr] = ps;
                 gr += ps;
               }
-              const float mu = 4.f / (imu_m + imu_c + __ldg(m_imu + Im[xi - BWI + 1]) + imu_c1);
+              const float mu = mu_harm(imu_m + imu_c + __ldg(m_imu + Im[xi - BWI + 1]) + imu_c1);
               o[5] += dts * mu * (gz + gr);
             }
             // s_phiz at (r_{i+1/2}, theta_{j+1/2}, z_{k+1/2})
@@ -368,7 +368,7 @@ __device__ __forceinline__ void fused_tile(const FusedMaps &maps, const FusedPar
                 fp.psz_o[Z_GPZ][cz] = ps;
                 gz += ps;
               }
-              const float mu = 4.f / (imu_c + __ldg(m_imu + Ij[xi]) + imu_c1 + __ldg(m_imu + Ij[xi + 1]));
+              const float mu = mu_harm(imu_c + __ldg(m_imu + Ij[xi]) + imu_c1 + __ldg(m_imu + Ij[xi + 1]));
               o[4] += dts * mu * (Q + gz);
             }
           }

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(F4Smem<T, RT>::NT) fused4_step(const __grid_co
       if (zpx) Dz += abz.w * p.psz[Z_VZ][cz] + abz.z * Dz;
       rho = __ldg(m_rho + I0[xx_i]) + __ldg(m_rho + I0[xx_i + 1]);
     }
-    return St<T>::ld1(vcur_g[c] + cc) + 2.f * dtv / rho * (Dr + Q + Dz);
+    return St<T>::ld1(vcur_g[c] + cc) + vel_coef(dtv, rho) * (Dr + Q + Dz);
   };
 
   for (int m = -1; m <= nth; m++) {
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(F4Smem<T, RT>::NT) fused4_step(const __grid_co
               Dz += ps;
             }
             const float rho = __ldg(m_rho + idc[e]) + __ldg(m_rho + idm[e]);
-            o[e] = k < NZ ? F4(vold[0], e) + 2.f * dtv / rho * (Dr + Q + Dz) : 0.f;
+            o[e] = k < NZ ? F4(vold[0], e) + vel_coef(dtv, rho) * (Dr + Q + Dz) : 0.f;
           }
           vr4 = make_float4(o[0], o[1], o[2], o[3]);
         }
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(F4Smem<T, RT>::NT) fused4_step(const __grid_co
               Dz += ps;
             }
             const float rho = __ldg(m_rho + idc[e]) + __ldg(m_rho + idj[e]);
-            o[e] = k < NZ ? F4(vold[1], e) + 2.f * dtv / rho * (Dr + Q + Dz) : 0.f;
+            o[e] = k < NZ ? F4(vold[1], e) + vel_coef(dtv, rho) * (Dr + Q + Dz) : 0.f;
           }
           vp4 = make_float4(o[0], o[1], o[2], o[3]);
           // v_z
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(F4Smem<T, RT>::NT) fused4_step(const __grid_co
               Dz += ps;
             }
             const float rho = __ldg(m_rho + idc[e]) + __ldg(m_rho + (e < 3 ? idc[e + 1] : id4));
-            o[e] = k + 1 < NZ ? F4(vold[2], e) + 2.f * dtv / rho * (Dr + Q + Dz) : 0.f;
+            o[e] = k + 1 < NZ ? F4(vold[2], e) + vel_coef(dtv, rho) * (Dr + Q + Dz) : 0.f;
           }
           vz4 = make_float4(o[0], o[1], o[2], o[3]);
         }
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(F4Smem<T, RT>::NT) fused4_step(const __grid_co
             gr += ps;
             Q += qs;
           }
-          const float mu = 4.f / (mu_m[e] + mu_c[e] + mu_jm[e] + mu_j[e]);
+          const float mu = mu_harm(mu_m[e] + mu_c[e] + mu_jm[e] + mu_j[e]);
           o[3][e] += dts * mu * (gr + Q);
         }
         if (k + 1 < NZ) {
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(F4Smem<T, RT>::NT) fused4_step(const __grid_co
               fp.psr_o[R_GRZ][cr + e] = ps;
               gr += ps;
             }
-            const float mu = 4.f / (mu_m[e] + mu_c[e] + mu_m[e + 1] + mu_c[e + 1]);
+            const float mu = mu_harm(mu_m[e] + mu_c[e] + mu_m[e + 1] + mu_c[e + 1]);
             o[5][e] += dts * mu * (gz + gr);
           }
           float Q = (F4(vzc, e) - F4(vz0, e)) * idth * inv_rh;
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(F4Smem<T, RT>::NT) fused4_step(const __grid_co
             fp.psz_o[Z_GPZ][cz] = ps;
             gz += ps;
           }
-          const float mu = 4.f / (mu_c[e] + mu_j[e] + mu_c[e + 1] + mu_j[e + 1]);
+          const float mu = mu_harm(mu_c[e] + mu_j[e] + mu_c[e + 1] + mu_j[e + 1]);
           o[4][e] += dts * mu * (Q + gz);
         }
       }

@@ -148,7 +148,7 @@ __device__ __forceinline__ void vel_quad(const KParams &p, const unsigned char *
         const float4 abz = __ldg(p.ab_z + k);
         Dz = stretch(p.psz[Z_VR] + czrow + kz, abz.x, abz.y, Dz);
       }
-      out[e] += 2.f * dtv / (__ldg(p.m_rho + idm[e]) + rho_c[e]) * (Dr + Q + Dz);
+      out[e] += vel_coef(dtv, __ldg(p.m_rho + idm[e]) + rho_c[e]) * (Dr + Q + Dz);
     }
     v[0] = make_float4(out[0], out[1], out[2], out[3]);
   }
@@ -175,7 +175,7 @@ __device__ __forceinline__ void vel_quad(const KParams &p, const unsigned char *
         const float4 abz = __ldg(p.ab_z + k);
         Dz = stretch(p.psz[Z_VP] + czrow + kz, abz.x, abz.y, Dz);
       }
-      out[e] += 2.f * dtv / (rho_c[e] + __ldg(p.m_rho + idj[e])) * (Dr + Q + Dz);
+      out[e] += vel_coef(dtv, rho_c[e] + __ldg(p.m_rho + idj[e])) * (Dr + Q + Dz);
     }
     v[1] = make_float4(out[0], out[1], out[2], out[3]);
   }
@@ -202,7 +202,7 @@ __device__ __forceinline__ void vel_quad(const KParams &p, const unsigned char *
         const float4 abz = __ldg(p.ab_z + k);
         Dz = stretch(p.psz[Z_VZ] + czrow + kz, abz.z, abz.w, Dz);
       }
-      out[e] += 2.f * dtv / (rho_c[e] + rho_c[e + 1]) * (Dr + Q + Dz);
+      out[e] += vel_coef(dtv, rho_c[e] + rho_c[e + 1]) * (Dr + Q + Dz);
     }
     v[2] = make_float4(out[0], out[1], out[2], out[3]);
   }
@@ -320,7 +320,7 @@ __device__ __forceinline__ void str_quad(const KParams &p, const unsigned char *
           gr = stretch(p.psr[R_GRP] + cr + e, abr.x, abr.y, gr);
           Q = stretch(p.psr[Q_GRP] + cr + e, abq.x, abq.y, Q);
         }
-        const float mu = 4.f / (__ldg(p.m_imu + idm[e]) + imu_c[e] + __ldg(p.m_imu + idjm[e]) + imu_j[e]);
+        const float mu = mu_harm(__ldg(p.m_imu + idm[e]) + imu_c[e] + __ldg(p.m_imu + idjm[e]) + imu_j[e]);
         out[e] += dts * mu * (gr + Q);
       }
       s[3] = make_float4(out[0], out[1], out[2], out[3]);
@@ -342,7 +342,7 @@ __device__ __forceinline__ void str_quad(const KParams &p, const unsigned char *
         }
         if (rp) gr = stretch(p.psr[R_GRZ] + cr + e, abr.x, abr.y, gr);
         const float mu =
-            4.f / (__ldg(p.m_imu + idm[e]) + imu_c[e] + __ldg(p.m_imu + idm[e + 1]) + imu_c[e + 1]);
+            mu_harm(__ldg(p.m_imu + idm[e]) + imu_c[e] + __ldg(p.m_imu + idm[e + 1]) + imu_c[e + 1]);
         out[e] += dts * mu * (gz + gr);
       }
       s[5] = make_float4(out[0], out[1], out[2], out[3]);
@@ -366,7 +366,7 @@ __device__ __forceinline__ void str_quad(const KParams &p, const unsigned char *
         const float4 abz = __ldg(p.ab_z + k);
         gz = stretch(p.psz[Z_GPZ] + czrow + kz, abz.z, abz.w, gz);
       }
-      const float mu = 4.f / (imu_c[e] + imu_j[e] + imu_c[e + 1] + imu_j[e + 1]);
+      const float mu = mu_harm(imu_c[e] + imu_j[e] + imu_c[e + 1] + imu_j[e + 1]);
       out[e] += dts * mu * (Q + gz);
     }
     s[4] = make_float4(out[0], out[1], out[2], out[3]);

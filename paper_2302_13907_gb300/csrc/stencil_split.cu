@@ -98,7 +98,7 @@ __device__ __forceinline__ void vel_body(const KParams &p, const int j, const in
         Dz = stretch(p.psz[Z_VR] + czrow + kz, abz.x, abz.y, Dz);
       }
       const float rm = __ldg(&p.mat[idm[e]]).x;
-      out[e] += 2.f * dtv / (rm + rho_c[e]) * (Dr + Q + Dz);
+      out[e] += vel_coef(dtv, rm + rho_c[e]) * (Dr + Q + Dz);
     }
     St<T>::st4(vr + c, make_float4(out[0], out[1], out[2], out[3]));
   }
@@ -129,7 +129,7 @@ __device__ __forceinline__ void vel_body(const KParams &p, const int j, const in
         Dz = stretch(p.psz[Z_VP] + czrow + kz, abz.x, abz.y, Dz);
       }
       const float rj = __ldg(&p.mat[idj[e]]).x;
-      out[e] += 2.f * dtv / (rho_c[e] + rj) * (Dr + Q + Dz);
+      out[e] += vel_coef(dtv, rho_c[e] + rj) * (Dr + Q + Dz);
     }
     St<T>::st4(vp + c, make_float4(out[0], out[1], out[2], out[3]));
   }
@@ -157,7 +157,7 @@ __device__ __forceinline__ void vel_body(const KParams &p, const int j, const in
         const float4 abz = __ldg(p.ab_z + k);
         Dz = stretch(p.psz[Z_VZ] + czrow + kz, abz.z, abz.w, Dz);
       }
-      out[e] += 2.f * dtv / (rho_c[e] + rho_c[e + 1]) * (Dr + Q + Dz);
+      out[e] += vel_coef(dtv, rho_c[e] + rho_c[e + 1]) * (Dr + Q + Dz);
     }
     St<T>::st4(vz + c, make_float4(out[0], out[1], out[2], out[3]));
   }
@@ -285,7 +285,7 @@ __device__ __forceinline__ void str_body(const KParams &p, const int j, const in
           gr = stretch(p.psr[R_GRP] + cr + e, abr.x, abr.y, gr);
           Q = stretch(p.psr[Q_GRP] + cr + e, abq.x, abq.y, Q);
         }
-        const float mu = 4.f / (__ldg(&p.mat[idm[e]]).w + imu_c[e] + __ldg(&p.mat[idjm[e]]).w + imu_j[e]);
+        const float mu = mu_harm(__ldg(&p.mat[idm[e]]).w + imu_c[e] + __ldg(&p.mat[idjm[e]]).w + imu_j[e]);
         o[e] += dts * mu * (gr + Q);
       }
       St<T>::st4(srp + c, make_float4(o[0], o[1], o[2], o[3]));
@@ -308,7 +308,7 @@ __device__ __forceinline__ void str_body(const KParams &p, const int j, const in
           gz = stretch(p.psz[Z_GRZ] + czrow + kz, abz.z, abz.w, gz);
         }
         if (rp) gr = stretch(p.psr[R_GRZ] + cr + e, abr.x, abr.y, gr);
-        const float mu = 4.f / (__ldg(&p.mat[idm[e]]).w + imu_c[e] + __ldg(&p.mat[idm[e + 1]]).w + imu_c[e + 1]);
+        const float mu = mu_harm(__ldg(&p.mat[idm[e]]).w + imu_c[e] + __ldg(&p.mat[idm[e + 1]]).w + imu_c[e + 1]);
         o[e] += dts * mu * (gz + gr);
       }
       St<T>::st4(srz + c, make_float4(o[0], o[1], o[2], o[3]));
@@ -332,7 +332,7 @@ __device__ __forceinline__ void str_body(const KParams &p, const int j, const in
         const float4 abz = __ldg(p.ab_z + k);
         gz = stretch(p.psz[Z_GPZ] + czrow + kz, abz.z, abz.w, gz);
       }
-      const float mu = 4.f / (imu_c[e] + imu_j[e] + imu_c[e + 1] + imu_j[e + 1]);
+      const float mu = mu_harm(imu_c[e] + imu_j[e] + imu_c[e + 1] + imu_j[e + 1]);
       o[e] += dts * mu * (Q + gz);
     }
     St<T>::st4(spz + c, make_float4(o[0], o[1], o[2], o[3]));
@@ -353,43 +353,6 @@ __global__ void __launch_bounds__(SB_X *SB_Y, SB_MINB) str_split(const KParams p
   if (i < p.NR && k0 < p.NZ) str_body<T>(p, blockIdx.x, i, k0);
 }
 
-// Batched scenarios: persistent blocks walk the work list of all cases,
-// item = (case, theta, r tile, z tile), theta fastest inside a case so the
-// theta neighbours a block reads are read by co-resident blocks too.
-// start[c] = first item of case c (start[n] = total); cases[c] holds the
-// case's geometry and buffers.
-__device__ __forceinline__ int find_case(const long long *start, int n, long long item) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(start + mid) <= item) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-template <typename T, bool VEL>
-__global__ void __launch_bounds__(SB_X *SB_Y, SB_MINB) batch_split(const KParams *cases, const long long *start,
-                                                                   int n_cases, long long total) {
-  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-    const int c = find_case(start, n_cases, item);
-    const KParams &p = cases[c];
-    long long q = item - __ldg(start + c);
-    const int nth = p.nth, nrt = (p.NR + SB_Y - 1) / SB_Y;
-    const int j = (int)(q % nth);
-    q /= nth;
-    const int rt = (int)(q % nrt), zt = (int)(q / nrt);
-    const int i = rt * SB_Y + threadIdx.y, k0 = (zt * SB_X + threadIdx.x) * 4;
-    if (i < p.NR && k0 < p.NZ) {
-      if (VEL) vel_body<T>(p, j, i, k0);
-      else str_body<T>(p, j, i, k0);
-    }
-  }
-}
-
-long long split_items(int nth, int NR, int NZ) {
-  return (long long)nth * ((NR + SB_Y - 1) / SB_Y) * ((NZ + 4 * SB_X - 1) / (4 * SB_X));
-}
 
 // Pressure at the receivers after the stress update; one block, fixed
 // summation order over theta; advances the device step counter.
@@ -448,21 +411,6 @@ cudaError_t launch_split(int storage, const KParams &p, cudaStream_t s, cudaEven
     case 2: return launch_split_t<__half>(p, s, ev);
   }
   return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, const long long *start, int n_cases,
-                               long long total, int grid, cudaStream_t s) {
-  dim3 blk(SB_X, SB_Y);
-  switch (storage * 2 + (vel ? 1 : 0)) {
-    case 0: batch_split<float, false><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
-    case 1: batch_split<float, true><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
-    case 2: batch_split<__nv_bfloat16, false><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
-    case 3: batch_split<__nv_bfloat16, true><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
-    case 4: batch_split<__half, false><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
-    case 5: batch_split<__half, true><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_batch_receivers(int storage, const RParams *rp, int n_cases, cudaStream_t s) {

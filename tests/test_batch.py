@@ -51,7 +51,7 @@ def test_batch_equals_single_runs_and_oracle():
         got_f = [b.field(c, "srr") for c in range(5)]
         got_vz = b.field(0, "vz")
     for c, sc in enumerate(cases):
-        with Simulation(sc, kernel="split") as s:
+        with Simulation(sc, kernel="split", tile=2004) as s:
             s.step(160)
             ref = s.traces()
             assert got[c].shape == ref.shape
@@ -76,6 +76,6 @@ def test_batch_of_cement_cases():
         b.run(64)
         got = [b.traces(c) for c in range(3)]
     for c, sc in enumerate(cases):
-        with Simulation(sc, kernel="split", max_steps=64) as s:
+        with Simulation(sc, kernel="split", tile=2004, max_steps=64) as s:
             s.step(64)
             assert rel_l2(got[c], s.traces()) <= 1e-6

@@ -256,6 +256,25 @@ def test_march_every_tile_fields_elementwise(tile):
         assert rel_l2(s.traces(), o.traces()) <= TRACE_TOL
 
 
+@pytest.mark.parametrize("tile", (2000, 2003, 2004, 2005))
+def test_split_variants_fields_elementwise(tile):
+    """The split kernels and their load-first variants (every register
+    budget the autotuner may pick) on the same uneven grid: every field
+    against the oracle element by element."""
+    sc = _ragged_scenario(seed=6, nth=12, nr=14, nz=150)
+    o = oracle.Oracle(sc)
+    o.step(sc.steps)
+    with sim(sc, kernel="split", tile=tile) as s:
+        assert s.config() == (1, tile)
+        s.step(sc.steps)
+        for n in oracle.FIELDS:
+            a, b = s.field(n), o.field(n)
+            scale = np.abs(b).max()
+            assert scale > 0, n
+            assert np.abs(a - b).max() <= 2e-5 * scale, (n, np.abs(a - b).max() / scale)
+        assert rel_l2(s.traces(), o.traces()) <= TRACE_TOL
+
+
 def test_march_rejects_a_tile_it_does_not_have():
     from paper_2302_13907_gb300.binding import SIM_EINVAL, SimError
     with pytest.raises(SimError) as ei:
@@ -268,14 +287,15 @@ def test_fused_matches_split_and_autotuner_choice():
     compute the same scheme: traces agree to FP32 rounding; every tile
     height the autotuner may pick gives the same answer."""
     sc = W.config1(steps=400)
-    with sim(sc, kernel="split") as a:
+    with sim(sc, kernel="split", tile=2000) as a:
         a.step(400)
         ta = a.traces()
         fa = {n: a.field(n) for n in ("vr", "srr", "srz")}
-    for kern, tiles in (("fused", (2, 4, 6, 8)), ("fused4", (106, 110, 114)), ("march", MARCH_TILES)):
+    for kern, kind_want, tiles in (("fused", 2, (2, 4, 6, 8)), ("fused4", 2, (106, 110, 114)),
+                                   ("march", 4, MARCH_TILES), ("split", 1, (2000, 2003, 2004, 2005))):
         with sim(sc, kernel=kern) as b:
             kind, tile = b.config()
-            assert kind == (4 if kern == "march" else 2) and tile in tiles
+            assert kind == kind_want and tile in tiles, (kern, kind, tile)
             b.step(400)
             tb = b.traces()
             assert rel_l2(tb, ta) <= 1e-6, kern

@@ -45,16 +45,26 @@ def test_fp32_long_window_matches_oracle(crop):
     assert rel_l2(got, ref["traces"]) <= 1e-4
 
 
-@pytest.mark.parametrize("storage,bound", [("bf16", 0.5), ("f16", 0.1)])
-def test_reduced_storage_error_is_bounded(crop, storage, bound):
-    """BF16 / FP16 storage with FP32 arithmetic: the error against the FP64
-    oracle over 4000 steps stays below a loose bound (the per-receiver
-    figures are reported by precision_report)."""
+def test_reduced_storage_error_is_finite_and_ordered(crop):
+    """BF16 / FP16 storage with FP32 arithmetic over the whole 20000-step
+    window (the direct arrivals reach the receivers after about 4000 steps).
+    A step changes a field by roughly 2 pi / (steps per source period) of its
+    amplitude, about 0.2 % here, which is of the order of BF16's resolution
+    (2^-8) and a few times FP16's (2^-11): increments are partly rounded away,
+    so the error against the FP64 oracle is large, and larger for BF16 than
+    for FP16.  The test pins that ordering and loose bounds around the
+    measured values (BF16 about 0.7, FP16 about 0.13 relative L2);
+    precision_report gives the per-receiver figures."""
     from paper_2302_13907_gb300.binding import Simulation
     sc, ref = crop
-    n = 4000
-    with Simulation(sc, storage=storage, max_steps=n) as s:
-        s.step(n)
-        got = s.traces()
-    assert np.all(np.isfinite(got))
-    assert rel_l2(got, ref["traces"][:, :n]) <= bound
+    n = int(ref["steps"])
+    err = {}
+    for storage in ("bf16", "f16"):
+        with Simulation(sc, storage=storage, max_steps=n, graph_chunk=200) as s:
+            s.step(n)
+            got = s.traces()
+        assert np.all(np.isfinite(got)), storage
+        assert np.abs(got).max() > 0, storage
+        err[storage] = rel_l2(got, ref["traces"])
+    assert err["f16"] < err["bf16"], err
+    assert err["f16"] <= 0.3 and err["bf16"] <= 1.0, err
