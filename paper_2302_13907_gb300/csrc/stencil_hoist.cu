@@ -26,7 +26,9 @@ __device__ __forceinline__ uint2 ldid(const uint16_t *p) { return __ldg(reinterp
 
 #define E4(v, e) ((e) == 0 ? (v).x : (e) == 1 ? (v).y : (e) == 2 ? (v).z : (v).w)
 
-template <typename T>
+// LEAN: the four cells are interior (no PML memory variable, all inside NZ,
+// k0 + 4 < NZ); the kernels pick the lean body per thread.
+template <typename T, bool LEAN>
 __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, const int i, const int k0) {
   const int nth = p.nth, NR = p.NR, NZ = p.NZ;
   const long long NZp = p.NZp, pl = p.plane;
@@ -37,7 +39,7 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
   const T *srr = (const T *)p.f[F_SRR], *spp = (const T *)p.f[F_SPP], *szz = (const T *)p.f[F_SZZ];
   const T *srp = (const T *)p.f[F_SRP], *spz = (const T *)p.f[F_SPZ], *srz = (const T *)p.f[F_SRZ];
   T *vr = (T *)p.f[F_VR], *vp = (T *)p.f[F_VP], *vz = (T *)p.f[F_VZ];
-  const bool im = i >= 1, ip = i + 1 < NR, k4 = k0 + 4 < NZ, km = k0 > 0;
+  const bool im = i >= 1, ip = i + 1 < NR, k4 = LEAN || k0 + 4 < NZ, km = k0 > 0;
 
   // ---- every load
   const float4 a_srr = St<T>::ld4(srr + c), a_spp = St<T>::ld4(spp + c), a_srp = St<T>::ld4(srp + c);
@@ -52,7 +54,7 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
   const uint2 u_c = ldid(p.id + c), u_j = ldid(p.id + cjp), u_m = im ? ldid(p.id + c - NZp) : make_uint2(0, 0);
   int id_k4 = 0;
   if (k4) id_k4 = __ldg(p.id + c + 4);
-  const bool rp = i >= p.nr;
+  const bool rp = !LEAN && i >= p.nr;
   const float inv_ri = __ldg(p.inv_ri + i), inv_rh = __ldg(p.inv_rh + i);
   const float4 abr = __ldg(p.ab_r + i), abq = __ldg(p.ab_q + i);
 
@@ -74,7 +76,7 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
   const float dtv = p.dtv, idr = p.inv_dr, idz = p.inv_dz, idth = p.inv_dth;
   const int pz = p.pml_z;
   const long long czrow = ((long long)j * NR + i) * (2 * pz);
-  const bool zl = pz > 0 && (k0 < pz || k0 + 3 >= NZ - pz);
+  const bool zl = !LEAN && pz > 0 && (k0 < pz || k0 + 3 >= NZ - pz);
 
   float out_r[4], out_p[4], out_z[4];
 #pragma unroll
@@ -86,7 +88,7 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
 #pragma unroll
   for (int e = 0; e < 4; e++) {
     const int k = k0 + e;
-    if (k >= NZ) break;
+    if (!LEAN && k >= NZ) break;
     const bool zp = zl && (k < pz || k >= NZ - pz);
     const int kz = k < pz ? k : k - (NZ - 2 * pz);
     const float4 abz = zp ? __ldg(p.ab_z + k) : z4();
@@ -120,7 +122,7 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
       out_p[e] += vel_coef(dtv, rho_c[e] + rho_j[e]) * (Dr + Q + Dz);
     }
     // v_z at (r_{i+1/2}, theta_j, z_{k+1/2}), k + 1 < NZ
-    if (k + 1 < NZ) {
+    if (LEAN || k + 1 < NZ) {
       const float s1 = E4(p_srz, e);
       float Dr = (s1 - srz_e) * idr;
       float Q = (0.5f * (s1 + srz_e) + (spz_e - E4(jm_spz, e)) * idth) * inv_rh;
@@ -138,7 +140,7 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
   St<T>::st4(vz + c, make_float4(out_z[0], out_z[1], out_z[2], out_z[3]));
 }
 
-template <typename T>
+template <typename T, bool LEAN>
 __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, const int i, const int k0) {
   const int nth = p.nth, NR = p.NR, NZ = p.NZ;
   const long long NZp = p.NZp, pl = p.plane;
@@ -149,7 +151,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
   const T *vr = (const T *)p.f[F_VR], *vp = (const T *)p.f[F_VP], *vz = (const T *)p.f[F_VZ];
   T *srr = (T *)p.f[F_SRR], *spp = (T *)p.f[F_SPP], *szz = (T *)p.f[F_SZZ];
   T *srp = (T *)p.f[F_SRP], *spz = (T *)p.f[F_SPZ], *srz = (T *)p.f[F_SRZ];
-  const bool im = i >= 1, ip = i + 1 < NR, k4 = k0 + 4 < NZ, km = k0 > 0;
+  const bool im = i >= 1, ip = i + 1 < NR, k4 = LEAN || k0 + 4 < NZ, km = k0 > 0;
 
   // ---- every load
   const float4 a_vr = St<T>::ld4(vr + c), a_vp = St<T>::ld4(vp + c), a_vz = St<T>::ld4(vz + c);
@@ -169,7 +171,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
     idj4 = __ldg(p.id + cjp + 4);
     if (im) idm4 = __ldg(p.id + c - NZp + 4);
   }
-  const bool rp = i >= p.nr;
+  const bool rp = !LEAN && i >= p.nr;
   const float inv_ri = __ldg(p.inv_ri + i), inv_rh = __ldg(p.inv_rh + i);
   const float4 abr = __ldg(p.ab_r + i), abq = __ldg(p.ab_q + i);
   float src[4] = {0.f, 0.f, 0.f, 0.f};
@@ -206,7 +208,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
   const float dts = p.dts, idr = p.inv_dr, idz = p.inv_dz, idth = p.inv_dth;
   const int pz = p.pml_z;
   const long long czrow = ((long long)j * NR + i) * (2 * pz);
-  const bool zl = pz > 0 && (k0 < pz || k0 + 3 >= NZ - pz);
+  const bool zl = !LEAN && pz > 0 && (k0 < pz || k0 + 3 >= NZ - pz);
 
   float orr[4], opp[4], ozz[4], orp[4], opz[4], orz[4];
 #pragma unroll
@@ -221,7 +223,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
 #pragma unroll
   for (int e = 0; e < 4; e++) {
     const int k = k0 + e;
-    if (k >= NZ) break;
+    if (!LEAN && k >= NZ) break;
     const bool zp = zl && (k < pz || k >= NZ - pz);
     const int kz = k < pz ? k : k - (NZ - 2 * pz);
     const float4 abz = zp ? __ldg(p.ab_z + k) : z4();
@@ -257,7 +259,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
         orp[e] += dts * mu * (gr + Q);
       }
       // s_rz at (r_i, theta_j, z_{k+1/2})
-      if (k + 1 < NZ) {
+      if (LEAN || k + 1 < NZ) {
         float gz = (vr_e1 - vr_e) * idz;
         float gr = (vz_e - E4(m_vz, e)) * idr;
         if (zp) gz = stretch(p.psz[Z_GRZ] + czrow + kz, abz.z, abz.w, gz);
@@ -267,7 +269,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
       }
     }
     // s_phiz at (r_{i+1/2}, theta_{j+1/2}, z_{k+1/2})
-    if (k + 1 < NZ) {
+    if (LEAN || k + 1 < NZ) {
       float Q = (E4(jp_vz, e) - vz_e) * idth * inv_rh;
       float gz = (vp_e1 - vp_e) * idz;
       if (rp) Q = stretch(p.psr[Q_GPZ] + cr + e, abq.z, abq.w, Q);
@@ -286,16 +288,31 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
   St<T>::st4(spz + c, make_float4(opz[0], opz[1], opz[2], opz[3]));
 }
 
+__device__ __forceinline__ bool lean_quad(const KParams &p, int i, int k0) {
+  return i < p.nr && k0 >= p.pml_z && k0 + 4 < p.NZ - p.pml_z;
+}
+
+template <typename T, bool VEL>
+__device__ __forceinline__ void hoist_quad(const KParams &p, int j, int i, int k0) {
+  if (lean_quad(p, i, k0)) {
+    if (VEL) vel_hoist_body<T, true>(p, j, i, k0);
+    else str_hoist_body<T, true>(p, j, i, k0);
+  } else {
+    if (VEL) vel_hoist_body<T, false>(p, j, i, k0);
+    else str_hoist_body<T, false>(p, j, i, k0);
+  }
+}
+
 template <typename T, int MINB>
 __global__ void __launch_bounds__(HB_X *HB_Y, MINB) vel_hoist(const KParams p) {
   const int i = blockIdx.y * HB_Y + threadIdx.y, k0 = (blockIdx.z * HB_X + threadIdx.x) * 4;
-  if (i < p.NR && k0 < p.NZ) vel_hoist_body<T>(p, blockIdx.x, i, k0);
+  if (i < p.NR && k0 < p.NZ) hoist_quad<T, true>(p, blockIdx.x, i, k0);
 }
 
 template <typename T, int MINB>
 __global__ void __launch_bounds__(HB_X *HB_Y, MINB) str_hoist(const KParams p) {
   const int i = blockIdx.y * HB_Y + threadIdx.y, k0 = (blockIdx.z * HB_X + threadIdx.x) * 4;
-  if (i < p.NR && k0 < p.NZ) str_hoist_body<T>(p, blockIdx.x, i, k0);
+  if (i < p.NR && k0 < p.NZ) hoist_quad<T, false>(p, blockIdx.x, i, k0);
 }
 
 // Batched scenarios: the blocks walk the work list of all cases, item =
@@ -324,10 +341,7 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) batch_hoist(const KParams *c
     const int j = q % nth;
     q /= nth;
     const int i = (q % nrt) * HB_Y + threadIdx.y, k0 = ((q / nrt) * HB_X + threadIdx.x) * 4;
-    if (i < p.NR && k0 < p.NZ) {
-      if (VEL) vel_hoist_body<T>(p, j, i, k0);
-      else str_hoist_body<T>(p, j, i, k0);
-    }
+    if (i < p.NR && k0 < p.NZ) hoist_quad<T, VEL>(p, j, i, k0);
   }
 }
 
