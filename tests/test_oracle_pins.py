@@ -6,8 +6,10 @@ the analytic cylindrical operators of Eq. 1 applied to smooth fields, the
 exact discrete energy invariant of the staggered scheme, the azimuthal
 symmetry of an axisymmetric problem, the liquid invariant (mu = 0, Sec. 2),
 the point-source closed form in a homogeneous liquid and its second-order
-convergence, the low-frequency tube-wave speed of an open hole, and the PML's
-reflected-energy bound.
+convergence, second-order convergence in a solid under refinement by three,
+the discrete stability limit (power iteration) against the CFL formula, the
+low-frequency tube-wave speed of an open hole, and the PML's reflected-energy
+bound.
 """
 import math
 
@@ -467,3 +469,98 @@ def test_pml_long_run_is_stable():
             assert peaks[-1] < 1e-4 * peaks[0], peaks
         else:
             assert peaks[10:].max() <= peaks[:10].max(), peaks
+
+
+# ---------------------------------------------------------------- convergence in a solid (Eq. 1, Sec. 3)
+def _ring_pulse_run(f, h0=0.01, n0=16, dt0=None):
+    """Axisymmetric smooth pulse in a homogeneous solid (liquid ring 0, never
+    reached in the window), rigid walls, no source; grid h0 / f, dt0 / f, n0 f
+    steps.  Returns the stresses at the final (integer) time and dt0."""
+    h = h0 / f
+    g = W.Grid(nr=30 * f, nth=4, nz=36 * f, pml_r=0, pml_z=0, dr=h, dz=h)
+    cid = np.ones(g.shape, dtype=np.uint16)
+    cid[:, 0, :] = 0
+    med = W.Medium(g, cid, np.array([1000.0, 2400.0]), np.array([1500.0, 4000.0]), np.array([0.0, 2300.0]))
+    sc = W.Scenario("conv", med, W.Source(z=0.05, amplitude=0.0), W.on_axis_receivers([0.05]), steps=0,
+                    pml_on=False)
+    if dt0 is None:
+        dt0 = oracle.cfl_dt(W.Medium(W.Grid(nr=30, nth=4, nz=36, pml_r=0, pml_z=0, dr=h0, dz=h0),
+                                     np.ones((4, 30, 36), np.uint16), med.rho, med.vp, med.vs), 0.5)
+    o = oracle.Oracle(sc, max_steps=0, dt=dt0 / f, pml_on=False)
+    r0, z0, s = 0.15, 0.18, 0.025
+    rh = (np.arange(g.NR) + 0.5) * h   # cell-centre radius
+    ri = np.arange(g.NR) * h           # integer-node radius
+    zc = np.arange(g.NZ) * h           # cell-centre depth
+    zh = (np.arange(g.NZ) + 0.5) * h   # half-node depth
+    G = lambda r, z: np.exp(-((r[:, None] - r0) ** 2 + (z[None, :] - z0) ** 2) / (2 * s * s))
+    # a velocity field at rest stresses (so dv/dt = 0 at t = 0 and v(-dt/2) = v(0) + O(dt^2)),
+    # mixing radial and vertical motion so that both P and S terms act
+    vr = G(ri, zc) * (zc[None, :] - z0) / s
+    vz = G(rh, zh) * (rh[:, None] - r0) / s
+    vr[0, :] = 0.0
+    vz[:, -1] = 0.0
+    o.field("vr")[:] = vr[None]
+    o.field("vz")[:] = vz[None]
+    o.step(n0 * f)
+    return {n: o.field(n)[0].copy() for n in ("srr", "spp", "szz", "srz")}, dt0
+
+
+def test_solid_refinement_by_three_is_second_order():
+    """Refinement ratio 3 (the staggered nodes of h/3 contain those of h):
+    log3(|u_h - u_h/3| / |u_h/3 - u_h/9|) = 2 +- 0.3 on the stresses at the
+    nodes the three grids share, at the same time (fixed dt / h)."""
+    u1, dt0 = _ring_pulse_run(1)
+    u3, _ = _ring_pulse_run(3, dt0=dt0)
+    u9, _ = _ring_pulse_run(9, dt0=dt0)
+
+    def restrict(u, f, name):
+        # coarse node (i, k) of a cell-centre radius / integer depth field sits at (f i + (f-1)/2, f k)
+        oi = (f - 1) // 2 if name in ("srr", "spp", "szz") else 0
+        ok = (f - 1) // 2 if name == "srz" else 0
+        return u[oi::f, ok::f][:30, :36]
+
+    e1 = e2 = 0.0
+    for n in ("srr", "spp", "szz", "srz"):
+        a, b, c = u1[n], restrict(u3[n], 3, n), restrict(u9[n], 9, n)
+        e1 += np.sum((a - b) ** 2)
+        e2 += np.sum((b - c) ** 2)
+    order = math.log(math.sqrt(e1 / e2), 3)
+    assert abs(order - 2.0) <= 0.3, order
+
+
+# ---------------------------------------------------------------- stability limit (power iteration)
+def test_cfl_formula_is_inside_the_discrete_stability_limit():
+    """The leapfrog step is stable iff dt <= 2 / sqrt(lambda_max) of the
+    operator v -> -(velocity update of the stress update of v) per unit dt^2.
+    Power iteration on the oracle's own half-steps (dt = 1, PML off, stresses
+    reset to zero) estimates lambda_max on the 70 x 16 x 320 cased well; the
+    CFL 0.5 formula's dt must sit below 0.6 of that limit."""
+    sc = W.config1(steps=0)
+    o = oracle.Oracle(sc, max_steps=0, dt=1.0, pml_on=False)
+    dt_formula = oracle.cfl_dt(sc.medium, 0.5)
+    rng = np.random.default_rng(1)
+    x = {n: rng.standard_normal(sc.grid.shape) for n in ("vr", "vp", "vz")}
+    x["vr"][:, 0, :] = 0.0
+    x["vz"][:, :, -1] = 0.0
+    lam = 0.0
+    for it in range(150):
+        nrm = math.sqrt(sum(np.sum(a * a) for a in x.values()))
+        for n in x:
+            x[n] /= nrm
+        for n in ("srr", "spp", "szz", "srp", "spz", "srz"):
+            o.field(n)[:] = 0.0
+        for n in x:
+            o.field(n)[:] = 0.0
+        # stress from v = x, then the velocity that stress drives from v = 0
+        for n in x:
+            o.field(n)[:] = x[n]
+        o.stress_update()
+        for n in x:
+            o.field(n)[:] = 0.0
+        o.velocity_update()
+        y = {n: -o.field(n).copy() for n in x}
+        lam = sum(np.sum(y[n] * x[n]) for n in x)  # Rayleigh quotient (x normalised)
+        x = y
+    dt_crit = 2.0 / math.sqrt(lam)
+    assert lam > 0
+    assert dt_formula <= 0.6 * dt_crit, (dt_formula, dt_crit)
