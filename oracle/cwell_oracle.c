@@ -64,6 +64,20 @@
  *      Outside the PML the walls are rigid.
  *  R9  closed walls: v_r = s_rphi = s_rz = 0 at r = NR dr; v_z = s_rz =
  *      s_phiz = 0 at the z half-nodes -1/2 and NZ - 1/2; theta periodic.
+ *  R12 point forces (the paper's transverse and longitudinal point impacts,
+ *      F = (1,0,0) f and (0,0,1) f; the printed normalisation is singular in
+ *      a liquid): v += dt * A f(t_n) / (rho_node * V_node) after the velocity
+ *      half-step, t_n = n dt, rho_node the two-cell mean of R5.  Longitudinal
+ *      on the axis: every ring-0 v_z node, V = pi dr^2 dz (as R6).
+ *      Transverse on the axis (a horizontal force in direction phi0): the
+ *      ring-1 v_r nodes, each with the share 2 cos(theta_j - phi0) / Ntheta
+ *      of the force, V = dr^2 dphi dz, so that the momentum put in along phi0
+ *      is dt A f.  Off the axis: the nearest v_r (v_z) node, V = r dr dphi dz.
+ *  R13 torsion source (printed G = (0,0,0,1,1,0) f): an axisymmetric torque
+ *      about the well axis, s_rphi and s_phiz += dt * A f(t_{n+1/2}) /
+ *      (2 pi r dr dz) on every theta node of the ring at r0 (s_rphi at
+ *      r_i = i dr, i = round(r0 / dr); s_phiz at r_{i'+1/2}, i' = floor(r0 /
+ *      dr)); both nodes must have a non-zero shear modulus.
  */
 #include <math.h>
 #include <stdint.h>
@@ -99,9 +113,11 @@ typedef struct {
   /* 1-D PML coefficients: r at integer / half nodes (radial difference and
      1/r group), z at integer / half nodes */
   double *ar_i, *br_i, *ar_h, *br_h, *aq_i, *bq_i, *aq_h, *bq_h, *az_i, *bz_i, *az_h, *bz_h;
-  /* source */
-  int src_kind, src_i, src_j, src_k; /* src_j = -1: all ring-0 nodes */
-  double src_amp, src_delta;
+  /* source: injection points (field, cell, weight per unit f(t)) */
+  int src_kind, src_n;
+  int *src_field;
+  size_t *src_cell;
+  double *src_w;
   /* receivers */
   int n_rec, *rec_i, *rec_j, *rec_k; /* rec_j = -1: mean over ring 0 */
   int cap, steps_done;
@@ -169,8 +185,21 @@ void or_destroy(or_sim *s) {
   free(s->aq_i); free(s->bq_i); free(s->aq_h); free(s->bq_h);
   free(s->az_i); free(s->bz_i); free(s->az_h); free(s->bz_h);
   free(s->rec_i); free(s->rec_j); free(s->rec_k);
+  free(s->src_field); free(s->src_cell); free(s->src_w);
   free(s->traces);
   free(s);
+}
+
+#define IX(j, i, k) (((size_t)(j) * NR + (i)) * NZ + (k))
+
+/* R5 averages */
+static inline double rho_avg2(const or_sim *s, size_t c1, size_t c2) {
+  return 0.5 * (s->rho[s->id[c1]] + s->rho[s->id[c2]]);
+}
+static inline double mu_harm4(const or_sim *s, size_t c1, size_t c2, size_t c3, size_t c4) {
+  double m1 = s->mu[s->id[c1]], m2 = s->mu[s->id[c2]], m3 = s->mu[s->id[c3]], m4 = s->mu[s->id[c4]];
+  if (m1 == 0.0 || m2 == 0.0 || m3 == 0.0 || m4 == 0.0) return 0.0;
+  return 4.0 / (1.0 / m1 + 1.0 / m2 + 1.0 / m3 + 1.0 / m4);
 }
 
 /*
@@ -185,7 +214,7 @@ or_sim *or_create(int nr, int nth, int nz, int pml_r, int pml_z, double dr, doub
                   int max_steps, int *err) {
   *err = OR_EINVAL;
   if (nr < 1 || nth < 4 || (nth & 1) || nz < 2 || pml_r < 0 || pml_z < 0 || !(dr > 0) || !(dz > 0) ||
-      n_mat < 1 || n_rec < 0 || max_steps < 0 || src_kind != 0)
+      n_mat < 1 || n_rec < 0 || max_steps < 0 || src_kind < 0 || src_kind > 3)
     return NULL;
   or_sim *s = (or_sim *)calloc(1, sizeof(or_sim));
   if (!s) { *err = OR_ENOMEM; return NULL; }
@@ -268,18 +297,64 @@ or_sim *or_create(int nr, int nth, int nz, int pml_r, int pml_z, double dr, doub
     cpml_ab(pml_d(xh, Lz, d0z), al, s->dt, &s->az_h[k], &s->bz_h[k]);
   }
 
-  /* R6: source node(s) */
+  /* R6, R12, R13: source injection points */
   s->src_kind = src_kind;
-  s->src_amp = src_amp;
-  s->src_k = (int)lround(src_z / dz) + pml_z;
-  if (s->src_k < pml_z || s->src_k >= pml_z + nz || src_r < 0 || src_r >= nr * dr) { or_destroy(s); return NULL; }
-  if (src_r < dr) {
-    s->src_i = 0; s->src_j = -1;
-    s->src_delta = 1.0 / (M_PI * dr * dr * dz);
-  } else {
-    s->src_i = (int)floor(src_r / dr);
-    s->src_j = (int)(((long)lround(src_theta / s->dth) % nth + nth) % nth);
-    s->src_delta = 1.0 / ((s->src_i + 0.5) * dr * dr * s->dth * dz);
+  {
+    const int k = (int)lround(src_z / dz) + pml_z;
+    if (k < pml_z || k >= pml_z + nz || src_r < 0 || src_r >= nr * dr) { or_destroy(s); return NULL; }
+    const int axis = src_r < dr;
+    const int js = (int)(((long)lround(src_theta / s->dth) % nth + nth) % nth);
+    const double dth = s->dth;
+    s->src_field = malloc(2 * nth * sizeof(int));
+    s->src_cell = malloc(2 * nth * sizeof(size_t));
+    s->src_w = malloc(2 * nth * sizeof(double));
+    if (!s->src_field || !s->src_cell || !s->src_w) { or_destroy(s); *err = OR_ENOMEM; return NULL; }
+    int n = 0, bad = 0;
+#define ADD(fld, cell, w) (s->src_field[n] = (fld), s->src_cell[n] = (cell), s->src_w[n] = (w), n++)
+    if (src_kind == 0) { /* volumetric, R6: the three normal stresses */
+      if (axis) {
+        for (int j = 0; j < nth; j++) ADD(F_SRR, IX(j, 0, k), src_amp / (M_PI * dr * dr * dz));
+      } else {
+        const int i = (int)floor(src_r / dr);
+        ADD(F_SRR, IX(js, i, k), src_amp / ((i + 0.5) * dr * dr * dth * dz));
+      }
+    } else if (src_kind == 1) { /* transverse point force, R12 */
+      if (axis) {
+        if (NR < 2) bad = 1;
+        for (int j = 0; j < nth && !bad; j++) {
+          const double w = 2.0 * cos(j * dth - src_theta) / nth;
+          ADD(F_VR, IX(j, 1, k), src_amp * w / (rho_avg2(s, IX(j, 0, k), IX(j, 1, k)) * dr * dr * dth * dz));
+        }
+      } else {
+        const int i = (int)lround(src_r / dr);
+        if (i < 1 || i >= NR) bad = 1;
+        else ADD(F_VR, IX(js, i, k), src_amp / (rho_avg2(s, IX(js, i - 1, k), IX(js, i, k)) * i * dr * dr * dth * dz));
+      }
+    } else if (src_kind == 2) { /* longitudinal point force, R12 */
+      if (k + 1 >= NZ) bad = 1;
+      else if (axis) {
+        for (int j = 0; j < nth; j++)
+          ADD(F_VZ, IX(j, 0, k), src_amp / (rho_avg2(s, IX(j, 0, k), IX(j, 0, k + 1)) * M_PI * dr * dr * dz));
+      } else {
+        const int i = (int)floor(src_r / dr);
+        ADD(F_VZ, IX(js, i, k), src_amp / (rho_avg2(s, IX(js, i, k), IX(js, i, k + 1)) * (i + 0.5) * dr * dr * dth * dz));
+      }
+    } else { /* torsion ring, R13 */
+      const int i = (int)lround(src_r / dr), ih = (int)floor(src_r / dr);
+      if (i < 1 || i >= NR || ih + 1 > NR || k + 1 >= NZ) bad = 1;
+      for (int j = 0; j < nth && !bad; j++) {
+        const int jp = (j + 1) % nth;
+        if (mu_harm4(s, IX(j, i - 1, k), IX(j, i, k), IX(jp, i - 1, k), IX(jp, i, k)) == 0.0 ||
+            mu_harm4(s, IX(j, ih, k), IX(jp, ih, k), IX(j, ih, k + 1), IX(jp, ih, k + 1)) == 0.0) {
+          or_destroy(s); *err = OR_EUNSUPPORTED; return NULL;
+        }
+        ADD(F_SRP, IX(j, i, k), src_amp / (2.0 * M_PI * i * dr * dr * dz));
+        ADD(F_SPZ, IX(j, ih, k), src_amp / (2.0 * M_PI * (ih + 0.5) * dr * dr * dz));
+      }
+    }
+#undef ADD
+    if (bad) { or_destroy(s); return NULL; }
+    s->src_n = n;
   }
   for (int n = 0; n < n_rec; n++) {
     s->rec_k[n] = (int)lround(rec_z[n] / dz) + pml_z;
@@ -296,17 +371,6 @@ or_sim *or_create(int nr, int nth, int nz, int pml_r, int pml_z, double dr, doub
   return s;
 }
 
-#define IX(j, i, k) (((size_t)(j) * NR + (i)) * NZ + (k))
-
-/* R5 averages */
-static inline double rho_avg2(const or_sim *s, size_t c1, size_t c2) {
-  return 0.5 * (s->rho[s->id[c1]] + s->rho[s->id[c2]]);
-}
-static inline double mu_harm4(const or_sim *s, size_t c1, size_t c2, size_t c3, size_t c4) {
-  double m1 = s->mu[s->id[c1]], m2 = s->mu[s->id[c2]], m3 = s->mu[s->id[c3]], m4 = s->mu[s->id[c4]];
-  if (m1 == 0.0 || m2 == 0.0 || m3 == 0.0 || m4 == 0.0) return 0.0;
-  return 4.0 / (1.0 / m1 + 1.0 / m2 + 1.0 / m3 + 1.0 / m4);
-}
 
 /* stretch a difference D with its memory variable psi (R8) */
 static inline double stretch(int on, double *psi, double a, double b, double D) {
@@ -445,17 +509,23 @@ void or_stress_update(or_sim *s) {
     }
 }
 
-/* Volumetric source at t_{n+1/2} (Sec. 2, R6). */
+/* Source of step n (Sec. 2, R6, R12, R13): point forces (kinds 1, 2) act on
+   the velocities with f(t_n) after the velocity half-step; the volumetric
+   source (kind 0, all three normal stresses) and the torsion ring (kind 3)
+   on the stresses with f(t_{n+1/2}) after the stress half-step. */
 void or_inject_source(or_sim *s, int n) {
-  const int NR = s->NR, NZ = s->NZ;
-  double t = (n + 0.5) * s->dt;
-  double add = s->dt * s->src_amp * or_ricker(t, s->f0) * s->src_delta;
-  int j0 = s->src_j < 0 ? 0 : s->src_j, j1 = s->src_j < 0 ? s->nth : s->src_j + 1;
-  for (int j = j0; j < j1; j++) {
-    size_t c = IX(j, s->src_i, s->src_k);
-    s->f[F_SRR][c] += add;
-    s->f[F_SPP][c] += add;
-    s->f[F_SZZ][c] += add;
+  const int force = s->src_kind == 1 || s->src_kind == 2;
+  const double f = or_ricker((force ? n : n + 0.5) * s->dt, s->f0);
+  for (int q = 0; q < s->src_n; q++) {
+    const double add = s->dt * s->src_w[q] * f;
+    const size_t c = s->src_cell[q];
+    if (s->src_kind == 0) {
+      s->f[F_SRR][c] += add;
+      s->f[F_SPP][c] += add;
+      s->f[F_SZZ][c] += add;
+    } else {
+      s->f[s->src_field[q]][c] += add;
+    }
   }
 }
 
@@ -478,9 +548,11 @@ int or_step(or_sim *s, int n) {
   if (!s || n < 0) return OR_EINVAL;
   for (int q = 0; q < n; q++) {
     int m = s->steps_done;
+    const int force = s->src_kind == 1 || s->src_kind == 2;
     or_velocity_update(s);
+    if (force) or_inject_source(s, m);
     or_stress_update(s);
-    or_inject_source(s, m);
+    if (!force) or_inject_source(s, m);
     or_sample(s, m);
     s->steps_done++;
   }

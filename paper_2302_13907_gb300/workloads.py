@@ -34,6 +34,9 @@ CEMENT = (1900.0, 3000.0, 1700.0)
 ROCK = (2400.0, 4000.0, 2300.0)
 
 SOURCE_MONOPOLE = 0  # volumetric point source (Sec. 2, first source type)
+SOURCE_TRANSVERSE = 1  # point force in the radial / horizontal direction (second type)
+SOURCE_LONGITUDINAL = 2  # point force along z (third type)
+SOURCE_TORSION = 3  # torsion ring about the well axis (fourth type)
 QUANTITY_PRESSURE = 0
 
 

@@ -564,3 +564,112 @@ def test_cfl_formula_is_inside_the_discrete_stability_limit():
     dt_crit = 2.0 / math.sqrt(lam)
     assert lam > 0
     assert dt_formula <= 0.6 * dt_crit, (dt_formula, dt_crit)
+
+
+# ------------------------------------------- point forces and torsion (R12, R13)
+def _force_field(c, rho, A, f0, cos_t, R, t):
+    """Pressure of a point force A f(t) in a homogeneous liquid at distance R,
+    cos_t = cosine between the force and the direction to the receiver:
+    p = cos_t / (4 pi) [A f'(t - R/c) / (c R) + A f(t - R/c) / R^2]."""
+    tau = t - R / c - 2.0 / f0
+    a = (math.pi * f0 * tau) ** 2
+    f = (1 - 2 * a) * np.exp(-a)
+    fp = 2 * math.pi ** 2 * f0 ** 2 * tau * (2 * a - 3) * np.exp(-a)
+    return cos_t / (4 * math.pi) * A * (fp / (c * R) + f / R ** 2), tau
+
+
+def test_longitudinal_force_closed_form_and_antisymmetry():
+    """Point force along z on the axis of a homogeneous liquid (R12): the
+    axis pressure above and below the force follows the dipole closed form
+    (opposite signs) within the scheme's second-order phase error."""
+    h, f0, c, rho = 0.002, 10e3, 1500.0, 1000.0
+    g = W.Grid(nr=150, nth=4, nz=350, pml_r=10, pml_z=10, dr=h, dz=h)
+    med = W.homogeneous(g, (rho, c, 0.0))
+    zs = 0.3
+    ks = int(round(zs / h))
+    z_force = (ks + 0.5) * h  # the v_z node the force acts on
+    zr = np.array([zs + 0.2, zs + 0.3, zs - 0.2])
+    sc = W.Scenario("fz", med, W.Source(kind=W.SOURCE_LONGITUDINAL, z=zs, f0=f0), W.on_axis_receivers(zr),
+                    cfl=0.5, steps=0)
+    dt = oracle.Oracle(sc, max_steps=1).dt
+    n = int(math.ceil((2.0 / f0 + 0.32 / c + 1.6 / f0) / dt))
+    o = oracle.Oracle(sc, max_steps=n)
+    o.step(n)
+    p = o.traces()
+    t = (np.arange(n) + 1) * dt
+    for q, z in enumerate(zr):
+        zc = round(z / h) * h
+        R = abs(zc - z_force)
+        exact, tau = _force_field(c, rho, 1.0, f0, np.sign(zc - z_force), R, t)
+        win = np.abs(tau) < 1.5 / f0
+        assert rel_l2(p[q, win], exact[win]) < 0.03, (z, rel_l2(p[q, win], exact[win]))
+
+
+def test_transverse_force_is_a_dipole():
+    """Horizontal point force on the axis (R12): the ring-mean (axis)
+    pressure vanishes, the field at theta and theta + pi is exactly opposite,
+    and off-axis pressure in the source plane follows the dipole closed form
+    with cos(theta - phi0)."""
+    h, f0, c, rho = 0.004, 5e3, 1500.0, 1000.0
+    nth = 16
+    g = W.Grid(nr=60, nth=nth, nz=120, pml_r=10, pml_z=10, dr=h, dz=h)
+    med = W.homogeneous(g, (rho, c, 0.0))
+    zs, phi0 = 0.24, 2 * math.pi * 3 / nth
+    r_rec = (30 + 0.5) * h
+    th = np.array([phi0, phi0 + math.pi, phi0 + math.pi / 2, 0.0])
+    rec = W.Receivers(r=np.array([r_rec] * 4 + [0.0]), theta=np.append(th, 0.0), z=np.array([zs] * 5))
+    sc = W.Scenario("fx", med, W.Source(kind=W.SOURCE_TRANSVERSE, theta=phi0, z=zs, f0=f0), rec, cfl=0.5, steps=0)
+    dt = oracle.Oracle(sc, max_steps=1).dt
+    n = int(math.ceil((2.0 / f0 + r_rec / c + 1.6 / f0) / dt))
+    o = oracle.Oracle(sc, max_steps=n)
+    o.step(n)
+    p = o.traces()
+    peak = np.abs(p[0]).max()
+    assert peak > 0
+    assert np.abs(p[0] + p[1]).max() <= 1e-12 * peak      # theta + pi: opposite
+    assert np.abs(p[2]).max() <= 1e-12 * peak              # perpendicular: zero
+    assert np.abs(p[4]).max() <= 1e-12 * peak              # axis (ring mean): zero
+    t = (np.arange(n) + 1) * dt
+    exact, tau = _force_field(c, rho, 1.0, f0, math.cos(0.0 - phi0), r_rec, t)
+    win = np.abs(tau) < 1.5 / f0
+    assert rel_l2(p[3, win], exact[win]) < 0.05, rel_l2(p[3, win], exact[win])
+
+
+def test_torsion_ring_in_a_free_pipe():
+    """Torsion ring in the wall of a free steel pipe (liquid inside and
+    outside, R13): the motion is pure SH (v_phi, s_rphi, s_phiz only, theta
+    independent), the liquid stays exactly at rest, and the torsional pulse
+    runs along the pipe at the steel's shear speed (the T(0,1) mode of a
+    free tube is non-dispersive)."""
+    dr, dz, f0 = 0.0025, 0.005, 10e3
+    g = W.Grid(nr=60, nth=4, nz=360, pml_r=8, pml_z=12, dr=dr, dz=dz)
+    med = W.layered_radial(g, [0.10, 0.11], [W.FLUID, W.STEEL, W.FLUID])
+    zs = 0.3
+    sc = W.Scenario("tor", med, W.Source(kind=W.SOURCE_TORSION, r=0.105, z=zs, f0=f0), W.on_axis_receivers([zs]),
+                    cfl=0.5, steps=0)
+    o = oracle.Oracle(sc, max_steps=0)
+    dt = o.dt
+    z1, z2 = zs + 0.4, zs + 1.2
+    k1, k2 = int(round(z1 / dz)) + 12, int(round(z2 / dz)) + 12
+    i_w = int(0.105 / dr)  # cell inside the wall
+    vs = W.STEEL[2]
+    n = int(math.ceil((2.0 / f0 + (z2 - zs) / vs + 1.5 / f0) / dt))
+    s1, s2 = np.zeros(n), np.zeros(n)
+    for m in range(n):
+        o.step(1)
+        vp = o.field("vp")
+        s1[m], s2[m] = vp[0, i_w, k1], vp[0, i_w, k2]
+    fl = np.zeros(g.shape, dtype=bool)
+    rc = g.r_centre()
+    fl[:, (rc < 0.10) | (rc >= 0.11), :] = True
+    for name in ("vr", "vz", "srr", "spp", "szz", "srz"):
+        assert np.all(o.field(name) == 0.0), name
+    vpf = o.field("vp")
+    assert np.abs(vpf).max() > 0
+    assert np.all(vpf[:, :i_w - 3, :] == 0.0) and np.all(vpf[:, i_w + 4:, :] == 0.0)  # liquid at rest
+    assert np.all(vpf == vpf[:1])  # theta independent
+    # moveout between the two stations (peak of the envelope by cross-correlation)
+    cc = np.correlate(s2, s1, mode="full")
+    lag = (np.argmax(cc) - (n - 1)) * dt
+    v = (z2 - z1) / lag
+    assert v == pytest.approx(vs, rel=0.02), v
