@@ -51,8 +51,10 @@ def _peaks():
 
 
 def kernel_hash() -> str:
+    """Hash of the stencil sources (the kernels the stored DRAM traffic was captured on)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2302_13907_gb300", "csrc", "*"))):
+    csrc = os.path.join(ROOT, "paper_2302_13907_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "stencil_*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
         h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
@@ -247,6 +249,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=200, help="leapfrog steps per bench step")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused", "fused4", "march"])
+    ap.add_argument("--tile", type=int, default=0, help="tile code to force (0: the autotuner picks)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nz", type=int, default=8192, help="interior z cells (8192 = the 20 m well; smaller for profiling)")
@@ -288,7 +291,7 @@ def main():
         uuid = None
 
     # ---------------- headline: device-resident, graph replays of T steps
-    sim = Simulation(sc, storage=args.storage, kernel=args.kernel, graph_chunk=T, stream=stream.cuda_stream,
+    sim = Simulation(sc, storage=args.storage, kernel=args.kernel, tile=args.tile, graph_chunk=T, stream=stream.cuda_stream,
                      max_steps=(K + Wm) * T + 1)
     for _ in range(Wm):
         sim.step(T)
@@ -325,7 +328,7 @@ def main():
     elem = 4 if args.storage == "f32" else 2
     _, b_vel, b_str = alg_bytes_split(g, elem)
     b_fused = alg_bytes_fused(g, elem)
-    tsim = Simulation(sc, storage=args.storage, kernel=args.kernel, stream=stream.cuda_stream, timing=True,
+    tsim = Simulation(sc, storage=args.storage, kernel=args.kernel, tile=args.tile, stream=stream.cuda_stream, timing=True,
                       max_steps=64)
     kind, tile = tsim.config()
     tsim.step(3)
@@ -367,7 +370,7 @@ def main():
         if pg:
             pg.barrier()
         t0 = time.perf_counter()
-        s2 = Simulation(sc_p, storage=args.storage, kernel=args.kernel, graph_chunk=T, stream=stream.cuda_stream,
+        s2 = Simulation(sc_p, storage=args.storage, kernel=args.kernel, tile=args.tile, graph_chunk=T, stream=stream.cuda_stream,
                         max_steps=K * T)
         for _ in range(K):
             s2.step(T)

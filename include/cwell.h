@@ -87,11 +87,23 @@ typedef struct {
   const uint16_t *cell_id;
 } sim_medium_t;
 
-/* Point source (Sec. 2).  kind 0 = volumetric (pressure) source: the three
- * normal stresses receive dt * amplitude * f(t_{n+1/2}) / V per step, f the
- * Ricker pulse with dominant frequency f0 and delay 2/f0, V the cell
- * volume; r < dr places it on the axis, shared by all ring-0 cells of the
- * nearest depth. Other kinds return SIM_EUNSUPPORTED. */
+/* Point source (Sec. 2, the four source types), f the Ricker pulse with
+ * dominant frequency f0 and delay 2/f0, A = amplitude, V the node's volume.
+ *  kind 0, volumetric: the three normal stresses receive dt * A f(t_{n+1/2}) / V
+ *    per step; r < dr places it on the axis, shared by all ring-0 cells of the
+ *    nearest depth (V = pi dr^2 dz).
+ *  kind 1, transverse point force (direction theta): after the velocity
+ *    update v_r += dt * A f(t_n) / (rho V) at the nearest v_r node; on the
+ *    axis a horizontal force spread over the ring-1 v_r nodes with the share
+ *    2 cos(theta_j - theta) / Ntheta each.
+ *  kind 2, longitudinal point force: the same on v_z (on the axis every
+ *    ring-0 v_z node, V = pi dr^2 dz).
+ *  kind 3, torsion: s_rphi and s_phiz += dt * A f(t_{n+1/2}) / (2 pi r dr dz)
+ *    on the whole ring at radius r (a torque about the axis); both shear
+ *    nodes must lie in a solid, else SIM_EUNSUPPORTED.
+ * Kinds 1-3 run on the split and marching paths (SIM_EUNSUPPORTED when the
+ * fused kernels are asked for; AUTO picks among the others) and not in
+ * batches. */
 typedef struct {
   int kind;
   double r, theta, z, f0, amplitude;
@@ -173,7 +185,8 @@ size_t sim_device_bytes(const sim_t *h);
  * 100 + r for its four-cells-per-thread variant; 1000 + 100 r + J for the
  * marching kernels with r rows per block and runs of J theta planes; 2000 for
  * the split kernels, 2000 + b for their load-first variant compiled for b
- * resident blocks per SM. */
+ * resident blocks per SM (blocks walk theta fastest), 2010 + b for the same
+ * with the blocks walking z fastest. */
 int sim_config(const sim_t *h, int *kernel, int *tile_rows);
 
 /* Kernel timings gathered with opts.timing = 1: for kernel slot q
@@ -282,9 +295,17 @@ const char *sur_last_error(const sur_t *s);
 
 /* Tensor-core GEMM of the surrogate on host buffers: C[M][N] = op(A) op(B),
  * A and B BF16 bit patterns (row-major, op = transpose when trans_* != 0),
- * C FP32; for testing the kernel against an FP64 product of the same inputs. */
+ * C FP32; for testing the kernel against an FP64 product of the same inputs.
+ * Products of at least 128 rows run on the tcgen05 kernel (accumulator in
+ * tensor memory), narrower ones on the mma.sync kernel, as in training. */
 int cw_gemm_bf16(int trans_a, int trans_b, int M, int N, int K, const uint16_t *A, int lda, const uint16_t *B,
                  int ldb, float *C, int ldc);
+
+/* The same with the kernel named: path 0 = by shape (as above), 1 = the
+ * mma.sync kernel, 2 = the tcgen05 kernel for any shape.  SIM_ETIMEOUT if a
+ * bounded wait of the tcgen05 kernel gave up (the TMEM it held is freed). */
+int cw_gemm_bf16_path(int path, int trans_a, int trans_b, int M, int N, int K, const uint16_t *A, int lda,
+                      const uint16_t *B, int ldb, float *C, int ldc);
 
 #ifdef __cplusplus
 }

@@ -364,6 +364,8 @@ def _sur_sigs(L):
     u16p = ctypes.POINTER(ctypes.c_uint16)
     L.cw_gemm_bf16.argtypes = [i, i, i, i, i, u16p, i, u16p, i, fp, i]
     L.cw_gemm_bf16.restype = i
+    L.cw_gemm_bf16_path.argtypes = [i, i, i, i, i, i, u16p, i, u16p, i, fp, i]
+    L.cw_gemm_bf16_path.restype = i
     L._sur_ready = True
 
 
@@ -371,8 +373,12 @@ def _fp(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
 
 
-def gemm_bf16(A16: np.ndarray, B16: np.ndarray, trans_a=False, trans_b=False) -> np.ndarray:
-    """Tensor-core GEMM on BF16 bit patterns (uint16 arrays), FP32 result."""
+GEMM_PATH = {"auto": 0, "mma": 1, "tcgen05": 2}
+
+
+def gemm_bf16(A16: np.ndarray, B16: np.ndarray, trans_a=False, trans_b=False, path="auto") -> np.ndarray:
+    """Tensor-core GEMM on BF16 bit patterns (uint16 arrays), FP32 result;
+    path "auto" (by shape, as in training), "mma" or "tcgen05"."""
     L = lib()
     _sur_sigs(L)
     A16 = np.ascontiguousarray(A16, np.uint16)
@@ -381,10 +387,10 @@ def gemm_bf16(A16: np.ndarray, B16: np.ndarray, trans_a=False, trans_b=False) ->
     N = B16.shape[0] if trans_b else B16.shape[1]
     C = np.zeros((M, N), np.float32)
     u16p = ctypes.POINTER(ctypes.c_uint16)
-    rc = L.cw_gemm_bf16(int(trans_a), int(trans_b), M, N, K, A16.ctypes.data_as(u16p), A16.shape[1],
-                        B16.ctypes.data_as(u16p), B16.shape[1], _fp(C), N)
+    rc = L.cw_gemm_bf16_path(GEMM_PATH[path], int(trans_a), int(trans_b), M, N, K, A16.ctypes.data_as(u16p),
+                             A16.shape[1], B16.ctypes.data_as(u16p), B16.shape[1], _fp(C), N)
     if rc != SIM_OK:
-        raise SimError(rc, "cw_gemm_bf16 failed")
+        raise SimError(rc, "cw_gemm_bf16_path failed")
     return C
 
 

@@ -108,6 +108,8 @@ extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *m
   for (int c = 0; c < n; c++) {  // host-side checks of every case before any device work
     int rc = validate_inputs(&grids[c], &media[c], &sources[c], &receivers[c], opts);
     if (rc) return bfail(nullptr, rc, "case " + std::to_string(c) + ": " + g_create_err);
+    if (sources[c].kind != 0)
+      return bfail(nullptr, SIM_EUNSUPPORTED, "case " + std::to_string(c) + ": batches run the volumetric source only");
   }
   simb_t *b = new simb_t();
   b->device = opts->device;

@@ -53,6 +53,21 @@ struct KParams {
   int *step;                // device step counter
 };
 
+// Point forces and the torsion ring (source kinds 1-3): entry e adds
+// w[e] * wav[step] to element off[e] of field fld[e] (stored units, so the
+// weights carry dt, A, the node's 1 / (rho V) or 1 / V, the angular share and
+// the storage scale); wav[n] = f(t) at the injection time of step n.
+struct IParams {
+  int n;
+  const int *fld;
+  const long long *off;
+  const float *w;
+  const float *wav;
+  int n_wav;
+  int *step;
+  void *f[NF];
+};
+
 struct RParams {
   int nth, NR, NZp, n_rec, cap;
   long long plane;
@@ -170,8 +185,10 @@ struct FusedParams {
 };
 
 // launchers implemented in the .cu files (host side)
-cudaError_t launch_split(int storage, const KParams &p, cudaStream_t s, cudaEvent_t *ev);
+// parts: 1 = velocity kernel, 2 = stress kernel, 3 = both (velocity first)
+cudaError_t launch_split(int storage, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts = 3);
 cudaError_t launch_receivers(int storage, const RParams &p, cudaStream_t s);
+cudaError_t launch_inject(int storage, const IParams &p, cudaStream_t s);
 cudaError_t launch_fused(int storage, int rt, const FusedMaps &maps, const FusedParams &fp, cudaStream_t s);
 size_t fused_smem_bytes(int storage, int rt);
 long long split_items(int nth, int NR, int NZ);
@@ -192,16 +209,24 @@ inline bool is_march(int code) { return code >= 1000 && code < 2000; }
 inline int march_rows(int code) { return (code / 100) % 10; }
 inline int march_planes(int code) { return code % 100; }
 cudaError_t launch_march(int storage, int code, const FusedMaps &maps, const KParams &p, int *status, cudaStream_t s,
-                         cudaEvent_t *ev);
+                         cudaEvent_t *ev, int parts = 3);
 size_t march_smem_bytes(int storage, int code);
-// split path: tile code 2000 = the kernels of stencil_split.cu; 2000 + b =
-// the load-first kernels of stencil_hoist.cu with b resident blocks per SM
-// asked of the register allocator (b = 3, 4 or 5)
+// split path: tile code 2000 = the kernels of stencil_split.cu; 2000 + 10 o + b
+// = the load-first kernels of stencil_hoist.cu with b resident blocks per SM
+// asked of the register allocator (b = 3, 4 or 5) and block order o (0: theta
+// fastest, 1: z fastest; b = 3 or 4 only)
 constexpr int SPLIT_CODE = 2000;
 inline bool is_split_family(int code) { return code >= 2000 && code < 3000; }
 inline bool is_hoist(int code) { return code > 2000 && code < 3000; }
-inline int hoist_blocks(int code) { return code - 2000; }
-cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev);
+inline int hoist_blocks(int code) { return code % 10; }
+inline bool hoist_zfast(int code) { return (code / 10) % 10 == 1; }
+cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts = 3);
+// BF16 GEMM on the tcgen05 tensor cores (gemm_tc.cu); status bit 0: a
+// bounded wait gave up (read and cleared by gemm_tcgen05_status)
+cudaError_t gemm_tcgen05(bool ta, bool tb, int M, int N, int K, const __nv_bfloat16 *A, int lda,
+                         const __nv_bfloat16 *B, int ldb, float *C, int ldc, float alpha, float beta,
+                         cudaStream_t s);
+cudaError_t gemm_tcgen05_status(int *out, cudaStream_t s);
 // batched marching kernels: one well's descriptors, parameters and status word
 struct MarchCase {
   FusedMaps maps;

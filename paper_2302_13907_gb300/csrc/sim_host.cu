@@ -70,11 +70,32 @@ int cwell::validate_inputs(const sim_grid_t *g, const sim_medium_t *m, const sim
     if (!(m->rho[q] > 0) || !(m->vp[q] > 0) || !(m->vs[q] >= 0) || m->vp[q] * m->vp[q] < 2.0 * m->vs[q] * m->vs[q] ||
         !isfinite(m->rho[q]) || !isfinite(m->vp[q]))
       return fail(nullptr, SIM_EINVAL, "medium: material " + std::to_string(q) + " needs rho, vp > 0, vs >= 0, vp^2 >= 2 vs^2");
-  if (s->kind != 0) return fail(nullptr, SIM_EUNSUPPORTED, "source: only kind 0 (volumetric) is implemented");
+  if (s->kind < 0 || s->kind > 3) return fail(nullptr, SIM_EINVAL, "source: kind must be 0 .. 3");
+  if (s->kind != 0 && (o->kernel == SIM_KERNEL_FUSED || o->kernel == SIM_KERNEL_FUSED_VEC))
+    return fail(nullptr, SIM_EUNSUPPORTED, "source: point forces and torsion run on the split and marching paths only");
   if (!(s->f0 > 0) || !isfinite(s->amplitude)) return fail(nullptr, SIM_EINVAL, "source: need f0 > 0, finite amplitude");
   if (!(s->r >= 0) || s->r >= g->nr * g->dr) return fail(nullptr, SIM_EINVAL, "source: r outside the interior");
   long ks = lround(s->z / g->dz);
   if (!isfinite(s->z) || ks < 0 || ks >= g->nz) return fail(nullptr, SIM_EINVAL, "source: z outside the interior");
+  if (s->kind != 0) {  // the nodes of a point force or of the torsion ring
+    const int NR = g->nr + g->pml_r, NZ = g->nz + 2 * g->pml_z, nth = g->nth;
+    const long k = ks + g->pml_z;
+    const int i_int = (int)lround(s->r / g->dr), i_half = (int)floor(s->r / g->dr);
+    if (s->kind == 1 && s->r >= g->dr && (i_int < 1 || i_int >= NR))
+      return fail(nullptr, SIM_EINVAL, "source: the transverse force's v_r node falls outside the grid");
+    if ((s->kind == 2 || s->kind == 3) && k + 1 >= NZ)
+      return fail(nullptr, SIM_EINVAL, "source: the node above the force / torsion depth falls outside the grid");
+    if (s->kind == 3) {
+      if (i_int < 1 || i_int >= NR) return fail(nullptr, SIM_EINVAL, "source: the torsion ring needs 1 <= r / dr < NR");
+      auto solid = [&](int j, int i, long kk) { return m->vs[m->cell_id[((size_t)j * NR + i) * NZ + kk]] > 0.0; };
+      for (int j = 0; j < nth; j++) {
+        const int jp = (j + 1) % nth;
+        if (!(solid(j, i_int - 1, k) && solid(j, i_int, k) && solid(jp, i_int - 1, k) && solid(jp, i_int, k) &&
+              solid(j, i_half, k) && solid(jp, i_half, k) && solid(j, i_half, k + 1) && solid(jp, i_half, k + 1)))
+          return fail(nullptr, SIM_EUNSUPPORTED, "source: the torsion ring needs a solid at both shear nodes");
+      }
+    }
+  }
   if (r->n < 0 || (r->n > 0 && (!r->r || !r->theta || !r->z)) || r->quantity != 0)
     return fail(nullptr, SIM_EINVAL, "receivers: bad count, arrays or quantity");
   for (int q = 0; q < r->n; q++) {
@@ -181,8 +202,9 @@ static cudaError_t launch_fused_any(int storage, int code, const FusedMaps &maps
 // Candidates: the fused kernels with each tile height that fits in shared
 // memory, the marching split kernels with each tile height and theta run, and
 // the split kernels (plain and load-first), as far as the requested kernel allows.
-static cudaError_t launch_split_family(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev) {
-  return is_hoist(code) ? launch_hoist(storage, code, p, s, ev) : launch_split(storage, p, s, ev);
+static cudaError_t launch_split_family(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev,
+                                       int parts = 3) {
+  return is_hoist(code) ? launch_hoist(storage, code, p, s, ev, parts) : launch_split(storage, p, s, ev, parts);
 }
 
 static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
@@ -200,7 +222,7 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
     }
   }
   const int cand[] = {2,    4,    6,    8,    106,  110,  114,  1216, 1232, 1264,
-                      1416, 1432, 1464, 1816, 1832, 1864, 2003, 2004, 2005, SPLIT_CODE};
+                      1416, 1432, 1464, 1816, 1832, 1864, 2003, 2004, 2005, 2013, 2014, SPLIT_CODE};
   cudaEvent_t a, b;
   CK(h, cudaEventCreate(&a));
   CK(h, cudaEventCreate(&b));
@@ -315,6 +337,9 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   h->kernel = opts->kernel == SIM_KERNEL_SPLIT   ? SIM_KERNEL_SPLIT
               : opts->kernel == SIM_KERNEL_MARCH ? SIM_KERNEL_MARCH
                                                  : SIM_KERNEL_FUSED;
+  h->src_kind = source->kind;
+  // point forces and torsion are injected between the half-steps: in-place paths only
+  if (h->src_kind != 0 && h->kernel == SIM_KERNEL_FUSED) h->kernel = SIM_KERNEL_AUTO;
   h->fused = h->kernel == SIM_KERNEL_FUSED;
 
   h->graph_chunk = opts->graph_chunk == 0 ? 64 : opts->graph_chunk;
@@ -425,6 +450,62 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   std::vector<float> wav(h->n_wav);
   for (int n = 0; n < h->n_wav; n++)
     wav[n] = (float)(dt * source->amplitude * ricker((n + 0.5) * dt, source->f0) / vol * h->sscale);
+  // --- point forces (R12) and the torsion ring (R13): injection points in stored units,
+  // weight = dt * A * share / (rho_node V) (forces) or dt * A / (2 pi r dr dz) (torsion),
+  // times the storage scale; wav2[n] = f(t_n) (forces) or f(t_{n+1/2}) (torsion)
+  std::vector<int> ifld;
+  std::vector<long long> ioff;
+  std::vector<float> iw, iwav;
+  if (source->kind != 0) {
+    const bool axis = source->r < g.dr;
+    const int jsrc = (int)(((lround(source->theta / dth) % nth) + nth) % nth);
+    const double A = source->amplitude, dr = g.dr, dz = g.dz;
+    auto hc = [&](int j, int i, long k) { return ((size_t)j * NR + i) * NZ + (size_t)k; };  // host cell
+    auto dc = [&](int j, int i, long k) { return ((long long)j * NR + i) * NZp + k; };      // device element
+    auto rho2 = [&](size_t a, size_t b) { return 0.5 * (medium->rho[cid[a]] + medium->rho[cid[b]]); };
+    auto solid = [&](size_t c) { return medium->vs[cid[c]] > 0.0; };
+    auto add = [&](int fld, long long off, double w) {
+      ifld.push_back(fld);
+      ioff.push_back(off);
+      iw.push_back((float)(dt * A * w * (fld <= F_VZ ? h->vscale : h->sscale)));
+    };
+    bool bad = false;
+    const long k = ks;
+    if (source->kind == 1) {
+      if (axis) {
+        for (int j = 0; j < nth; j++)
+          add(F_VR, dc(j, 1, k), 2.0 * cos(j * dth - source->theta) / nth / (rho2(hc(j, 0, k), hc(j, 1, k)) * dr * dr * dth * dz));
+      } else {
+        const int i = (int)lround(source->r / dr);
+        if (i < 1 || i >= NR) bad = true;
+        else add(F_VR, dc(jsrc, i, k), 1.0 / (rho2(hc(jsrc, i - 1, k), hc(jsrc, i, k)) * i * dr * dr * dth * dz));
+      }
+    } else if (source->kind == 2) {
+      if (k + 1 >= NZ) bad = true;
+      else if (axis) {
+        for (int j = 0; j < nth; j++)
+          add(F_VZ, dc(j, 0, k), 1.0 / (rho2(hc(j, 0, k), hc(j, 0, k + 1)) * M_PI * dr * dr * dz));
+      } else {
+        const int i = (int)floor(source->r / dr);
+        add(F_VZ, dc(jsrc, i, k), 1.0 / (rho2(hc(jsrc, i, k), hc(jsrc, i, k + 1)) * (i + 0.5) * dr * dr * dth * dz));
+      }
+    } else {
+      const int i = (int)lround(source->r / dr), ih = (int)floor(source->r / dr);
+      if (i < 1 || i >= NR || ih + 1 > NR || k + 1 >= NZ) bad = true;
+      for (int j = 0; j < nth && !bad; j++) {
+        const int jp = (j + 1) % nth;
+        if (!(solid(hc(j, i - 1, k)) && solid(hc(j, i, k)) && solid(hc(jp, i - 1, k)) && solid(hc(jp, i, k)) &&
+              solid(hc(j, ih, k)) && solid(hc(jp, ih, k)) && solid(hc(j, ih, k + 1)) && solid(hc(jp, ih, k + 1))))
+          return bail(fail(h, SIM_EUNSUPPORTED, "source: the torsion ring needs a solid at both shear nodes"));
+        add(F_SRP, dc(j, i, k), 1.0 / (2.0 * M_PI * i * dr * dr * dz));
+        add(F_SPZ, dc(j, ih, k), 1.0 / (2.0 * M_PI * (ih + 0.5) * dr * dr * dz));
+      }
+    }
+    if (bad) return bail(fail(h, SIM_EINVAL, "source: the force / torsion node falls outside the grid"));
+    const bool force = source->kind != 3;
+    iwav.resize(h->n_wav);
+    for (int n = 0; n < h->n_wav; n++) iwav[n] = (float)ricker((force ? n : n + 0.5) * dt, source->f0);
+  }
   // --- receivers
   std::vector<int> rec(3 * std::max(1, h->n_rec));
   for (int q = 0; q < h->n_rec; q++) {
@@ -471,6 +552,15 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   if ((rc = dev_alloc(h, (void **)&h->traces, (size_t)std::max(1, h->n_rec) * h->cap * 4))) return bail(rc);
   if ((rc = dev_alloc(h, (void **)&h->step, 16))) return bail(rc);
   if ((rc = dev_alloc(h, (void **)&h->status, 16))) return bail(rc);
+  int *d_ifld = nullptr;
+  long long *d_ioff = nullptr;
+  float *d_iw = nullptr, *d_iwav = nullptr;
+  if (!ifld.empty()) {
+    if ((rc = dev_alloc(h, (void **)&d_ifld, ifld.size() * 4))) return bail(rc);
+    if ((rc = dev_alloc(h, (void **)&d_ioff, ioff.size() * 8))) return bail(rc);
+    if ((rc = dev_alloc(h, (void **)&d_iw, iw.size() * 4))) return bail(rc);
+    if ((rc = dev_alloc(h, (void **)&d_iwav, iwav.size() * 4))) return bail(rc);
+  }
 
   cudaStream_t st = h->stream;
 #define UP(dst, src, n) \
@@ -488,6 +578,12 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   UP(h->inv_rh, inv_rh.data(), NR * 4);
   UP(h->wav, wav.data(), wav.size() * 4);
   UP(h->rec, rec.data(), rec.size() * 4);
+  if (!ifld.empty()) {
+    UP(d_ifld, ifld.data(), ifld.size() * 4);
+    UP(d_ioff, ioff.data(), ioff.size() * 8);
+    UP(d_iw, iw.data(), iw.size() * 4);
+    UP(d_iwav, iwav.data(), iwav.size() * 4);
+  }
 #undef UP
   // pageable host sources: make the upload complete before the host vectors go away
   e = cudaStreamSynchronize(st);
@@ -523,10 +619,18 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   for (int q = 0; q < NPZ; q++) p.psz[q] = h->psz[q];
   p.wav = h->wav;
   p.n_wav = h->n_wav;
-  p.src_i = is;
+  p.src_i = source->kind == 0 ? is : -1;  // the stress kernels inject only the volumetric source
   p.src_j = js;
   p.src_k = (int)ks;
   p.step = h->step;
+  h->ip.n = (int)ifld.size();
+  h->ip.fld = d_ifld;
+  h->ip.off = d_ioff;
+  h->ip.w = d_iw;
+  h->ip.wav = d_iwav;
+  h->ip.n_wav = h->n_wav;
+  h->ip.step = h->step;
+  for (int q = 0; q < NF; q++) h->ip.f[q] = h->f[q];
   RParams &r = h->rp;
   r.nth = nth;
   r.NR = NR;
@@ -580,10 +684,11 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
     }
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "autotune"));
-  } else {  // the marching or the split kernels, asked for by name
+  } else {  // the marching or the split kernels (asked for by name, or the in-place paths of AUTO)
     if ((rc = autotune(h, h->kernel, opts->tile, &h->tile_rt))) return bail(rc);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "autotune"));
+    h->kernel = is_march(h->tile_rt) ? SIM_KERNEL_MARCH : SIM_KERNEL_SPLIT;
   }
   if (h->kernel == SIM_KERNEL_MARCH) {
     h->march = true;
@@ -608,12 +713,22 @@ static cudaError_t enqueue_step(sim_t *h, int parity, bool timed) {
       cudaEventRecord(h->ev[2], h->stream);
     }
     e = launch_receivers(h->storage, h->rp2[parity], h->stream);
-  } else if (h->march) {
-    e = launch_march(h->storage, h->tile_rt, h->mmaps, h->kp, h->status, h->stream, timed ? h->ev : nullptr);
-    if (e != cudaSuccess) return e;
-    e = launch_receivers(h->storage, h->rp, h->stream);
   } else {
-    e = launch_split_family(h->storage, h->tile_rt, h->kp, h->stream, timed ? h->ev : nullptr);
+    // point forces act after the velocity kernel, the torsion ring after the stress kernel
+    cudaEvent_t *ev = timed ? h->ev : nullptr;
+    const bool force = h->src_kind == 1 || h->src_kind == 2;
+    auto half = [&](int parts) {
+      return h->march ? launch_march(h->storage, h->tile_rt, h->mmaps, h->kp, h->status, h->stream, ev, parts)
+                      : launch_split_family(h->storage, h->tile_rt, h->kp, h->stream, ev, parts);
+    };
+    if (force) {
+      e = half(1);
+      if (e == cudaSuccess) e = launch_inject(h->storage, h->ip, h->stream);
+      if (e == cudaSuccess) e = half(2);
+    } else {
+      e = half(3);
+      if (e == cudaSuccess && h->src_kind == 3) e = launch_inject(h->storage, h->ip, h->stream);
+    }
     if (e != cudaSuccess) return e;
     e = launch_receivers(h->storage, h->rp, h->stream);
   }

@@ -42,6 +42,9 @@ struct sim_s {
   float *psr2[NPR] = {};
   float *psz2[NPZ] = {};
   FusedMaps maps[2];
+  // point forces / torsion ring (source kinds 1-3): injection points
+  int src_kind = 0;
+  IParams ip{};
   // marching split path (in place on the first buffer set): TMA descriptors
   bool march = false;
   FusedMaps mmaps;

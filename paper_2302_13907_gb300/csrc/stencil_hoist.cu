@@ -303,16 +303,30 @@ __device__ __forceinline__ void hoist_quad(const KParams &p, int j, int i, int k
   }
 }
 
-template <typename T, int MINB>
-__global__ void __launch_bounds__(HB_X *HB_Y, MINB) vel_hoist(const KParams p) {
-  const int i = blockIdx.y * HB_Y + threadIdx.y, k0 = (blockIdx.z * HB_X + threadIdx.x) * 4;
-  if (i < p.NR && k0 < p.NZ) hoist_quad<T, true>(p, blockIdx.x, i, k0);
+// Block order: ZF = false walks theta fastest (blockIdx.x = theta, y = r tile,
+// z = z tile: co-resident blocks share theta-neighbour rows); ZF = true walks
+// z fastest (x = z tile, y = r tile, z = theta: co-resident blocks stream
+// whole rows, theta neighbours come back from L2).
+template <bool ZF>
+__device__ __forceinline__ void block_cell(int &j, int &i, int &k0) {
+  const int zt = ZF ? blockIdx.x : blockIdx.z;
+  j = ZF ? blockIdx.z : blockIdx.x;
+  i = blockIdx.y * HB_Y + threadIdx.y;
+  k0 = (zt * HB_X + threadIdx.x) * 4;
 }
 
-template <typename T, int MINB>
+template <typename T, int MINB, bool ZF>
+__global__ void __launch_bounds__(HB_X *HB_Y, MINB) vel_hoist(const KParams p) {
+  int j, i, k0;
+  block_cell<ZF>(j, i, k0);
+  if (i < p.NR && k0 < p.NZ) hoist_quad<T, true>(p, j, i, k0);
+}
+
+template <typename T, int MINB, bool ZF>
 __global__ void __launch_bounds__(HB_X *HB_Y, MINB) str_hoist(const KParams p) {
-  const int i = blockIdx.y * HB_Y + threadIdx.y, k0 = (blockIdx.z * HB_X + threadIdx.x) * 4;
-  if (i < p.NR && k0 < p.NZ) hoist_quad<T, false>(p, blockIdx.x, i, k0);
+  int j, i, k0;
+  block_cell<ZF>(j, i, k0);
+  if (i < p.NR && k0 < p.NZ) hoist_quad<T, false>(p, j, i, k0);
 }
 
 // Batched scenarios: the blocks walk the work list of all cases, item =
@@ -345,24 +359,32 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) batch_hoist(const KParams *c
   }
 }
 
-template <typename T, int MINB>
-cudaError_t launch_hoist_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev) {
+template <typename T, int MINB, bool ZF>
+cudaError_t launch_hoist_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
   dim3 blk(HB_X, HB_Y);
-  dim3 grd(p.nth, (p.NR + HB_Y - 1) / HB_Y, (p.NZ + 4 * HB_X - 1) / (4 * HB_X));
-  if (ev) cudaEventRecord(ev[0], s);
-  vel_hoist<T, MINB><<<grd, blk, 0, s>>>(p);
-  if (ev) cudaEventRecord(ev[1], s);
-  str_hoist<T, MINB><<<grd, blk, 0, s>>>(p);
-  if (ev) cudaEventRecord(ev[2], s);
+  const int nzt = (p.NZ + 4 * HB_X - 1) / (4 * HB_X), nrt = (p.NR + HB_Y - 1) / HB_Y;
+  if (nzt > 65535 || p.nth > 65535) return cudaErrorInvalidValue;
+  dim3 grd = ZF ? dim3(nzt, nrt, p.nth) : dim3(p.nth, nrt, nzt);
+  if (parts & 1) {
+    if (ev) cudaEventRecord(ev[0], s);
+    vel_hoist<T, MINB, ZF><<<grd, blk, 0, s>>>(p);
+    if (ev) cudaEventRecord(ev[1], s);
+  }
+  if (parts & 2) {
+    str_hoist<T, MINB, ZF><<<grd, blk, 0, s>>>(p);
+    if (ev) cudaEventRecord(ev[2], s);
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_hoist_st(int minb, const KParams &p, cudaStream_t s, cudaEvent_t *ev) {
-  switch (minb) {
-    case 3: return launch_hoist_t<T, 3>(p, s, ev);
-    case 4: return launch_hoist_t<T, 4>(p, s, ev);
-    case 5: return launch_hoist_t<T, 5>(p, s, ev);
+cudaError_t launch_hoist_st(int minb, bool zf, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
+  switch (minb * 2 + (zf ? 1 : 0)) {
+    case 6: return launch_hoist_t<T, 3, false>(p, s, ev, parts);
+    case 7: return launch_hoist_t<T, 3, true>(p, s, ev, parts);
+    case 8: return launch_hoist_t<T, 4, false>(p, s, ev, parts);
+    case 9: return launch_hoist_t<T, 4, true>(p, s, ev, parts);
+    case 10: return launch_hoist_t<T, 5, false>(p, s, ev, parts);
   }
   return cudaErrorInvalidValue;
 }
@@ -391,12 +413,13 @@ cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev) {
+cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
   const int minb = hoist_blocks(code);
+  const bool zf = hoist_zfast(code);
   switch (storage) {
-    case 0: return launch_hoist_st<float>(minb, p, s, ev);
-    case 1: return launch_hoist_st<__nv_bfloat16>(minb, p, s, ev);
-    case 2: return launch_hoist_st<__half>(minb, p, s, ev);
+    case 0: return launch_hoist_st<float>(minb, zf, p, s, ev, parts);
+    case 1: return launch_hoist_st<__nv_bfloat16>(minb, zf, p, s, ev, parts);
+    case 2: return launch_hoist_st<__half>(minb, zf, p, s, ev, parts);
   }
   return cudaErrorInvalidValue;
 }

@@ -546,23 +546,28 @@ cudaError_t launch_march_t(const FusedMaps &maps, const KParams &p, int nj, int 
 
 template <typename T, int RT>
 cudaError_t launch_march_rt(const FusedMaps &maps, const KParams &p, int nj, int *status, cudaStream_t s,
-                            cudaEvent_t *ev) {
-  if (ev) cudaEventRecord(ev[0], s);
-  cudaError_t e = launch_march_t<T, RT, true>(maps, p, nj, status, s);
-  if (e != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[1], s);
-  e = launch_march_t<T, RT, false>(maps, p, nj, status, s);
-  if (ev) cudaEventRecord(ev[2], s);
+                            cudaEvent_t *ev, int parts) {
+  cudaError_t e = cudaSuccess;
+  if (parts & 1) {
+    if (ev) cudaEventRecord(ev[0], s);
+    e = launch_march_t<T, RT, true>(maps, p, nj, status, s);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], s);
+  }
+  if (parts & 2) {
+    e = launch_march_t<T, RT, false>(maps, p, nj, status, s);
+    if (ev) cudaEventRecord(ev[2], s);
+  }
   return e;
 }
 
 template <typename T>
 cudaError_t launch_march_st(int rt, const FusedMaps &m, const KParams &p, int nj, int *status, cudaStream_t s,
-                            cudaEvent_t *ev) {
+                            cudaEvent_t *ev, int parts) {
   switch (rt) {
-    case 2: return launch_march_rt<T, 2>(m, p, nj, status, s, ev);
-    case 4: return launch_march_rt<T, 4>(m, p, nj, status, s, ev);
-    case 8: return launch_march_rt<T, 8>(m, p, nj, status, s, ev);
+    case 2: return launch_march_rt<T, 2>(m, p, nj, status, s, ev, parts);
+    case 4: return launch_march_rt<T, 4>(m, p, nj, status, s, ev, parts);
+    case 8: return launch_march_rt<T, 8>(m, p, nj, status, s, ev, parts);
   }
   return cudaErrorInvalidValue;
 }
@@ -640,13 +645,13 @@ cudaError_t launch_march_batch(int storage, int code, bool vel, const MarchCase 
 }
 
 cudaError_t launch_march(int storage, int code, const FusedMaps &maps, const KParams &p, int *status, cudaStream_t s,
-                         cudaEvent_t *ev) {
+                         cudaEvent_t *ev, int parts) {
   const int rt = march_rows(code), nj = march_planes(code);
   if (nj < 1) return cudaErrorInvalidValue;
   switch (storage) {
-    case 0: return launch_march_st<float>(rt, maps, p, nj, status, s, ev);
-    case 1: return launch_march_st<__nv_bfloat16>(rt, maps, p, nj, status, s, ev);
-    case 2: return launch_march_st<__half>(rt, maps, p, nj, status, s, ev);
+    case 0: return launch_march_st<float>(rt, maps, p, nj, status, s, ev, parts);
+    case 1: return launch_march_st<__nv_bfloat16>(rt, maps, p, nj, status, s, ev, parts);
+    case 2: return launch_march_st<__half>(rt, maps, p, nj, status, s, ev, parts);
   }
   return cudaErrorInvalidValue;
 }

@@ -381,6 +381,27 @@ __device__ __forceinline__ void receivers_body(const RParams &p) {
   if (threadIdx.x == 0) *p.step = n + 1;
 }
 
+// Point forces / torsion ring: one thread per injection point, after the
+// velocity (forces) or the stress (torsion) kernel of the step.
+template <typename T>
+__device__ __forceinline__ T to_store(float v);
+template <>
+__device__ __forceinline__ float to_store<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
+
+template <typename T>
+__global__ void __launch_bounds__(128) inject_kernel(const IParams p) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.n) return;
+  const int n = *p.step;
+  if (n < 0 || n >= p.n_wav) return;
+  T *x = (T *)p.f[p.fld[e]] + p.off[e];
+  *x = to_store<T>(st_to_float<T>(*x) + p.w[e] * __ldg(p.wav + n));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) receivers_kernel(const RParams p) {
   receivers_body<T>(p);
@@ -393,22 +414,26 @@ __global__ void __launch_bounds__(256) receivers_batch(const RParams *rp) {
 }
 
 template <typename T>
-static cudaError_t launch_split_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev) {
+static cudaError_t launch_split_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
   dim3 blk(SB_X, SB_Y);
   dim3 grd(p.nth, (p.NR + SB_Y - 1) / SB_Y, (p.NZ + 4 * SB_X - 1) / (4 * SB_X));
-  if (ev) cudaEventRecord(ev[0], s);
-  vel_split<T><<<grd, blk, 0, s>>>(p);
-  if (ev) cudaEventRecord(ev[1], s);
-  str_split<T><<<grd, blk, 0, s>>>(p);
-  if (ev) cudaEventRecord(ev[2], s);
+  if (parts & 1) {
+    if (ev) cudaEventRecord(ev[0], s);
+    vel_split<T><<<grd, blk, 0, s>>>(p);
+    if (ev) cudaEventRecord(ev[1], s);
+  }
+  if (parts & 2) {
+    str_split<T><<<grd, blk, 0, s>>>(p);
+    if (ev) cudaEventRecord(ev[2], s);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_split(int storage, const KParams &p, cudaStream_t s, cudaEvent_t *ev) {
+cudaError_t launch_split(int storage, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
   switch (storage) {
-    case 0: return launch_split_t<float>(p, s, ev);
-    case 1: return launch_split_t<__nv_bfloat16>(p, s, ev);
-    case 2: return launch_split_t<__half>(p, s, ev);
+    case 0: return launch_split_t<float>(p, s, ev, parts);
+    case 1: return launch_split_t<__nv_bfloat16>(p, s, ev, parts);
+    case 2: return launch_split_t<__half>(p, s, ev, parts);
   }
   return cudaErrorInvalidValue;
 }
@@ -418,6 +443,18 @@ cudaError_t launch_batch_receivers(int storage, const RParams *rp, int n_cases, 
     case 0: receivers_batch<float><<<n_cases, 256, 0, s>>>(rp); break;
     case 1: receivers_batch<__nv_bfloat16><<<n_cases, 256, 0, s>>>(rp); break;
     case 2: receivers_batch<__half><<<n_cases, 256, 0, s>>>(rp); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inject(int storage, const IParams &p, cudaStream_t s) {
+  if (p.n < 1) return cudaSuccess;
+  const int blocks = (p.n + 127) / 128;
+  switch (storage) {
+    case 0: inject_kernel<float><<<blocks, 128, 0, s>>>(p); break;
+    case 1: inject_kernel<__nv_bfloat16><<<blocks, 128, 0, s>>>(p); break;
+    case 2: inject_kernel<__half><<<blocks, 128, 0, s>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -104,8 +104,9 @@ __global__ void __launch_bounds__(128) gemm_bf16(int M, int N, int K, const __nv
       }
 }
 
-static cudaError_t gemm(bool ta, bool tb, int M, int N, int K, const __nv_bfloat16 *A, int lda,
-                        const __nv_bfloat16 *B, int ldb, float *C, int ldc, float alpha, float beta, cudaStream_t s) {
+static cudaError_t gemm_mma(bool ta, bool tb, int M, int N, int K, const __nv_bfloat16 *A, int lda,
+                            const __nv_bfloat16 *B, int ldb, float *C, int ldc, float alpha, float beta,
+                            cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grd((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
   if (!ta && !tb) gemm_bf16<false, false><<<grd, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta);
@@ -113,6 +114,23 @@ static cudaError_t gemm(bool ta, bool tb, int M, int N, int K, const __nv_bfloat
   else if (ta && !tb) gemm_bf16<true, false><<<grd, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta);
   else gemm_bf16<true, true><<<grd, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta);
   return cudaGetLastError();
+}
+
+// Path of a GEMM: products with at least 128 rows run on the tcgen05 kernel
+// (gemm_tc.cu: 128 x 128 tiles, accumulator in tensor memory); the narrow
+// ones (weight gradients: rows = channels) on the mma.sync kernel above.
+// path: 0 = by shape, 1 = mma.sync, 2 = tcgen05.
+static cudaError_t gemm_path(int path, bool ta, bool tb, int M, int N, int K, const __nv_bfloat16 *A, int lda,
+                             const __nv_bfloat16 *B, int ldb, float *C, int ldc, float alpha, float beta,
+                             cudaStream_t s) {
+  const bool tc = path == 2 || (path == 0 && M >= 128);
+  return tc ? gemm_tcgen05(ta, tb, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, s)
+            : gemm_mma(ta, tb, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, s);
+}
+
+static cudaError_t gemm(bool ta, bool tb, int M, int N, int K, const __nv_bfloat16 *A, int lda,
+                        const __nv_bfloat16 *B, int ldb, float *C, int ldc, float alpha, float beta, cudaStream_t s) {
+  return gemm_path(0, ta, tb, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, s);
 }
 
 // ------------------------------------------------------------ elementwise
@@ -295,6 +313,16 @@ struct sur_s {
 };
 
 static thread_local std::string g_sur_err;
+static int sfail(sur_t *s, int code, const std::string &m);
+
+// a bounded wait of the tcgen05 GEMM that gave up surfaces as SIM_ETIMEOUT
+static int tc_status(sur_t *s) {
+  int st = 0;
+  cudaError_t e = gemm_tcgen05_status(&st, s->stream);
+  if (e != cudaSuccess) return sfail(s, SIM_ECUDA, cudaGetErrorString(e));
+  if (st) return sfail(s, SIM_ETIMEOUT, "a tcgen05 GEMM wait gave up");
+  return SIM_OK;
+}
 
 static int sfail(sur_t *s, int code, const std::string &m) {
   if (s) s->err = m;
@@ -596,7 +624,7 @@ extern "C" int sur_forward(sur_t *s, const float *X, int n, float *Y) {
                            cudaMemcpyDeviceToHost, s->stream));
   }
   SCK(s, cudaStreamSynchronize(s->stream));
-  return SIM_OK;
+  return tc_status(s);
 }
 
 extern "C" int sur_loss_grad(sur_t *s, const float *X, const float *Y, int n, float *loss, float *grad, size_t ng) {
@@ -613,7 +641,7 @@ extern "C" int sur_loss_grad(sur_t *s, const float *X, const float *Y, int n, fl
   // the gradient kernels run on the handle's (non-blocking) stream: copy on it and wait
   if (grad) SCK(s, cudaMemcpyAsync(grad, s->g, s->nparam * 4, cudaMemcpyDeviceToHost, s->stream));
   SCK(s, cudaStreamSynchronize(s->stream));
-  return SIM_OK;
+  return tc_status(s);
 }
 
 extern "C" int sur_train(sur_t *s, const float *X, const float *Y, int n, int epochs, int batch, float lr,
@@ -675,7 +703,7 @@ extern "C" int sur_train(sur_t *s, const float *X, const float *Y, int n, int ep
   cudaFree(dX);
   cudaFree(dY);
   if (e != cudaSuccess) return sfail(s, SIM_ECUDA, cudaGetErrorString(e));
-  return SIM_OK;
+  return tc_status(s);
 }
 
 // fallback gate: errors of validation cases indexed by their normalised inputs
@@ -735,7 +763,12 @@ extern "C" const char *sur_last_error(const sur_t *s) { return s ? s->err.c_str(
 // tensor-core GEMM on host buffers (BF16 bit patterns in, FP32 out)
 extern "C" int cw_gemm_bf16(int trans_a, int trans_b, int M, int N, int K, const uint16_t *A, int lda,
                             const uint16_t *B, int ldb, float *C, int ldc) {
-  if (M < 0 || N < 0 || K < 0 || !A || !B || !C) return SIM_EINVAL;
+  return cw_gemm_bf16_path(0, trans_a, trans_b, M, N, K, A, lda, B, ldb, C, ldc);
+}
+
+extern "C" int cw_gemm_bf16_path(int path, int trans_a, int trans_b, int M, int N, int K, const uint16_t *A, int lda,
+                                 const uint16_t *B, int ldb, float *C, int ldc) {
+  if (path < 0 || path > 2 || M < 0 || N < 0 || K < 0 || !A || !B || !C) return SIM_EINVAL;
   const size_t na = (size_t)(trans_a ? K : M) * lda, nb = (size_t)(trans_b ? N : K) * ldb, nc = (size_t)M * ldc;
   __nv_bfloat16 *dA = nullptr, *dB = nullptr;
   float *dC = nullptr;
@@ -744,10 +777,14 @@ extern "C" int cw_gemm_bf16(int trans_a, int trans_b, int M, int N, int K, const
   if (e == cudaSuccess) e = cudaMalloc(&dC, std::max<size_t>(nc, 1) * 4);
   if (e == cudaSuccess) e = cudaMemcpy(dA, A, na * 2, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(dB, B, nb * 2, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = gemm(trans_a != 0, trans_b != 0, M, N, K, dA, lda, dB, ldb, dC, ldc, 1.f, 0.f, 0);
+  if (e == cudaSuccess)
+    e = gemm_path(path, trans_a != 0, trans_b != 0, M, N, K, dA, lda, dB, ldb, dC, ldc, 1.f, 0.f, 0);
   if (e == cudaSuccess) e = cudaMemcpy(C, dC, nc * 4, cudaMemcpyDeviceToHost);
+  int st = 0;
+  if (e == cudaSuccess) e = gemm_tcgen05_status(&st, 0);
   cudaFree(dA);
   cudaFree(dB);
   cudaFree(dC);
-  return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
+  if (e != cudaSuccess) return SIM_ECUDA;
+  return st ? SIM_ETIMEOUT : SIM_OK;
 }

@@ -53,7 +53,9 @@ def _tiny():
     (lambda sc: setattr(sc.medium, "grid", W.Grid(8, 5, 16, 2, 2, 0.005, 0.005)), B.SIM_EINVAL),  # odd nth
     (lambda sc: setattr(sc.source, "z", 5.0), B.SIM_EINVAL),  # source outside
     (lambda sc: setattr(sc.receivers, "z", np.array([-1.0])), B.SIM_EINVAL),  # receiver outside
-    (lambda sc: setattr(sc.source, "kind", 3), B.SIM_EUNSUPPORTED),  # torsion source not built
+    (lambda sc: setattr(sc.source, "kind", 3), B.SIM_EINVAL),  # torsion ring on the axis
+    (lambda sc: (setattr(sc.source, "kind", 3), setattr(sc.source, "r", 0.01)), B.SIM_EUNSUPPORTED),  # ring in liquid
+    (lambda sc: setattr(sc.source, "kind", 4), B.SIM_EINVAL),  # no such kind
     (lambda sc: sc.medium.cell_id.__setitem__((0, 0, 3), 99), B.SIM_EINVAL),  # id out of range
     (lambda sc: setattr(sc.medium, "vs", np.full_like(sc.medium.vs, 100.0)), B.SIM_EUNSUPPORTED),  # solid axis
     (lambda sc: setattr(sc.medium, "rho", -sc.medium.rho), B.SIM_EINVAL),
@@ -67,11 +69,16 @@ def test_host_validation_rejects_bad_input(mutate, code):
     assert L.sim_last_error(None)
 
 
-@pytest.mark.parametrize("kw", [dict(kernel="split", tile=1416), dict(kernel="march", tile=-3), dict(kernel=7)])
+@pytest.mark.parametrize("kw", [dict(kernel="split", tile=1416), dict(kernel="march", tile=-3), dict(kernel=7),
+                                dict(kernel="fused", source_kind=2)])
 def test_host_validation_rejects_bad_kernel_options(kw):
-    """Kernel / tile options are checked on the host before any device call."""
-    rc, h, L = _create(_tiny(), **kw)
-    assert rc == B.SIM_EINVAL, L.sim_last_error(None)
+    """Kernel / tile options are checked on the host before any device call
+    (point forces cannot run on the fused kernels)."""
+    sc = _tiny()
+    kind = kw.pop("source_kind", 0)
+    sc.source.kind = kind
+    rc, h, L = _create(sc, **kw)
+    assert rc == (B.SIM_EUNSUPPORTED if kind else B.SIM_EINVAL), L.sim_last_error(None)
     assert not h.value
 
 

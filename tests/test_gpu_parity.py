@@ -93,6 +93,42 @@ def test_ragged_grid_fields_elementwise(kernel, seed, nth, nr, nz):
         assert rel_l2(s.traces(), o.traces()) <= TRACE_TOL
 
 
+def _torsion_scenario():
+    """Small cased section (liquid, steel, rock) with the torsion ring in the steel."""
+    g = W.Grid(nr=12, nth=6, nz=40, pml_r=3, pml_z=3, dr=0.004, dz=0.003)
+    med = W.layered_radial(g, [0.016, 0.032], [W.FLUID, W.STEEL, W.ROCK])
+    rec = W.Receivers(r=np.array([0.0, 0.026]), theta=np.array([0.0, 1.0]), z=np.array([0.03, 0.06]))
+    return W.Scenario("torsion", med, W.Source(kind=W.SOURCE_TORSION, r=0.024, z=0.05, f0=60e3), rec, steps=200)
+
+
+@pytest.mark.parametrize("kernel", ["split", "march"])
+@pytest.mark.parametrize("kind,r,theta", [(1, 0.0, 0.7), (1, 0.013, 1.1), (2, 0.0, 0.0), (2, 0.014, 2.0),
+                                          (3, 0.024, 0.0)])
+def test_point_forces_and_torsion_fields_elementwise(kernel, kind, r, theta):
+    """The transverse and longitudinal point forces (on and off the axis)
+    and the torsion ring, injected between the half-steps, against the
+    oracle element by element on every field."""
+    if kind == 3:
+        sc = _torsion_scenario()
+    else:
+        sc = _ragged_scenario(seed=7, nth=8, nr=11, nz=45)
+        sc.source = W.Source(kind=kind, r=r, theta=theta, z=0.06, f0=60e3)
+    o = oracle.Oracle(sc)
+    o.step(sc.steps)
+    with sim(sc, kernel=kernel) as s:
+        s.step(sc.steps)
+        for n in oracle.FIELDS:
+            a, b = s.field(n), o.field(n)
+            scale = np.abs(b).max()
+            if scale == 0:
+                assert np.abs(a).max() == 0, n
+                continue
+            assert np.abs(a - b).max() <= 2e-5 * scale, (n, np.abs(a - b).max() / scale)
+        tr, ref = s.traces(), o.traces()
+        if np.abs(ref).max() > 0:
+            assert rel_l2(tr, ref) <= TRACE_TOL
+
+
 def test_energy_conserved_fp32_pml_off():
     g = W.Grid(nr=40, nth=8, nz=60, pml_r=0, pml_z=0, dr=0.005, dz=0.005)
     med = W.cased_well(g, z_top=0.15)
@@ -256,7 +292,7 @@ def test_march_every_tile_fields_elementwise(tile):
         assert rel_l2(s.traces(), o.traces()) <= TRACE_TOL
 
 
-@pytest.mark.parametrize("tile", (2000, 2003, 2004, 2005))
+@pytest.mark.parametrize("tile", (2000, 2003, 2004, 2005, 2013, 2014))
 def test_split_variants_fields_elementwise(tile):
     """The split kernels and their load-first variants (every register
     budget the autotuner may pick) on the same uneven grid: every field
@@ -292,7 +328,7 @@ def test_fused_matches_split_and_autotuner_choice():
         ta = a.traces()
         fa = {n: a.field(n) for n in ("vr", "srr", "srz")}
     for kern, kind_want, tiles in (("fused", 2, (2, 4, 6, 8)), ("fused4", 2, (106, 110, 114)),
-                                   ("march", 4, MARCH_TILES), ("split", 1, (2000, 2003, 2004, 2005))):
+                                   ("march", 4, MARCH_TILES), ("split", 1, (2000, 2003, 2004, 2005, 2013, 2014))):
         with sim(sc, kernel=kern) as b:
             kind, tile = b.config()
             assert kind == kind_want and tile in tiles, (kern, kind, tile)

@@ -29,14 +29,19 @@ def cosine(a, b):
     return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
 
 
+@pytest.mark.parametrize("path", ["mma", "tcgen05"])
 @pytest.mark.parametrize("ta,tb", [(False, False), (False, True), (True, False), (True, True)])
-@pytest.mark.parametrize("M,N,K", [(37, 70, 45), (128, 64, 32), (5, 3, 200), (300, 130, 17)])
-def test_tensor_core_gemm_against_fp64(ta, tb, M, N, K):
+@pytest.mark.parametrize("M,N,K", [(37, 70, 45), (128, 64, 32), (5, 3, 200), (300, 130, 17), (257, 300, 129),
+                                   (1024, 16, 64)])
+def test_tensor_core_gemm_against_fp64(path, ta, tb, M, N, K):
+    """Both tensor-core kernels (mma.sync; tcgen05 with the accumulator in
+    tensor memory) against the FP64 product of the same BF16 inputs, over
+    every transpose combination and ragged M, N, K (tiles of 64 / 128)."""
     from paper_2302_13907_gb300.binding import gemm_bf16
     rng = np.random.default_rng(M * 7 + N + K)
     A = to_bf16_bits(rng.standard_normal((K, M) if ta else (M, K)))
     B = to_bf16_bits(rng.standard_normal((N, K) if tb else (K, N)))
-    C = gemm_bf16(A, B, ta, tb)
+    C = gemm_bf16(A, B, ta, tb, path=path)
     a, b = bf16_value(A), bf16_value(B)
     ref = (a.T if ta else a) @ (b.T if tb else b)
     assert np.abs(C - ref).max() <= 1e-5 * np.abs(ref).max() * max(1.0, K / 64)
