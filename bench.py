@@ -204,6 +204,40 @@ def bench_batch(stream, n_cases=64, steps=60, warm=8):
             "workload": "64 cement-hardening cases: 136 x 32 x Nz, Nz in {2080, 3104, 4128, 6176} with PML, FP32"}
 
 
+def bench_batch_small(stream, n_cases=64, steps=400, warm=8):
+    """The batching machinery on small wells, where one case cannot fill the
+    GPU: 64 miniature cement cases (44 x 8 x 256 cells each) batched against
+    the same cases run one after another; full 1200-step scenarios per second."""
+    import torch
+    from paper_2302_13907_gb300 import workloads as W
+    from paper_2302_13907_gb300.binding import BatchSimulation, Simulation
+
+    cases = [W.small_cement_case(s) for s in range(n_cases)]
+    full = cases[0].steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with BatchSimulation(cases, graph_chunk=steps // 2, stream=stream.cuda_stream, max_steps=steps + warm) as b:
+        b.run(warm)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b.run(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tb = e0.elapsed_time(e1) / 1e3
+    tp = 0.0
+    for sc in cases:
+        with Simulation(sc, graph_chunk=steps // 2, stream=stream.cuda_stream, max_steps=steps + warm) as s:
+            s.step(warm)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tp += e0.elapsed_time(e1) / 1e3
+    return {"metric": "scenarios/s", "value": n_cases * steps / full / tb, "plain": n_cases * steps / full / tp,
+            "speedup_vs_plain": tp / tb, "cases": n_cases, "steps_timed": steps, "steps_per_scenario": full,
+            "workload": "64 miniature cement cases: 44 x 8 x 256 cells with PML, FP32"}
+
+
 def run_reference(args, ws, rank):
     """--impl reference: the FP64 CPU oracle on bounded samples of the same workload."""
     if rank != 0:
@@ -390,6 +424,7 @@ def main():
     batch = None
     if not args.no_batch:
         batch = bench_batch(stream)
+        batch["small_cases"] = bench_batch_small(stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -1,8 +1,9 @@
 // Batched scenarios: many wells advanced by one launch per kernel per step.
 // Every case is a regular simulator handle (same validation and set-up as
 // sim_create, buffers updated in place by the load-first split bodies); the batch
-// holds device arrays of their kernel parameters and a prefix sum of their
-// work items, and captures its steps in a CUDA graph.
+// holds their kernel parameters and the prefix sum of their work items (host
+// arrays: they travel as kernel parameters, in launches of up to 64 cases), and
+// captures its steps in a CUDA graph.
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -14,9 +15,9 @@ struct simb_s {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<sim_t *> cases;
-  KParams *d_cases = nullptr;
+  std::vector<KParams> kp;        // the cases' kernel parameters (host: they travel as kernel parameters)
+  std::vector<long long> start;   // prefix sum of work items, n + 1 entries
   RParams *d_rp = nullptr;
-  long long *d_start = nullptr;
   long long total = 0;
   int grid = 0, graph_chunk = 64, steps_done = 0;
   cudaGraphExec_t gexec = nullptr;
@@ -41,16 +42,14 @@ static void brelease(simb_t *b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   for (sim_t *h : b->cases) sim_destroy(h);
   b->cases.clear();
-  if (b->d_cases) cudaFree(b->d_cases);
   if (b->d_rp) cudaFree(b->d_rp);
-  if (b->d_start) cudaFree(b->d_start);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
 static cudaError_t batch_step(simb_t *b, const KParams *cases) {
   const int n = (int)b->cases.size();
-  cudaError_t e = launch_batch_split(b->storage, true, cases, b->d_start, n, b->total, b->grid, b->stream);
-  if (e == cudaSuccess) e = launch_batch_split(b->storage, false, cases, b->d_start, n, b->total, b->grid, b->stream);
+  cudaError_t e = launch_batch_split(b->storage, true, cases, b->start.data(), n, b->grid, b->stream);
+  if (e == cudaSuccess) e = launch_batch_split(b->storage, false, cases, b->start.data(), n, b->grid, b->stream);
   return e;
 }
 
@@ -65,10 +64,7 @@ static int tune_grid(simb_t *b) {
     dry[c] = b->cases[c]->kp;
     dry[c].src_i = -1;
   }
-  KParams *d_dry = nullptr;
-  cudaError_t e = cudaMalloc(&d_dry, n * sizeof(KParams));
-  if (e != cudaSuccess) return bcuda(b, e, "cudaMalloc");
-  e = cudaMemcpy(d_dry, dry.data(), n * sizeof(KParams), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaSuccess;
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
@@ -79,9 +75,9 @@ static int tune_grid(simb_t *b) {
   for (long long g : cand) {
     if (e != cudaSuccess) break;
     b->grid = (int)std::max<long long>(1, std::min<long long>(g, std::min<long long>(b->total, 1LL << 30)));
-    e = batch_step(b, d_dry);
+    e = batch_step(b, dry.data());
     cudaEventRecord(t0, b->stream);
-    for (int w = 0; w < 3 && e == cudaSuccess; w++) e = batch_step(b, d_dry);
+    for (int w = 0; w < 3 && e == cudaSuccess; w++) e = batch_step(b, dry.data());
     cudaEventRecord(t1, b->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(t1);
     float ms = 0;
@@ -93,7 +89,6 @@ static int tune_grid(simb_t *b) {
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
-  cudaFree(d_dry);
   if (e != cudaSuccess) return bcuda(b, e, "batch autotune");
   b->grid = pick;
   return SIM_OK;
@@ -151,21 +146,18 @@ extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *m
     start[c + 1] = start[c] + items;
   }
   b->total = start[n];
-  std::vector<KParams> kp(n);
+  b->start = start;
+  b->kp.resize(n);
   std::vector<RParams> rp(n);
   for (int c = 0; c < n; c++) {
-    kp[c] = b->cases[c]->kp;
+    b->kp[c] = b->cases[c]->kp;
     rp[c] = b->cases[c]->rp;
   }
-  if ((e = cudaMalloc(&b->d_cases, n * sizeof(KParams))) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_rp, n * sizeof(RParams))) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_start, (n + 1) * sizeof(long long))) != cudaSuccess) {
+  if ((e = cudaMalloc(&b->d_rp, n * sizeof(RParams))) != cudaSuccess) {
     cudaGetLastError();
     return bail(bfail(b, SIM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)));
   }
-  if ((e = cudaMemcpy(b->d_cases, kp.data(), n * sizeof(KParams), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(b->d_rp, rp.data(), n * sizeof(RParams), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(b->d_start, start.data(), (n + 1) * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = cudaMemcpy(b->d_rp, rp.data(), n * sizeof(RParams), cudaMemcpyHostToDevice)) != cudaSuccess)
     return bail(bcuda(b, e, "upload batch tables"));
   int rc = tune_grid(b);
   if (rc) return bail(rc);
@@ -174,7 +166,7 @@ extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *m
 }
 
 static cudaError_t enqueue_batch_step(simb_t *b) {
-  cudaError_t e = batch_step(b, b->d_cases);
+  cudaError_t e = batch_step(b, b->kp.data());
   if (e == cudaSuccess) e = launch_batch_receivers(b->storage, b->d_rp, (int)b->cases.size(), b->stream);
   return e;
 }

@@ -192,8 +192,12 @@ cudaError_t launch_inject(int storage, const IParams &p, cudaStream_t s);
 cudaError_t launch_fused(int storage, int rt, const FusedMaps &maps, const FusedParams &fp, cudaStream_t s);
 size_t fused_smem_bytes(int storage, int rt);
 long long split_items(int nth, int NR, int NZ);
+// batched load-first kernels: cases and start[] (prefix sum of work items,
+// n_cases + 1 entries) are host arrays; launched in chunks of BATCH_MAX cases
+// whose parameters travel in the kernel's parameter space
+constexpr int BATCH_MAX = 64;
 cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, const long long *start, int n_cases,
-                               long long total, int grid, cudaStream_t s);
+                               int grid, cudaStream_t s);
 cudaError_t launch_batch_receivers(int storage, const RParams *rp, int n_cases, cudaStream_t s);
 int fused_box_x(int storage);
 cudaError_t launch_fused4(int storage, int rt, const FusedMaps &maps, const FusedParams &fp, cudaStream_t s);

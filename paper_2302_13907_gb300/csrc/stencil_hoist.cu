@@ -5,6 +5,8 @@
 // {rho}, {1/mu}, {lambda, lambda + 2 mu}.  Same thread layout (four z cells
 // per thread, 16-byte loads, block = 32 quads x 4 rows, theta fastest across
 // blocks), same arithmetic, same in-place update.
+#include <algorithm>
+
 #include "cwell_internal.cuh"
 
 namespace cwell {
@@ -329,28 +331,32 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) str_hoist(const KParams p) {
   if (i < p.NR && k0 < p.NZ) hoist_quad<T, false>(p, j, i, k0);
 }
 
-// Batched scenarios: the blocks walk the work list of all cases, item =
-// (case, theta, r tile, z tile), theta fastest inside a case so that the theta
-// neighbours a block reads are read by co-resident blocks too.  start[c] =
-// first item of case c (start[n] = total); cases[c] holds the case's geometry
-// and buffers.  The index inside a case is 32-bit (checked on the host).
-__device__ __forceinline__ int find_case(const long long *start, int n, long long item) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(start + mid) <= item) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
+// Batched scenarios: the blocks walk the work list of up to BATCH_MAX cases,
+// item = (case, theta, r tile, z tile), theta fastest inside a case so that
+// the theta neighbours a block reads are read by co-resident blocks too.  The
+// cases' parameters and the prefix sum of their items (start[c] = first item
+// of case c, start[n] = total) travel in the kernel's parameter space, so a
+// block reads its case's geometry and buffers from the constant bank.  The
+// index inside a case is 32-bit (checked on the host).
+struct BatchParams {
+  KParams cases[BATCH_MAX];
+  long long start[BATCH_MAX + 1];
+  int n;
+};
+static_assert(sizeof(BatchParams) <= 32000, "batch parameters exceed the kernel parameter space");
 
 template <typename T, bool VEL, int MINB>
-__global__ void __launch_bounds__(HB_X *HB_Y, MINB) batch_hoist(const KParams *cases, const long long *start,
-                                                                int n_cases, long long total) {
+__global__ void __launch_bounds__(HB_X *HB_Y, MINB) batch_hoist(const __grid_constant__ BatchParams bp) {
+  const long long total = bp.start[bp.n];
   for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-    const int c = find_case(start, n_cases, item);
-    const KParams &p = cases[c];
-    int q = (int)(item - __ldg(start + c));
+    int lo = 0, hi = bp.n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (bp.start[mid] <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const KParams &p = bp.cases[lo];
+    int q = (int)(item - bp.start[lo]);
     const int nth = p.nth, nrt = (p.NR + HB_Y - 1) / HB_Y;
     const int j = q % nth;
     q /= nth;
@@ -398,19 +404,33 @@ long long split_items(int nth, int NR, int NZ) {
 constexpr int BATCH_MINB = 4;  // the load-first bodies at four resident blocks per SM
 
 cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, const long long *start, int n_cases,
-                               long long total, int grid, cudaStream_t s) {
+                               int grid, cudaStream_t s) {
   dim3 blk(HB_X, HB_Y);
-  if (grid < 1 || total < 1) return cudaErrorInvalidValue;
-  switch (storage * 2 + (vel ? 1 : 0)) {
-    case 0: batch_hoist<float, false, BATCH_MINB><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
-    case 1: batch_hoist<float, true, BATCH_MINB><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
-    case 2: batch_hoist<__nv_bfloat16, false, BATCH_MINB><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
-    case 3: batch_hoist<__nv_bfloat16, true, BATCH_MINB><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
-    case 4: batch_hoist<__half, false, BATCH_MINB><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
-    case 5: batch_hoist<__half, true, BATCH_MINB><<<grid, blk, 0, s>>>(cases, start, n_cases, total); break;
-    default: return cudaErrorInvalidValue;
+  if (grid < 1 || n_cases < 1) return cudaErrorInvalidValue;
+  static thread_local BatchParams bp;  // large: kept off the stack
+  for (int c0 = 0; c0 < n_cases; c0 += BATCH_MAX) {
+    const int n = std::min(BATCH_MAX, n_cases - c0);
+    bp.n = n;
+    for (int c = 0; c < n; c++) {
+      bp.cases[c] = cases[c0 + c];
+      bp.start[c] = start[c0 + c] - start[c0];
+    }
+    bp.start[n] = start[c0 + n] - start[c0];
+    if (bp.start[n] < 1) continue;
+    const int g = (int)std::min<long long>(grid, bp.start[n]);
+    switch (storage * 2 + (vel ? 1 : 0)) {
+      case 0: batch_hoist<float, false, BATCH_MINB><<<g, blk, 0, s>>>(bp); break;
+      case 1: batch_hoist<float, true, BATCH_MINB><<<g, blk, 0, s>>>(bp); break;
+      case 2: batch_hoist<__nv_bfloat16, false, BATCH_MINB><<<g, blk, 0, s>>>(bp); break;
+      case 3: batch_hoist<__nv_bfloat16, true, BATCH_MINB><<<g, blk, 0, s>>>(bp); break;
+      case 4: batch_hoist<__half, false, BATCH_MINB><<<g, blk, 0, s>>>(bp); break;
+      case 5: batch_hoist<__half, true, BATCH_MINB><<<g, blk, 0, s>>>(bp); break;
+      default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {

@@ -475,6 +475,31 @@ def scenario_case(seed: int, surrogate_inputs: bool = False) -> Scenario:
                     receivers=on_axis_receivers(zr), cfl=0.5, steps=6000, params=params)
 
 
+def small_cement_case(seed: int, steps: int = 1200) -> Scenario:
+    """Miniature of the cement-hardening family: 5 mm cells, Nr = 36 + 8 PML,
+    Ntheta = 8, Nz = 240 + 8 PML per end; top depth U(0.55, 0.65) m, ramp
+    U(0, 0.2) m, top shear fraction U(0, 1), casing thickness U(8, 12) mm,
+    cement and rock Vs scaled by U(0.9, 1.1); 8 kHz axis monopole 0.075 m above
+    the top, 4 axis receivers 15 mm apart above it.  params holds the six
+    surrogate inputs."""
+    rng = np.random.default_rng(np.random.SeedSequence([2302, 13907, int(seed)]))
+    u = rng.random(6)
+    g = Grid(nr=36, nth=8, nz=240, pml_r=8, pml_z=8, dr=0.005, dz=0.005)
+    z_top = 0.55 + 0.10 * u[0]
+    ramp = 0.2 * u[1]
+    frac = float(u[2])
+    t = 0.008 + 0.004 * u[3]
+    cvs, rvs = 0.9 + 0.2 * u[4], 0.9 + 0.2 * u[5]
+    cement = (CEMENT[0], CEMENT[1] * cvs, CEMENT[2] * cvs)
+    rock = (ROCK[0], ROCK[1] * rvs, ROCK[2] * rvs)
+    med = cased_well(g, z_top=z_top, ramp=ramp, top_frac=frac, casing_t=t, cement=cement, rock=rock)
+    zs = z_top - 0.075
+    params = dict(seed=int(seed), nz=g.nz, z_top=z_top, ramp=ramp, top_frac=frac, casing_t=t,
+                  cement_vs=cement[2], rock_vs=rock[2])
+    return Scenario(name=f"small{seed}", medium=med, source=Source(z=zs, f0=8e3),
+                    receivers=on_axis_receivers(zs - 0.015 * np.arange(1, 5)), cfl=0.5, steps=steps, params=params)
+
+
 def surrogate_features(sc: Scenario) -> np.ndarray:
     """The six surrogate inputs: cement-top depth, ramp length, top shear
     fraction, casing thickness, cement Vs, rock Vs."""

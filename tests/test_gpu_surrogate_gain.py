@@ -23,22 +23,8 @@ STEPS = 1200
 
 
 def mini_case(seed):
-    rng = np.random.default_rng(np.random.SeedSequence([2302, 13907, int(seed)]))
-    u = rng.random(6)
-    g = W.Grid(nr=36, nth=8, nz=240, pml_r=8, pml_z=8, dr=0.005, dz=0.005)
-    z_top = 0.55 + 0.10 * u[0]
-    ramp = 0.2 * u[1]
-    frac = float(u[2])
-    t = 0.008 + 0.004 * u[3]
-    cvs, rvs = 0.9 + 0.2 * u[4], 0.9 + 0.2 * u[5]
-    cement = (W.CEMENT[0], W.CEMENT[1] * cvs, W.CEMENT[2] * cvs)
-    rock = (W.ROCK[0], W.ROCK[1] * rvs, W.ROCK[2] * rvs)
-    med = W.cased_well(g, z_top=z_top, ramp=ramp, top_frac=frac, casing_t=t, cement=cement, rock=rock)
-    zs = z_top - 0.075
-    sc = W.Scenario(f"mini{seed}", med, W.Source(z=zs, f0=8e3), W.on_axis_receivers(zs - 0.015 * np.arange(1, 5)),
-                    cfl=0.5, steps=STEPS)
-    x = np.array([z_top, ramp, frac, t, cement[2], rock[2]])
-    return sc, x
+    sc = W.small_cement_case(seed, steps=STEPS)
+    return sc, W.surrogate_features(sc)
 
 
 def rel_err(pred, true):

@@ -132,3 +132,15 @@ def test_full_scale_well_medium_is_valid():
     assert len(np.unique(rock)) > 500
     full = W.config2.__doc__
     assert "20000 steps" in full
+
+
+def test_small_cement_case_draws_and_geometry():
+    """Miniature cement cases: inputs inside their ranges, source 0.075 m
+    above the cement top, every cell of ring 0 a liquid."""
+    for seed in range(6):
+        sc = W.small_cement_case(seed)
+        x = W.surrogate_features(sc)
+        assert 0.55 <= x[0] <= 0.65 and 0.0 <= x[1] <= 0.2 and 0.0 <= x[2] <= 1.0 and 0.008 <= x[3] <= 0.012
+        assert 0.9 * W.CEMENT[2] <= x[4] <= 1.1 * W.CEMENT[2] and 0.9 * W.ROCK[2] <= x[5] <= 1.1 * W.ROCK[2]
+        assert sc.source.z == pytest.approx(x[0] - 0.075)
+        assert np.all(sc.medium.vs[sc.medium.cell_id[:, 0, :]] == 0)
