@@ -103,12 +103,38 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def split_half_code(tile, vel):
+    """Split code of one half: a pair code v * 10000 + s runs v's velocity
+    kernel and s's stress kernel."""
+    return (tile // 10000 if vel else tile % 10000) if tile >= 10000 else tile
+
+
+def split_kernel_name(tile, vel):
+    """Name of one half of the split path, with its split code: 'vel:2205'.
+    2000 = plain split kernels, 20xx / 21xx = load-first kernels, 22xx =
+    interior + edge launches (one half = both launches)."""
+    return f"{'vel' if vel else 'str'}:{split_half_code(tile, vel)}"
+
+
+def launches_per_step(kind, tile):
+    """Kernel launches of one leapfrog step (volumetric source): the fused
+    kernel or the two halves, plus the receiver kernel; an interior / edge
+    split half (22xx) is two launches."""
+    if kind == 2:
+        return 2
+    if kind == 4:
+        return 3
+    return 1 + sum(2 if split_half_code(tile, v) // 100 == 22 else 1 for v in (True, False))
+
+
 def kernel_label(kind, tile):
     """Name of the path sim_config reports (kernel kind, tile code)."""
     if kind == 2:
         return "fused4" if tile >= 100 else "fused"
     if kind == 4:
         return "march"
+    if tile >= 10000:
+        return f"split (velocity {split_half_code(tile, True)}, stress {split_half_code(tile, False)})"
     return "split (load-first)" if tile > 2000 else "split"
 
 
@@ -376,7 +402,7 @@ def main():
         qd, per_cell = 0, b_fused
     else:
         names = ["march_step(velocity)", "march_step(stress)", "receivers"] if kind == 4 else \
-            ["vel_hoist", "str_hoist", "receivers"] if tile > 2000 else ["vel_split", "str_split", "receivers"]
+            [split_kernel_name(tile, True), split_kernel_name(tile, False), "receivers"]
         qd = 0 if avg[0] >= avg[1] else 1
         per_cell = b_vel if qd == 0 else b_str
     alg = per_cell * cells
@@ -441,7 +467,7 @@ def main():
                            "storage": args.storage, "parallelism": f"replicas x{ws}",
                            "l2": f"inputs larger than L2 ({bytes_held / 1e9:.1f} GB resident)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batch": batch,
-                "gpu_launches": K * T * (2 if kind == 2 else 3), "clocks": ck}
+                "gpu_launches": K * T * launches_per_step(kind, tile), "clocks": ck}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()

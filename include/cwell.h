@@ -184,9 +184,15 @@ size_t sim_device_bytes(const sim_t *h);
  * forced by opts.tile): r (< 100) for the fused kernel with r rows per block,
  * 100 + r for its four-cells-per-thread variant; 1000 + 100 r + J for the
  * marching kernels with r rows per block and runs of J theta planes; 2000 for
- * the split kernels, 2000 + b for their load-first variant compiled for b
- * resident blocks per SM (blocks walk theta fastest), 2010 + b for the same
- * with the blocks walking z fastest. */
+ * the split kernels, 2000 + b for their load-first variant (four z cells per
+ * thread) compiled for b resident blocks per SM (b = 3, 4, 5; blocks walk theta
+ * fastest), 2010 + b for the same with the blocks walking z fastest (b = 3, 4),
+ * 2100 + b for two z cells per thread (b = 6, 8), 2200 + 10 c + b for interior /
+ * edge split launches (a kernel with the interior body only on the tiles away
+ * from every PML and end, compiled for b blocks per SM, and the general kernel
+ * on the rest; c = 0: four cells per thread, b = 4, 5; c = 1: two, b = 6, 8);
+ * v * 10000 + s (a pair code) for the velocity kernel of split code v with the
+ * stress kernel of split code s.  opts.tile accepts every code listed here. */
 int sim_config(const sim_t *h, int *kernel, int *tile_rows);
 
 /* Kernel timings gathered with opts.timing = 1: for kernel slot q

@@ -216,14 +216,30 @@ cudaError_t launch_march(int storage, int code, const FusedMaps &maps, const KPa
                          cudaEvent_t *ev, int parts = 3);
 size_t march_smem_bytes(int storage, int code);
 // split path: tile code 2000 = the kernels of stencil_split.cu; 2000 + 10 o + b
-// = the load-first kernels of stencil_hoist.cu with b resident blocks per SM
-// asked of the register allocator (b = 3, 4 or 5) and block order o (0: theta
-// fastest, 1: z fastest; b = 3 or 4 only)
+// = the load-first kernels of stencil_hoist.cu (four z cells per thread) with b
+// resident blocks per SM asked of the register allocator (b = 3, 4 or 5) and
+// block order o (0: theta fastest, 1: z fastest; b = 3 or 4 only); 2100 + b =
+// the two-cells-per-thread variant, theta fastest (b = 6 or 8); 2200 + 10 c + b
+// = interior / edge split launches (a lean-only interior kernel for b blocks per
+// SM, the general kernel on the PML and end tiles), c = 0: four cells per
+// thread (b = 4 or 5), c = 1: two cells (b = 6 or 8).  A pair code
+// v * 10000 + s runs the velocity kernel of split code v and the stress kernel
+// of split code s (the autotuner times the two apart).
 constexpr int SPLIT_CODE = 2000;
-inline bool is_split_family(int code) { return code >= 2000 && code < 3000; }
+inline bool is_split_single(int code) { return code >= 2000 && code < 3000; }
+inline bool is_split_pair(int code) {
+  return code >= 10000 && is_split_single(code / 10000) && is_split_single(code % 10000);
+}
+inline bool is_split_family(int code) { return is_split_single(code) || is_split_pair(code); }
+inline int split_vel_code(int code) { return code >= 10000 ? code / 10000 : code; }
+inline int split_str_code(int code) { return code >= 10000 ? code % 10000 : code; }
 inline bool is_hoist(int code) { return code > 2000 && code < 3000; }
 inline int hoist_blocks(int code) { return code % 10; }
-inline bool hoist_zfast(int code) { return (code / 10) % 10 == 1; }
+inline bool hoist_split(int code) { return (code / 100) % 10 == 2; }
+inline bool hoist_zfast(int code) { return !hoist_split(code) && (code / 10) % 10 == 1; }
+inline int hoist_cells_per_thread(int code) {
+  return ((code / 100) % 10 == 1 || (hoist_split(code) && (code / 10) % 10 == 1)) ? 2 : 4;
+}
 cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts = 3);
 // BF16 GEMM on the tcgen05 tensor cores (gemm_tc.cu); status bit 0: a
 // bounded wait gave up (read and cleared by gemm_tcgen05_status)

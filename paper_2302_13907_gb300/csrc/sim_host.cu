@@ -111,7 +111,7 @@ int cwell::validate_inputs(const sim_grid_t *g, const sim_medium_t *m, const sim
                               (o->kernel == SIM_KERNEL_FUSED && t < 100) ||
                               (o->kernel == SIM_KERNEL_FUSED_VEC && t >= 100 && t < 1000) ||
                               (o->kernel == SIM_KERNEL_MARCH && is_march(t)) ||
-                              (o->kernel == SIM_KERNEL_AUTO && t < 3000));
+                              (o->kernel == SIM_KERNEL_AUTO && (t < 3000 || is_split_pair(t))));
     if (!ok) return fail(nullptr, SIM_EINVAL, "opts: tile " + std::to_string(t) + " is not a tile code of the kernel asked for");
   }
   if (o->max_steps < 0) return fail(nullptr, SIM_EINVAL, "opts: max_steps < 0");
@@ -202,9 +202,20 @@ static cudaError_t launch_fused_any(int storage, int code, const FusedMaps &maps
 // Candidates: the fused kernels with each tile height that fits in shared
 // memory, the marching split kernels with each tile height and theta run, and
 // the split kernels (plain and load-first), as far as the requested kernel allows.
+static cudaError_t launch_split_one(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev,
+                                    int parts) {
+  return is_hoist(code) ? launch_hoist(storage, code, p, s, ev, parts) : launch_split(storage, p, s, ev, parts);
+}
+
+// a pair code runs the velocity half of one split code and the stress half of another
 static cudaError_t launch_split_family(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev,
                                        int parts = 3) {
-  return is_hoist(code) ? launch_hoist(storage, code, p, s, ev, parts) : launch_split(storage, p, s, ev, parts);
+  const int v = split_vel_code(code), c = split_str_code(code);
+  if (v == c) return launch_split_one(storage, v, p, s, ev, parts);
+  cudaError_t e = cudaSuccess;
+  if (parts & 1) e = launch_split_one(storage, v, p, s, ev, 1);
+  if (e == cudaSuccess && (parts & 2)) e = launch_split_one(storage, c, p, s, ev, 2);
+  return e;
 }
 
 static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
@@ -221,13 +232,19 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
       return SIM_OK;
     }
   }
-  const int cand[] = {2,    4,    6,    8,    106,  110,  114,  1216, 1232, 1264,
-                      1416, 1432, 1464, 1816, 1832, 1864, 2003, 2004, 2005, 2013, 2014, SPLIT_CODE};
-  cudaEvent_t a, b;
+  const int cand[] = {2,    4,    6,    8,    106,  110,  114,  1216, 1232, 1264, 1416, 1432, 1464, 1816, 1832,
+                      1864, 2003, 2004, 2005, 2013, 2014, 2106, 2108, 2204, 2205, 2216, 2218, SPLIT_CODE};
+  cudaEvent_t a, b, c3;
   CK(h, cudaEventCreate(&a));
   CK(h, cudaEventCreate(&b));
-  float best = INFINITY;
-  int pick = -1;
+  CK(h, cudaEventCreate(&c3));
+  float best = INFINITY, best_v = INFINITY, best_s = INFINITY;
+  int pick = -1, pick_v = -1, pick_s = -1;
+  if (forced && is_split_pair(forced) && allow_split) {  // both halves must be split candidates; nothing to fit
+    bool v = false, c = false;
+    for (int rt : cand) v |= rt == split_vel_code(forced), c |= rt == split_str_code(forced);
+    if (v && c) pick = forced;
+  }
   for (int rt : cand) {
     cudaError_t e = cudaSuccess;
     const bool fused_code = rt < 1000;
@@ -247,13 +264,28 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
       pick = rt;
       break;
     }
-    if (is_split_family(rt)) {
+    if (is_split_family(rt)) {  // each half timed on its own: the best velocity and stress kernels may differ
       KParams dry = h->kp;
       dry.src_i = -1;  // no source: zero state stays zero
       for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_split_family(h->storage, rt, dry, h->stream, nullptr);
       cudaEventRecord(a, h->stream);
-      for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_split_family(h->storage, rt, dry, h->stream, nullptr);
+      for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_split_family(h->storage, rt, dry, h->stream, nullptr, 1);
       cudaEventRecord(b, h->stream);
+      for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_split_family(h->storage, rt, dry, h->stream, nullptr, 2);
+      cudaEventRecord(c3, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(c3);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        cudaEventDestroy(c3);
+        return cuda_fail(h, e, "autotune launch");
+      }
+      float mv = 0, ms = 0;
+      cudaEventElapsedTime(&mv, a, b);
+      cudaEventElapsedTime(&ms, b, c3);
+      if (mv < best_v) best_v = mv, pick_v = rt;
+      if (ms < best_s) best_s = ms, pick_s = rt;
+      continue;
     } else if (is_march(rt)) {
       const size_t need = march_smem_bytes(h->storage, rt);
       if (need == 0 || need > (size_t)maxsm) continue;
@@ -284,6 +316,7 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
     if (e != cudaSuccess) {
       cudaEventDestroy(a);
       cudaEventDestroy(b);
+      cudaEventDestroy(c3);
       return cuda_fail(h, e, "autotune launch");
     }
     float ms = 0;
@@ -295,6 +328,9 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  cudaEventDestroy(c3);
+  if (!forced && pick_v >= 0 && best_v + best_s < best)  // the split family's best halves win
+    pick = pick_v == pick_s ? pick_v : pick_v * 10000 + pick_s;
   if (pick < 0 && forced)
     return fail(h, SIM_EINVAL, "opts.tile " + std::to_string(forced) + " is not a tile of the requested kernel that fits");
   if (pick < 0) return fail(h, SIM_EUNSUPPORTED, "no tile of the requested kernel fits in shared memory");

@@ -3,8 +3,10 @@
 // its arithmetic or stores (one round trip to memory per thread instead of
 // one per component), and the material lookups from the split tables
 // {rho}, {1/mu}, {lambda, lambda + 2 mu}.  Same thread layout (four z cells
-// per thread, 16-byte loads, block = 32 quads x 4 rows, theta fastest across
-// blocks), same arithmetic, same in-place update.
+// per thread, 16-byte loads, block = 32 x 4 threads, theta fastest across
+// blocks), same arithmetic, same in-place update; variants with two z cells
+// per thread (8-byte loads, fewer registers), and interior / edge split
+// launches (a lean-only kernel on the interior tiles).
 #include <algorithm>
 
 #include "cwell_internal.cuh"
@@ -12,25 +14,93 @@
 namespace cwell {
 namespace {
 
-constexpr int HB_X = 32;  // z-quads per block
+constexpr int HB_X = 32;  // threads along z per block (NV cells each)
 constexpr int HB_Y = 4;   // r rows per block
 
 __device__ __forceinline__ float4 z4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-__device__ __forceinline__ void ids4(uint2 u, int (&o)[4]) {
+// NV consecutive values of a row: 16-byte (four FP32) or 8-byte (two FP32,
+// four 16-bit) vector loads and stores, converted to / from FP32
+template <typename T, int NV>
+struct Vec;
+template <typename T>
+struct Vec<T, 4> {
+  static __device__ __forceinline__ void ld(float (&d)[4], const T *p) {
+    const float4 v = St<T>::ld4(p);
+    d[0] = v.x;
+    d[1] = v.y;
+    d[2] = v.z;
+    d[3] = v.w;
+  }
+  static __device__ __forceinline__ void st(T *p, const float (&v)[4]) { St<T>::st4(p, make_float4(v[0], v[1], v[2], v[3])); }
+};
+template <>
+struct Vec<float, 2> {
+  static __device__ __forceinline__ void ld(float (&d)[2], const float *p) {
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    d[0] = v.x;
+    d[1] = v.y;
+  }
+  static __device__ __forceinline__ void st(float *p, const float (&v)[2]) {
+    *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+  }
+};
+template <>
+struct Vec<__nv_bfloat16, 2> {
+  static __device__ __forceinline__ void ld(float (&d)[2], const __nv_bfloat16 *p) {
+    const unsigned u = __ldg(reinterpret_cast<const unsigned *>(p));
+    const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
+    d[0] = v.x;
+    d[1] = v.y;
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16 *p, const float (&v)[2]) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+    *reinterpret_cast<unsigned *>(p) = *reinterpret_cast<const unsigned *>(&a);
+  }
+};
+template <>
+struct Vec<__half, 2> {
+  static __device__ __forceinline__ void ld(float (&d)[2], const __half *p) {
+    const unsigned u = __ldg(reinterpret_cast<const unsigned *>(p));
+    const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(&u));
+    d[0] = v.x;
+    d[1] = v.y;
+  }
+  static __device__ __forceinline__ void st(__half *p, const float (&v)[2]) {
+    const __half2 a = __floats2half2_rn(v[0], v[1]);
+    *reinterpret_cast<unsigned *>(p) = *reinterpret_cast<const unsigned *>(&a);
+  }
+};
+
+template <int NV>
+__device__ __forceinline__ void zero(float (&d)[NV]) {
+#pragma unroll
+  for (int e = 0; e < NV; e++) d[e] = 0.f;
+}
+
+// NV consecutive material IDs (8- or 4-byte load)
+__device__ __forceinline__ void ldids(const uint16_t *p, int (&o)[4]) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
   o[0] = u.x & 0xffff;
   o[1] = u.x >> 16;
   o[2] = u.y & 0xffff;
   o[3] = u.y >> 16;
 }
+__device__ __forceinline__ void ldids(const uint16_t *p, int (&o)[2]) {
+  const unsigned u = __ldg(reinterpret_cast<const unsigned *>(p));
+  o[0] = u & 0xffff;
+  o[1] = u >> 16;
+}
+template <int NV>
+__device__ __forceinline__ void zero_ids(int (&o)[NV]) {
+#pragma unroll
+  for (int e = 0; e < NV; e++) o[e] = 0;
+}
 
-__device__ __forceinline__ uint2 ldid(const uint16_t *p) { return __ldg(reinterpret_cast<const uint2 *>(p)); }
-
-#define E4(v, e) ((e) == 0 ? (v).x : (e) == 1 ? (v).y : (e) == 2 ? (v).z : (v).w)
-
-// LEAN: the four cells are interior (no PML memory variable, all inside NZ,
-// k0 + 4 < NZ); the kernels pick the lean body per thread.
-template <typename T, bool LEAN>
+// NV cells per thread (4 or 2).  LEAN: the NV cells are interior (no PML
+// memory variable, all inside NZ, k0 + NV < NZ); the kernels pick the lean
+// body per thread, or run it alone on the interior tiles.
+template <typename T, int NV, bool LEAN>
 __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, const int i, const int k0) {
   const int nth = p.nth, NR = p.NR, NZ = p.NZ;
   const long long NZp = p.NZp, pl = p.plane;
@@ -41,66 +111,95 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
   const T *srr = (const T *)p.f[F_SRR], *spp = (const T *)p.f[F_SPP], *szz = (const T *)p.f[F_SZZ];
   const T *srp = (const T *)p.f[F_SRP], *spz = (const T *)p.f[F_SPZ], *srz = (const T *)p.f[F_SRZ];
   T *vr = (T *)p.f[F_VR], *vp = (T *)p.f[F_VP], *vz = (T *)p.f[F_VZ];
-  const bool im = i >= 1, ip = i + 1 < NR, k4 = LEAN || k0 + 4 < NZ, km = k0 > 0;
+  const bool im = i >= 1, ip = i + 1 < NR, k4 = LEAN || k0 + NV < NZ, km = k0 > 0;
 
   // ---- every load
-  const float4 a_srr = St<T>::ld4(srr + c), a_spp = St<T>::ld4(spp + c), a_srp = St<T>::ld4(srp + c);
-  const float4 a_srz = St<T>::ld4(srz + c), a_spz = St<T>::ld4(spz + c), a_szz = St<T>::ld4(szz + c);
-  const float szz_k4 = k4 ? St<T>::ld1(szz + c + 4) : 0.f;
+  float a_srr[NV];
+  Vec<T, NV>::ld(a_srr, srr + c);
+  float a_spp[NV];
+  Vec<T, NV>::ld(a_spp, spp + c);
+  float a_srp[NV];
+  Vec<T, NV>::ld(a_srp, srp + c);
+  float a_srz[NV];
+  Vec<T, NV>::ld(a_srz, srz + c);
+  float a_spz[NV];
+  Vec<T, NV>::ld(a_spz, spz + c);
+  float a_szz[NV];
+  Vec<T, NV>::ld(a_szz, szz + c);
+  const float szz_k4 = k4 ? St<T>::ld1(szz + c + NV) : 0.f;
   const float srz_km = km ? St<T>::ld1(srz + c - 1) : 0.f, spz_km = km ? St<T>::ld1(spz + c - 1) : 0.f;
-  const float4 m_srr = im ? St<T>::ld4(srr + c - NZp) : z4(), m_spp = im ? St<T>::ld4(spp + c - NZp) : z4();
-  const float4 jm_srp = St<T>::ld4(srp + cjm), jm_spz = St<T>::ld4(spz + cjm);
-  const float4 p_srp = ip ? St<T>::ld4(srp + c + NZp) : z4(), p_srz = ip ? St<T>::ld4(srz + c + NZp) : z4();
-  const float4 jp_spp = St<T>::ld4(spp + cjp);
-  const float4 o_vr = St<T>::ld4(vr + c), o_vp = St<T>::ld4(vp + c), o_vz = St<T>::ld4(vz + c);
-  const uint2 u_c = ldid(p.id + c), u_j = ldid(p.id + cjp), u_m = im ? ldid(p.id + c - NZp) : make_uint2(0, 0);
+  float m_srr[NV];
+  if (im) Vec<T, NV>::ld(m_srr, srr + c - NZp);
+  else zero(m_srr);
+  float m_spp[NV];
+  if (im) Vec<T, NV>::ld(m_spp, spp + c - NZp);
+  else zero(m_spp);
+  float jm_srp[NV];
+  Vec<T, NV>::ld(jm_srp, srp + cjm);
+  float jm_spz[NV];
+  Vec<T, NV>::ld(jm_spz, spz + cjm);
+  float p_srp[NV];
+  if (ip) Vec<T, NV>::ld(p_srp, srp + c + NZp);
+  else zero(p_srp);
+  float p_srz[NV];
+  if (ip) Vec<T, NV>::ld(p_srz, srz + c + NZp);
+  else zero(p_srz);
+  float jp_spp[NV];
+  Vec<T, NV>::ld(jp_spp, spp + cjp);
+  float o_vr[NV];
+  Vec<T, NV>::ld(o_vr, vr + c);
+  float o_vp[NV];
+  Vec<T, NV>::ld(o_vp, vp + c);
+  float o_vz[NV];
+  Vec<T, NV>::ld(o_vz, vz + c);
+  int idc[NV], idj[NV], idm[NV];
+  ldids(p.id + c, idc);
+  ldids(p.id + cjp, idj);
+  if (im) ldids(p.id + c - NZp, idm);
+  else zero_ids(idm);
   int id_k4 = 0;
-  if (k4) id_k4 = __ldg(p.id + c + 4);
+  if (k4) id_k4 = __ldg(p.id + c + NV);
   const bool rp = !LEAN && i >= p.nr;
   const float inv_ri = __ldg(p.inv_ri + i), inv_rh = __ldg(p.inv_rh + i);
   const float4 abr = __ldg(p.ab_r + i), abq = __ldg(p.ab_q + i);
 
-  int idc[4], idj[4], idm[4];
-  ids4(u_c, idc);
-  ids4(u_j, idj);
-  ids4(u_m, idm);
-  if (!k4) id_k4 = idc[3];
-  float rho_c[5], rho_j[4], rho_m[4];
+  if (!k4) id_k4 = idc[NV - 1];
+  float rho_c[NV + 1], rho_j[NV], rho_m[NV];
 #pragma unroll
-  for (int e = 0; e < 4; e++) {
+  for (int e = 0; e < NV; e++) {
     rho_c[e] = __ldg(p.m_rho + idc[e]);
     rho_j[e] = __ldg(p.m_rho + idj[e]);
     rho_m[e] = __ldg(p.m_rho + idm[e]);
   }
-  rho_c[4] = __ldg(p.m_rho + id_k4);
+  rho_c[NV] = __ldg(p.m_rho + id_k4);
 
   const long long cr = rp ? ((long long)j * p.pml_r + (i - p.nr)) * NZp + k0 : 0;
   const float dtv = p.dtv, idr = p.inv_dr, idz = p.inv_dz, idth = p.inv_dth;
   const int pz = p.pml_z;
   const long long czrow = ((long long)j * NR + i) * (2 * pz);
-  const bool zl = !LEAN && pz > 0 && (k0 < pz || k0 + 3 >= NZ - pz);
+  const bool zl = !LEAN && pz > 0 && (k0 < pz || k0 + NV - 1 >= NZ - pz);
 
-  float out_r[4], out_p[4], out_z[4];
+  float out_r[NV], out_p[NV], out_z[NV];
 #pragma unroll
-  for (int e = 0; e < 4; e++) {
-    out_r[e] = E4(o_vr, e);
-    out_p[e] = E4(o_vp, e);
-    out_z[e] = E4(o_vz, e);
+  for (int e = 0; e < NV; e++) {
+    out_r[e] = o_vr[e];
+    out_p[e] = o_vp[e];
+    out_z[e] = o_vz[e];
   }
 #pragma unroll
-  for (int e = 0; e < 4; e++) {
+  for (int e = 0; e < NV; e++) {
     const int k = k0 + e;
     if (!LEAN && k >= NZ) break;
     const bool zp = zl && (k < pz || k >= NZ - pz);
     const int kz = k < pz ? k : k - (NZ - 2 * pz);
     const float4 abz = zp ? __ldg(p.ab_z + k) : z4();
-    const float srr_e = E4(a_srr, e), spp_e = E4(a_spp, e), srp_e = E4(a_srp, e);
-    const float srz_e = E4(a_srz, e), spz_e = E4(a_spz, e), szz_e = E4(a_szz, e);
-    const float srz_m1 = e ? E4(a_srz, e - 1) : srz_km, spz_m1 = e ? E4(a_spz, e - 1) : spz_km;
+    const float srr_e = a_srr[e], spp_e = a_spp[e], srp_e = a_srp[e];
+    const float srz_e = a_srz[e], spz_e = a_spz[e], szz_e = a_szz[e];
+    const float srz_m1 = e ? a_srz[e - 1] : srz_km, spz_m1 = e ? a_spz[e - 1] : spz_km;
     // v_r at (r_i, theta_j, z_k), i >= 1
     if (im) {
-      float Dr = (srr_e - E4(m_srr, e)) * idr;
-      float Q = (0.5f * (srr_e + E4(m_srr, e)) - 0.5f * (spp_e + E4(m_spp, e)) + (srp_e - E4(jm_srp, e)) * idth) *
+      float Dr = (srr_e - m_srr[e]) * idr;
+      float Q = (0.5f * (srr_e + m_srr[e]) - 0.5f * (spp_e + m_spp[e]) + (srp_e - jm_srp[e]) * idth) *
                 inv_ri;
       float Dz = (srz_e - srz_m1) * idz;
       if (rp) {
@@ -112,9 +211,9 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
     }
     // v_phi at (r_{i+1/2}, theta_{j+1/2}, z_k)
     {
-      const float s1 = E4(p_srp, e);
+      const float s1 = p_srp[e];
       float Dr = (s1 - srp_e) * idr;
-      float Q = ((s1 + srp_e) + (E4(jp_spp, e) - spp_e) * idth) * inv_rh;
+      float Q = ((s1 + srp_e) + (jp_spp[e] - spp_e) * idth) * inv_rh;
       float Dz = (spz_e - spz_m1) * idz;
       if (rp) {
         Dr = stretch(p.psr[R_VP] + cr + e, abr.z, abr.w, Dr);
@@ -125,10 +224,10 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
     }
     // v_z at (r_{i+1/2}, theta_j, z_{k+1/2}), k + 1 < NZ
     if (LEAN || k + 1 < NZ) {
-      const float s1 = E4(p_srz, e);
+      const float s1 = p_srz[e];
       float Dr = (s1 - srz_e) * idr;
-      float Q = (0.5f * (s1 + srz_e) + (spz_e - E4(jm_spz, e)) * idth) * inv_rh;
-      float Dz = ((e < 3 ? E4(a_szz, e + 1) : szz_k4) - szz_e) * idz;
+      float Q = (0.5f * (s1 + srz_e) + (spz_e - jm_spz[e]) * idth) * inv_rh;
+      float Dz = ((e < NV - 1 ? a_szz[e + 1] : szz_k4) - szz_e) * idz;
       if (rp) {
         Dr = stretch(p.psr[R_VZ] + cr + e, abr.z, abr.w, Dr);
         Q = stretch(p.psr[Q_VZ] + cr + e, abq.z, abq.w, Q);
@@ -137,12 +236,12 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
       out_z[e] += vel_coef(dtv, rho_c[e] + rho_c[e + 1]) * (Dr + Q + Dz);
     }
   }
-  if (im) St<T>::st4(vr + c, make_float4(out_r[0], out_r[1], out_r[2], out_r[3]));
-  St<T>::st4(vp + c, make_float4(out_p[0], out_p[1], out_p[2], out_p[3]));
-  St<T>::st4(vz + c, make_float4(out_z[0], out_z[1], out_z[2], out_z[3]));
+  if (im) Vec<T, NV>::st(vr + c, out_r);
+  Vec<T, NV>::st(vp + c, out_p);
+  Vec<T, NV>::st(vz + c, out_z);
 }
 
-template <typename T, bool LEAN>
+template <typename T, int NV, bool LEAN>
 __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, const int i, const int k0) {
   const int nth = p.nth, NR = p.NR, NZ = p.NZ;
   const long long NZp = p.NZp, pl = p.plane;
@@ -153,90 +252,119 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
   const T *vr = (const T *)p.f[F_VR], *vp = (const T *)p.f[F_VP], *vz = (const T *)p.f[F_VZ];
   T *srr = (T *)p.f[F_SRR], *spp = (T *)p.f[F_SPP], *szz = (T *)p.f[F_SZZ];
   T *srp = (T *)p.f[F_SRP], *spz = (T *)p.f[F_SPZ], *srz = (T *)p.f[F_SRZ];
-  const bool im = i >= 1, ip = i + 1 < NR, k4 = LEAN || k0 + 4 < NZ, km = k0 > 0;
+  const bool im = i >= 1, ip = i + 1 < NR, k4 = LEAN || k0 + NV < NZ, km = k0 > 0;
 
   // ---- every load
-  const float4 a_vr = St<T>::ld4(vr + c), a_vp = St<T>::ld4(vp + c), a_vz = St<T>::ld4(vz + c);
-  const float vr_k4 = k4 ? St<T>::ld1(vr + c + 4) : 0.f, vp_k4 = k4 ? St<T>::ld1(vp + c + 4) : 0.f;
+  float a_vr[NV];
+  Vec<T, NV>::ld(a_vr, vr + c);
+  float a_vp[NV];
+  Vec<T, NV>::ld(a_vp, vp + c);
+  float a_vz[NV];
+  Vec<T, NV>::ld(a_vz, vz + c);
+  const float vr_k4 = k4 ? St<T>::ld1(vr + c + NV) : 0.f, vp_k4 = k4 ? St<T>::ld1(vp + c + NV) : 0.f;
   const float vz_km = km ? St<T>::ld1(vz + c - 1) : 0.f;
-  const float4 p_vr = ip ? St<T>::ld4(vr + c + NZp) : z4();
-  const float4 jm_vp = St<T>::ld4(vp + cjm);
-  const float4 m_vp = im ? St<T>::ld4(vp + c - NZp) : z4(), m_vz = im ? St<T>::ld4(vz + c - NZp) : z4();
-  const float4 jp_vr = St<T>::ld4(vr + cjp), jp_vz = St<T>::ld4(vz + cjp);
-  const float4 o_rr = St<T>::ld4(srr + c), o_pp = St<T>::ld4(spp + c), o_zz = St<T>::ld4(szz + c);
-  const float4 o_rp = St<T>::ld4(srp + c), o_pz = St<T>::ld4(spz + c), o_rz = St<T>::ld4(srz + c);
-  const uint2 u_c = ldid(p.id + c), u_j = ldid(p.id + cjp);
-  const uint2 u_m = im ? ldid(p.id + c - NZp) : make_uint2(0, 0), u_jm = im ? ldid(p.id + cjp - NZp) : make_uint2(0, 0);
+  float p_vr[NV];
+  if (ip) Vec<T, NV>::ld(p_vr, vr + c + NZp);
+  else zero(p_vr);
+  float jm_vp[NV];
+  Vec<T, NV>::ld(jm_vp, vp + cjm);
+  float m_vp[NV];
+  if (im) Vec<T, NV>::ld(m_vp, vp + c - NZp);
+  else zero(m_vp);
+  float m_vz[NV];
+  if (im) Vec<T, NV>::ld(m_vz, vz + c - NZp);
+  else zero(m_vz);
+  float jp_vr[NV];
+  Vec<T, NV>::ld(jp_vr, vr + cjp);
+  float jp_vz[NV];
+  Vec<T, NV>::ld(jp_vz, vz + cjp);
+  float o_rr[NV];
+  Vec<T, NV>::ld(o_rr, srr + c);
+  float o_pp[NV];
+  Vec<T, NV>::ld(o_pp, spp + c);
+  float o_zz[NV];
+  Vec<T, NV>::ld(o_zz, szz + c);
+  float o_rp[NV];
+  Vec<T, NV>::ld(o_rp, srp + c);
+  float o_pz[NV];
+  Vec<T, NV>::ld(o_pz, spz + c);
+  float o_rz[NV];
+  Vec<T, NV>::ld(o_rz, srz + c);
+  int idc[NV], idj[NV], idm[NV], idjm[NV];
+  ldids(p.id + c, idc);
+  ldids(p.id + cjp, idj);
+  if (im) {
+    ldids(p.id + c - NZp, idm);
+    ldids(p.id + cjp - NZp, idjm);
+  } else {
+    zero_ids(idm);
+    zero_ids(idjm);
+  }
   int idc4 = 0, idj4 = 0, idm4 = 0;
   if (k4) {
-    idc4 = __ldg(p.id + c + 4);
-    idj4 = __ldg(p.id + cjp + 4);
-    if (im) idm4 = __ldg(p.id + c - NZp + 4);
+    idc4 = __ldg(p.id + c + NV);
+    idj4 = __ldg(p.id + cjp + NV);
+    if (im) idm4 = __ldg(p.id + c - NZp + NV);
   }
   const bool rp = !LEAN && i >= p.nr;
   const float inv_ri = __ldg(p.inv_ri + i), inv_rh = __ldg(p.inv_rh + i);
   const float4 abr = __ldg(p.ab_r + i), abq = __ldg(p.ab_q + i);
-  float src[4] = {0.f, 0.f, 0.f, 0.f};
-  if (i == p.src_i && (p.src_j < 0 || p.src_j == j) && p.src_k >= k0 && p.src_k < k0 + 4) {
+  float src[NV] = {};
+  if (i == p.src_i && (p.src_j < 0 || p.src_j == j) && p.src_k >= k0 && p.src_k < k0 + NV) {
     const int n = *p.step;
     src[p.src_k - k0] = n < p.n_wav ? __ldg(p.wav + n) : 0.f;
   }
 
-  int idc[4], idj[4], idm[4], idjm[4];
-  ids4(u_c, idc);
-  ids4(u_j, idj);
-  ids4(u_m, idm);
-  ids4(u_jm, idjm);
   if (!k4) {
-    idc4 = idc[3];
-    idj4 = idj[3];
-    idm4 = idm[3];
+    idc4 = idc[NV - 1];
+    idj4 = idj[NV - 1];
+    idm4 = idm[NV - 1];
   }
-  float imu_c[5], imu_j[5], imu_m[5], imu_jm[4];
-  float2 lam[4];
+  float imu_c[NV + 1], imu_j[NV + 1], imu_m[NV + 1], imu_jm[NV];
+  float2 lam[NV];
 #pragma unroll
-  for (int e = 0; e < 4; e++) {
+  for (int e = 0; e < NV; e++) {
     imu_c[e] = __ldg(p.m_imu + idc[e]);
     imu_j[e] = __ldg(p.m_imu + idj[e]);
     imu_m[e] = __ldg(p.m_imu + idm[e]);
     imu_jm[e] = __ldg(p.m_imu + idjm[e]);
     lam[e] = __ldg(p.m_lam + idc[e]);
   }
-  imu_c[4] = __ldg(p.m_imu + idc4);
-  imu_j[4] = __ldg(p.m_imu + idj4);
-  imu_m[4] = __ldg(p.m_imu + idm4);
+  imu_c[NV] = __ldg(p.m_imu + idc4);
+  imu_j[NV] = __ldg(p.m_imu + idj4);
+  imu_m[NV] = __ldg(p.m_imu + idm4);
 
   const long long cr = rp ? ((long long)j * p.pml_r + (i - p.nr)) * NZp + k0 : 0;
   const float dts = p.dts, idr = p.inv_dr, idz = p.inv_dz, idth = p.inv_dth;
   const int pz = p.pml_z;
   const long long czrow = ((long long)j * NR + i) * (2 * pz);
-  const bool zl = !LEAN && pz > 0 && (k0 < pz || k0 + 3 >= NZ - pz);
+  const bool zl = !LEAN && pz > 0 && (k0 < pz || k0 + NV - 1 >= NZ - pz);
 
-  float orr[4], opp[4], ozz[4], orp[4], opz[4], orz[4];
+  float orr[NV], opp[NV], ozz[NV], orp[NV], opz[NV], orz[NV];
 #pragma unroll
-  for (int e = 0; e < 4; e++) {
-    orr[e] = E4(o_rr, e);
-    opp[e] = E4(o_pp, e);
-    ozz[e] = E4(o_zz, e);
-    orp[e] = E4(o_rp, e);
-    opz[e] = E4(o_pz, e);
-    orz[e] = E4(o_rz, e);
+  for (int e = 0; e < NV; e++) {
+    orr[e] = o_rr[e];
+    opp[e] = o_pp[e];
+    ozz[e] = o_zz[e];
+    orp[e] = o_rp[e];
+    opz[e] = o_pz[e];
+    orz[e] = o_rz[e];
   }
 #pragma unroll
-  for (int e = 0; e < 4; e++) {
+  for (int e = 0; e < NV; e++) {
     const int k = k0 + e;
     if (!LEAN && k >= NZ) break;
     const bool zp = zl && (k < pz || k >= NZ - pz);
     const int kz = k < pz ? k : k - (NZ - 2 * pz);
     const float4 abz = zp ? __ldg(p.ab_z + k) : z4();
-    const float vr_e = E4(a_vr, e), vp_e = E4(a_vp, e), vz_e = E4(a_vz, e);
-    const float vr_e1 = e < 3 ? E4(a_vr, e + 1) : vr_k4, vp_e1 = e < 3 ? E4(a_vp, e + 1) : vp_k4;
-    const float vz_m1 = e ? E4(a_vz, e - 1) : vz_km;
+    const float vr_e = a_vr[e], vp_e = a_vp[e], vz_e = a_vz[e];
+    const float vr_e1 = e < NV - 1 ? a_vr[e + 1] : vr_k4, vp_e1 = e < NV - 1 ? a_vp[e + 1] : vp_k4;
+    const float vz_m1 = e ? a_vz[e - 1] : vz_km;
     // normal stresses at the cell centre
     {
-      const float vr1 = E4(p_vr, e);
+      const float vr1 = p_vr[e];
       float err = (vr1 - vr_e) * idr;
-      float epp = ((vp_e - E4(jm_vp, e)) * idth + 0.5f * (vr_e + vr1)) * inv_rh;
+      float epp = ((vp_e - jm_vp[e]) * idth + 0.5f * (vr_e + vr1)) * inv_rh;
       float ezz = (vz_e - vz_m1) * idz;
       if (rp) {
         err = stretch(p.psr[R_ERR] + cr + e, abr.z, abr.w, err);
@@ -251,8 +379,8 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
     if (im) {
       // s_rphi at (r_i, theta_{j+1/2}, z_k)
       {
-        float gr = (vp_e - E4(m_vp, e)) * idr;
-        float Q = ((E4(jp_vr, e) - vr_e) * idth - 0.5f * (vp_e + E4(m_vp, e))) * inv_ri;
+        float gr = (vp_e - m_vp[e]) * idr;
+        float Q = ((jp_vr[e] - vr_e) * idth - 0.5f * (vp_e + m_vp[e])) * inv_ri;
         if (rp) {
           gr = stretch(p.psr[R_GRP] + cr + e, abr.x, abr.y, gr);
           Q = stretch(p.psr[Q_GRP] + cr + e, abq.x, abq.y, Q);
@@ -263,7 +391,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
       // s_rz at (r_i, theta_j, z_{k+1/2})
       if (LEAN || k + 1 < NZ) {
         float gz = (vr_e1 - vr_e) * idz;
-        float gr = (vz_e - E4(m_vz, e)) * idr;
+        float gr = (vz_e - m_vz[e]) * idr;
         if (zp) gz = stretch(p.psz[Z_GRZ] + czrow + kz, abz.z, abz.w, gz);
         if (rp) gr = stretch(p.psr[R_GRZ] + cr + e, abr.x, abr.y, gr);
         const float mu = mu_harm(imu_m[e] + imu_c[e] + imu_m[e + 1] + imu_c[e + 1]);
@@ -272,7 +400,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
     }
     // s_phiz at (r_{i+1/2}, theta_{j+1/2}, z_{k+1/2})
     if (LEAN || k + 1 < NZ) {
-      float Q = (E4(jp_vz, e) - vz_e) * idth * inv_rh;
+      float Q = (jp_vz[e] - vz_e) * idth * inv_rh;
       float gz = (vp_e1 - vp_e) * idz;
       if (rp) Q = stretch(p.psr[Q_GPZ] + cr + e, abq.z, abq.w, Q);
       if (zp) gz = stretch(p.psz[Z_GPZ] + czrow + kz, abz.z, abz.w, gz);
@@ -280,28 +408,29 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
       opz[e] += dts * mu * (Q + gz);
     }
   }
-  St<T>::st4(srr + c, make_float4(orr[0], orr[1], orr[2], orr[3]));
-  St<T>::st4(spp + c, make_float4(opp[0], opp[1], opp[2], opp[3]));
-  St<T>::st4(szz + c, make_float4(ozz[0], ozz[1], ozz[2], ozz[3]));
+  Vec<T, NV>::st(srr + c, orr);
+  Vec<T, NV>::st(spp + c, opp);
+  Vec<T, NV>::st(szz + c, ozz);
   if (im) {
-    St<T>::st4(srp + c, make_float4(orp[0], orp[1], orp[2], orp[3]));
-    St<T>::st4(srz + c, make_float4(orz[0], orz[1], orz[2], orz[3]));
+    Vec<T, NV>::st(srp + c, orp);
+    Vec<T, NV>::st(srz + c, orz);
   }
-  St<T>::st4(spz + c, make_float4(opz[0], opz[1], opz[2], opz[3]));
+  Vec<T, NV>::st(spz + c, opz);
 }
 
-__device__ __forceinline__ bool lean_quad(const KParams &p, int i, int k0) {
-  return i < p.nr && k0 >= p.pml_z && k0 + 4 < p.NZ - p.pml_z;
+template <int NV>
+__device__ __forceinline__ bool lean_cells(const KParams &p, int i, int k0) {
+  return i < p.nr && k0 >= p.pml_z && k0 + NV < p.NZ - p.pml_z;
 }
 
-template <typename T, bool VEL>
-__device__ __forceinline__ void hoist_quad(const KParams &p, int j, int i, int k0) {
-  if (lean_quad(p, i, k0)) {
-    if (VEL) vel_hoist_body<T, true>(p, j, i, k0);
-    else str_hoist_body<T, true>(p, j, i, k0);
+template <typename T, int NV, bool VEL>
+__device__ __forceinline__ void hoist_cells(const KParams &p, int j, int i, int k0) {
+  if (lean_cells<NV>(p, i, k0)) {
+    if (VEL) vel_hoist_body<T, NV, true>(p, j, i, k0);
+    else str_hoist_body<T, NV, true>(p, j, i, k0);
   } else {
-    if (VEL) vel_hoist_body<T, false>(p, j, i, k0);
-    else str_hoist_body<T, false>(p, j, i, k0);
+    if (VEL) vel_hoist_body<T, NV, false>(p, j, i, k0);
+    else str_hoist_body<T, NV, false>(p, j, i, k0);
   }
 }
 
@@ -309,26 +438,78 @@ __device__ __forceinline__ void hoist_quad(const KParams &p, int j, int i, int k
 // z = z tile: co-resident blocks share theta-neighbour rows); ZF = true walks
 // z fastest (x = z tile, y = r tile, z = theta: co-resident blocks stream
 // whole rows, theta neighbours come back from L2).
-template <bool ZF>
+template <bool ZF, int NV>
 __device__ __forceinline__ void block_cell(int &j, int &i, int &k0) {
   const int zt = ZF ? blockIdx.x : blockIdx.z;
   j = ZF ? blockIdx.z : blockIdx.x;
   i = blockIdx.y * HB_Y + threadIdx.y;
-  k0 = (zt * HB_X + threadIdx.x) * 4;
+  k0 = (zt * HB_X + threadIdx.x) * NV;
 }
 
-template <typename T, int MINB, bool ZF>
+template <typename T, int NV, int MINB, bool ZF>
 __global__ void __launch_bounds__(HB_X *HB_Y, MINB) vel_hoist(const KParams p) {
   int j, i, k0;
-  block_cell<ZF>(j, i, k0);
-  if (i < p.NR && k0 < p.NZ) hoist_quad<T, true>(p, j, i, k0);
+  block_cell<ZF, NV>(j, i, k0);
+  if (i < p.NR && k0 < p.NZ) hoist_cells<T, NV, true>(p, j, i, k0);
 }
 
-template <typename T, int MINB, bool ZF>
+template <typename T, int NV, int MINB, bool ZF>
 __global__ void __launch_bounds__(HB_X *HB_Y, MINB) str_hoist(const KParams p) {
   int j, i, k0;
-  block_cell<ZF>(j, i, k0);
-  if (i < p.NR && k0 < p.NZ) hoist_quad<T, false>(p, j, i, k0);
+  block_cell<ZF, NV>(j, i, k0);
+  if (i < p.NR && k0 < p.NZ) hoist_cells<T, NV, false>(p, j, i, k0);
+}
+
+// Interior / edge split: the interior tiles (every row outside the radial
+// PML, every cell of the tile away from the z PML and the z end) run a kernel
+// compiled with the lean body only, so it needs fewer registers and more
+// blocks fit on an SM; the remaining tiles (radial-PML rows, the z ends) run
+// the per-thread lean / general dispatch.  Both walk theta fastest.
+struct Split2 {
+  int nrt_in;        // r tiles whose rows are all outside the radial PML
+  int zt_lo, zt_hi;  // interior z tiles: zt_lo <= zt < zt_hi
+  int nrt, nzt;      // all r and z tiles
+};
+
+template <int NV>
+Split2 split2(const KParams &p) {
+  const int W = NV * HB_X;
+  Split2 q;
+  q.nrt = (p.NR + HB_Y - 1) / HB_Y;
+  q.nzt = (p.NZ + W - 1) / W;
+  q.nrt_in = p.nr / HB_Y;
+  q.zt_lo = (p.pml_z + W - 1) / W;
+  q.zt_hi = std::max(q.zt_lo, (p.NZ - p.pml_z - 1) / W);  // (zt + 1) W <= NZ - pml_z - 1
+  return q;
+}
+
+template <typename T, int NV, int MINB, bool VEL>
+__global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_interior(const KParams p, int zt_lo) {
+  const int j = blockIdx.x, i = blockIdx.y * HB_Y + threadIdx.y;
+  const int k0 = ((zt_lo + blockIdx.z) * HB_X + threadIdx.x) * NV;
+  if (VEL) vel_hoist_body<T, NV, true>(p, j, i, k0);
+  else str_hoist_body<T, NV, true>(p, j, i, k0);
+}
+
+// edge tile t: first the r tiles nrt_in .. nrt-1 with every z tile, then the
+// interior r tiles with the z tiles below zt_lo and from zt_hi on
+template <typename T, int NV, int MINB, bool VEL>
+__global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_edge(const KParams p, Split2 q) {
+  const int j = blockIdx.x;
+  int t = blockIdx.y, rt, zt;
+  const int a = (q.nrt - q.nrt_in) * q.nzt;
+  if (t < a) {
+    rt = q.nrt_in + t / q.nzt;
+    zt = t % q.nzt;
+  } else {
+    t -= a;
+    const int nlo = q.zt_lo, nz_edge = q.zt_lo + (q.nzt - q.zt_hi);
+    rt = t / nz_edge;
+    const int e = t % nz_edge;
+    zt = e < nlo ? e : q.zt_hi + (e - nlo);
+  }
+  const int i = rt * HB_Y + threadIdx.y, k0 = (zt * HB_X + threadIdx.x) * NV;
+  if (i < p.NR && k0 < p.NZ) hoist_cells<T, NV, VEL>(p, j, i, k0);
 }
 
 // Batched scenarios: the blocks walk the work list of up to BATCH_MAX cases,
@@ -361,36 +542,83 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) batch_hoist(const __grid_con
     const int j = q % nth;
     q /= nth;
     const int i = (q % nrt) * HB_Y + threadIdx.y, k0 = ((q / nrt) * HB_X + threadIdx.x) * 4;
-    if (i < p.NR && k0 < p.NZ) hoist_quad<T, VEL>(p, j, i, k0);
+    if (i < p.NR && k0 < p.NZ) hoist_cells<T, 4, VEL>(p, j, i, k0);
   }
 }
 
-template <typename T, int MINB, bool ZF>
+template <typename T, int NV, int MINB_IN, int MINB_EDGE, bool VEL>
+cudaError_t launch_split2_half(const KParams &p, const Split2 &q, cudaStream_t s) {
+  dim3 blk(HB_X, HB_Y);
+  const int nin = q.zt_hi - q.zt_lo;
+  if (q.nrt_in > 0 && nin > 0)
+    hoist_interior<T, NV, MINB_IN, VEL><<<dim3(p.nth, q.nrt_in, nin), blk, 0, s>>>(p, q.zt_lo);
+  const long long nedge = (long long)(q.nrt - q.nrt_in) * q.nzt + (long long)q.nrt_in * (q.zt_lo + q.nzt - q.zt_hi);
+  if (nedge > 65535 || p.nth > 65535) return cudaErrorInvalidValue;
+  if (nedge > 0) hoist_edge<T, NV, MINB_EDGE, VEL><<<dim3(p.nth, (unsigned)nedge), blk, 0, s>>>(p, q);
+  return cudaGetLastError();
+}
+
+template <typename T, int NV, int MINB_IN, int MINB_EDGE>
+cudaError_t launch_split2_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
+  const Split2 q = split2<NV>(p);
+  if (q.zt_hi - q.zt_lo > 65535) return cudaErrorInvalidValue;
+  cudaError_t e = cudaSuccess;
+  if (parts & 1) {
+    if (ev) cudaEventRecord(ev[0], s);
+    e = launch_split2_half<T, NV, MINB_IN, MINB_EDGE, true>(p, q, s);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], s);
+  }
+  if (parts & 2) {
+    e = launch_split2_half<T, NV, MINB_IN, MINB_EDGE, false>(p, q, s);
+    if (ev) cudaEventRecord(ev[2], s);
+  }
+  return e;
+}
+
+template <typename T, int NV, int MINB, bool ZF>
 cudaError_t launch_hoist_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
   dim3 blk(HB_X, HB_Y);
-  const int nzt = (p.NZ + 4 * HB_X - 1) / (4 * HB_X), nrt = (p.NR + HB_Y - 1) / HB_Y;
+  const int nzt = (p.NZ + NV * HB_X - 1) / (NV * HB_X), nrt = (p.NR + HB_Y - 1) / HB_Y;
   if (nzt > 65535 || p.nth > 65535) return cudaErrorInvalidValue;
   dim3 grd = ZF ? dim3(nzt, nrt, p.nth) : dim3(p.nth, nrt, nzt);
   if (parts & 1) {
     if (ev) cudaEventRecord(ev[0], s);
-    vel_hoist<T, MINB, ZF><<<grd, blk, 0, s>>>(p);
+    vel_hoist<T, NV, MINB, ZF><<<grd, blk, 0, s>>>(p);
     if (ev) cudaEventRecord(ev[1], s);
   }
   if (parts & 2) {
-    str_hoist<T, MINB, ZF><<<grd, blk, 0, s>>>(p);
+    str_hoist<T, NV, MINB, ZF><<<grd, blk, 0, s>>>(p);
     if (ev) cudaEventRecord(ev[2], s);
   }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_hoist_st(int minb, bool zf, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
+cudaError_t launch_hoist_st(int nv, int minb, bool zf, bool split, const KParams &p, cudaStream_t s, cudaEvent_t *ev,
+                            int parts) {
+  if (split) {  // interior kernel compiled for minb blocks per SM, edge kernel for the general body's budget
+    switch (nv * 10 + minb) {
+      case 44: return launch_split2_t<T, 4, 4, 4>(p, s, ev, parts);
+      case 45: return launch_split2_t<T, 4, 5, 4>(p, s, ev, parts);
+      case 26: return launch_split2_t<T, 2, 6, 6>(p, s, ev, parts);
+      case 28: return launch_split2_t<T, 2, 8, 6>(p, s, ev, parts);
+    }
+    return cudaErrorInvalidValue;
+  }
+  if (nv == 2) {
+    switch (minb) {
+      case 6: return launch_hoist_t<T, 2, 6, false>(p, s, ev, parts);
+      case 8: return launch_hoist_t<T, 2, 8, false>(p, s, ev, parts);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (minb * 2 + (zf ? 1 : 0)) {
-    case 6: return launch_hoist_t<T, 3, false>(p, s, ev, parts);
-    case 7: return launch_hoist_t<T, 3, true>(p, s, ev, parts);
-    case 8: return launch_hoist_t<T, 4, false>(p, s, ev, parts);
-    case 9: return launch_hoist_t<T, 4, true>(p, s, ev, parts);
-    case 10: return launch_hoist_t<T, 5, false>(p, s, ev, parts);
+    case 6: return launch_hoist_t<T, 4, 3, false>(p, s, ev, parts);
+    case 7: return launch_hoist_t<T, 4, 3, true>(p, s, ev, parts);
+    case 8: return launch_hoist_t<T, 4, 4, false>(p, s, ev, parts);
+    case 9: return launch_hoist_t<T, 4, 4, true>(p, s, ev, parts);
+    case 10: return launch_hoist_t<T, 4, 5, false>(p, s, ev, parts);
   }
   return cudaErrorInvalidValue;
 }
@@ -434,12 +662,12 @@ cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, cons
 }
 
 cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
-  const int minb = hoist_blocks(code);
-  const bool zf = hoist_zfast(code);
+  const int minb = hoist_blocks(code), nv = hoist_cells_per_thread(code);
+  const bool zf = hoist_zfast(code), split = hoist_split(code);
   switch (storage) {
-    case 0: return launch_hoist_st<float>(minb, zf, p, s, ev, parts);
-    case 1: return launch_hoist_st<__nv_bfloat16>(minb, zf, p, s, ev, parts);
-    case 2: return launch_hoist_st<__half>(minb, zf, p, s, ev, parts);
+    case 0: return launch_hoist_st<float>(nv, minb, zf, split, p, s, ev, parts);
+    case 1: return launch_hoist_st<__nv_bfloat16>(nv, minb, zf, split, p, s, ev, parts);
+    case 2: return launch_hoist_st<__half>(nv, minb, zf, split, p, s, ev, parts);
   }
   return cudaErrorInvalidValue;
 }

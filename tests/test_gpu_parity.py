@@ -292,12 +292,18 @@ def test_march_every_tile_fields_elementwise(tile):
         assert rel_l2(s.traces(), o.traces()) <= TRACE_TOL
 
 
-@pytest.mark.parametrize("tile", (2000, 2003, 2004, 2005, 2013, 2014))
+SPLIT_TILES = (2000, 2003, 2004, 2005, 2013, 2014, 2106, 2108, 2204, 2205, 2216, 2218)
+
+
+@pytest.mark.parametrize("tile", SPLIT_TILES)
 def test_split_variants_fields_elementwise(tile):
     """The split kernels and their load-first variants (every register
-    budget the autotuner may pick) on the same uneven grid: every field
-    against the oracle element by element."""
-    sc = _ragged_scenario(seed=6, nth=12, nr=14, nz=150)
+    budget, cells per thread and interior / edge split the autotuner may
+    pick) on an uneven grid: every field against the oracle element by
+    element.  NZ = 307 and NR = 17 leave interior tiles for both the
+    four- and the two-cells-per-thread split launches, edge tiles in the
+    radial PML, at both z ends and in a ragged z tail."""
+    sc = _ragged_scenario(seed=6, nth=12, nr=14, nz=301)
     o = oracle.Oracle(sc)
     o.step(sc.steps)
     with sim(sc, kernel="split", tile=tile) as s:
@@ -309,6 +315,39 @@ def test_split_variants_fields_elementwise(tile):
             assert scale > 0, n
             assert np.abs(a - b).max() <= 2e-5 * scale, (n, np.abs(a - b).max() / scale)
         assert rel_l2(s.traces(), o.traces()) <= TRACE_TOL
+
+
+@pytest.mark.parametrize("tile", (2204, 2205, 2216, 2218))
+def test_interior_edge_split_on_config1(tile):
+    """The interior / edge split launches on the cased-well geometry, where
+    most tiles are interior: traces and fields against the oracle."""
+    sc = W.config1(steps=300)
+    o = oracle.Oracle(sc)
+    o.step(sc.steps)
+    with sim(sc, kernel="split", tile=tile) as s:
+        assert s.config() == (1, tile)
+        s.step(sc.steps)
+        assert rel_l2(s.traces(), o.traces()) <= TRACE_TOL
+        for n in ("vr", "vz", "srr", "srz", "spp"):
+            assert rel_l2(s.field(n), o.field(n)) <= TRACE_TOL, n
+
+
+def test_split_pair_code_runs_two_variants():
+    """A pair code v * 10000 + s runs the velocity kernel of split code v and
+    the stress kernel of split code s; the scheme is the same, so the fields
+    agree with a single code to FP32 rounding."""
+    sc = _ragged_scenario(seed=8, nth=10, nr=14, nz=301)
+    with sim(sc, kernel="split", tile=2004) as a, sim(sc, kernel="split", tile=22052204) as b:
+        assert b.config() == (1, 22052204)
+        a.step(150)
+        b.step(150)
+        for n in ("vr", "vp", "vz", "srr", "srz", "spz"):
+            x = a.field(n)
+            assert rel_l2(b.field(n), x) <= 1e-6, n
+    from paper_2302_13907_gb300.binding import SIM_EINVAL, SimError
+    with pytest.raises(SimError) as ei:
+        sim(sc, kernel="split", tile=22072204)  # 2207 is not a split code
+    assert ei.value.code == SIM_EINVAL
 
 
 def test_march_rejects_a_tile_it_does_not_have():
@@ -328,10 +367,11 @@ def test_fused_matches_split_and_autotuner_choice():
         ta = a.traces()
         fa = {n: a.field(n) for n in ("vr", "srr", "srz")}
     for kern, kind_want, tiles in (("fused", 2, (2, 4, 6, 8)), ("fused4", 2, (106, 110, 114)),
-                                   ("march", 4, MARCH_TILES), ("split", 1, (2000, 2003, 2004, 2005, 2013, 2014))):
+                                   ("march", 4, MARCH_TILES), ("split", 1, SPLIT_TILES)):
         with sim(sc, kernel=kern) as b:
             kind, tile = b.config()
-            assert kind == kind_want and tile in tiles, (kern, kind, tile)
+            halves = (tile // 10000, tile % 10000) if tile >= 10000 else (tile, tile)
+            assert kind == kind_want and all(t in tiles for t in halves), (kern, kind, tile)
             b.step(400)
             tb = b.traces()
             assert rel_l2(tb, ta) <= 1e-6, kern
