@@ -1,9 +1,9 @@
 // Batched scenarios: many wells advanced by one launch per kernel per step.
 // Every case is a regular simulator handle (same validation and set-up as
-// sim_create, buffers updated in place by the load-first split bodies); the batch
-// holds their kernel parameters and the prefix sum of their work items (host
-// arrays: they travel as kernel parameters, in launches of up to 64 cases), and
-// captures its steps in a CUDA graph.
+// sim_create, buffers updated in place by the load-first split bodies, in an
+// interior and an edge launch per half step); the batch holds their kernel
+// parameters (a host array: they travel as kernel parameters, in launches of up
+// to 64 cases), and captures its steps in a CUDA graph.
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -16,9 +16,8 @@ struct simb_s {
   bool own_stream = false;
   std::vector<sim_t *> cases;
   std::vector<KParams> kp;        // the cases' kernel parameters (host: they travel as kernel parameters)
-  std::vector<long long> start;   // prefix sum of work items, n + 1 entries
   RParams *d_rp = nullptr;
-  long long total = 0;
+  long long total = 0;  // bound on the items of one work list of all cases
   int grid = 0, graph_chunk = 64, steps_done = 0;
   cudaGraphExec_t gexec = nullptr;
   int gsteps = 0;
@@ -48,8 +47,8 @@ static void brelease(simb_t *b) {
 
 static cudaError_t batch_step(simb_t *b, const KParams *cases) {
   const int n = (int)b->cases.size();
-  cudaError_t e = launch_batch_split(b->storage, true, cases, b->start.data(), n, b->grid, b->stream);
-  if (e == cudaSuccess) e = launch_batch_split(b->storage, false, cases, b->start.data(), n, b->grid, b->stream);
+  cudaError_t e = launch_batch_split(b->storage, true, cases, n, b->grid, b->stream);
+  if (e == cudaSuccess) e = launch_batch_split(b->storage, false, cases, n, b->grid, b->stream);
   return e;
 }
 
@@ -132,7 +131,6 @@ extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *m
   o.graph_chunk = -1;
   o.timing = 0;
   size_t used = 0;
-  std::vector<long long> start(n + 1, 0);
   for (int c = 0; c < n; c++) {
     if (opts->mem_cap) o.mem_cap = opts->mem_cap > used ? opts->mem_cap - used : 1;
     sim_t *h = nullptr;
@@ -143,10 +141,8 @@ extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *m
     const long long items = split_items(grids[c].nth, grids[c].nr + grids[c].pml_r, grids[c].nz + 2 * grids[c].pml_z);
     if (items > 0x7fffffffLL)
       return bail(bfail(b, SIM_EINVAL, "case " + std::to_string(c) + ": more work items than a 32-bit index holds"));
-    start[c + 1] = start[c] + items;
+    b->total += items;
   }
-  b->total = start[n];
-  b->start = start;
   b->kp.resize(n);
   std::vector<RParams> rp(n);
   for (int c = 0; c < n; c++) {

@@ -191,13 +191,13 @@ cudaError_t launch_receivers(int storage, const RParams &p, cudaStream_t s);
 cudaError_t launch_inject(int storage, const IParams &p, cudaStream_t s);
 cudaError_t launch_fused(int storage, int rt, const FusedMaps &maps, const FusedParams &fp, cudaStream_t s);
 size_t fused_smem_bytes(int storage, int rt);
+// upper bound on the work items of one case in either batched work list
 long long split_items(int nth, int NR, int NZ);
-// batched load-first kernels: cases and start[] (prefix sum of work items,
-// n_cases + 1 entries) are host arrays; launched in chunks of BATCH_MAX cases
-// whose parameters travel in the kernel's parameter space
+// batched load-first kernels (interior and edge launches per half step): cases
+// is a host array, launched in chunks of BATCH_MAX cases whose parameters
+// travel in the kernel's parameter space; grid = persistent blocks per launch
 constexpr int BATCH_MAX = 64;
-cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, const long long *start, int n_cases,
-                               int grid, cudaStream_t s);
+cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, int n_cases, int grid, cudaStream_t s);
 cudaError_t launch_batch_receivers(int storage, const RParams *rp, int n_cases, cudaStream_t s);
 int fused_box_x(int storage);
 cudaError_t launch_fused4(int storage, int rt, const FusedMaps &maps, const FusedParams &fp, cudaStream_t s);
@@ -221,8 +221,11 @@ size_t march_smem_bytes(int storage, int code);
 // block order o (0: theta fastest, 1: z fastest; b = 3 or 4 only); 2100 + b =
 // the two-cells-per-thread variant, theta fastest (b = 6 or 8); 2200 + 10 c + b
 // = interior / edge split launches (a lean-only interior kernel for b blocks per
-// SM, the general kernel on the PML and end tiles), c = 0: four cells per
-// thread (b = 4 or 5), c = 1: two cells (b = 6 or 8).  A pair code
+// SM, the general kernel on the PML and end tiles): c = 1: two cells per thread
+// in both (b = 6 or 8; edge for 6 blocks per SM); otherwise four cells per
+// thread in the interior (b = 4 or 5) and an edge kernel with c = 0: four cells,
+// 4 blocks per SM; c = 2: two cells, 4 blocks; c = 3: two cells, 6 blocks;
+// c = 4: four cells, 3 blocks.  A pair code
 // v * 10000 + s runs the velocity kernel of split code v and the stress kernel
 // of split code s (the autotuner times the two apart).
 constexpr int SPLIT_CODE = 2000;

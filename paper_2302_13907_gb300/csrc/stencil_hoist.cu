@@ -72,6 +72,42 @@ struct Vec<__half, 2> {
   }
 };
 
+// PML memory variables: plain (not read-only path) vector loads and stores,
+// since the thread that reads a memory variable rewrites it
+template <int NV>
+__device__ __forceinline__ void ldv(float (&d)[NV], const float *p);
+template <>
+__device__ __forceinline__ void ldv<4>(float (&d)[4], const float *p) {
+  const float4 v = *reinterpret_cast<const float4 *>(p);
+  d[0] = v.x;
+  d[1] = v.y;
+  d[2] = v.z;
+  d[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void ldv<2>(float (&d)[2], const float *p) {
+  const float2 v = *reinterpret_cast<const float2 *>(p);
+  d[0] = v.x;
+  d[1] = v.y;
+}
+template <int NV>
+__device__ __forceinline__ void stv(float *p, const float (&v)[NV]);
+template <>
+__device__ __forceinline__ void stv<4>(float *p, const float (&v)[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void stv<2>(float *p, const float (&v)[2]) {
+  *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+
+// the memory-variable recursion of the stretched derivative on a register
+// copy: psi <- b psi + a D, result D + psi (same arithmetic as stretch())
+__device__ __forceinline__ float stretch_reg(float &psi, float a, float b, float D) {
+  psi = b * psi + a * D;
+  return D + psi;
+}
+
 template <int NV>
 __device__ __forceinline__ void zero(float (&d)[NV]) {
 #pragma unroll
@@ -100,7 +136,7 @@ __device__ __forceinline__ void zero_ids(int (&o)[NV]) {
 // NV cells per thread (4 or 2).  LEAN: the NV cells are interior (no PML
 // memory variable, all inside NZ, k0 + NV < NZ); the kernels pick the lean
 // body per thread, or run it alone on the interior tiles.
-template <typename T, int NV, bool LEAN>
+template <typename T, int NV, bool LEAN, bool PRE = false>
 __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, const int i, const int k0) {
   const int nth = p.nth, NR = p.NR, NZ = p.NZ;
   const long long NZp = p.NZp, pl = p.plane;
@@ -162,6 +198,34 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
   const bool rp = !LEAN && i >= p.nr;
   const float inv_ri = __ldg(p.inv_ri + i), inv_rh = __ldg(p.inv_rh + i);
   const float4 abr = __ldg(p.ab_r + i), abq = __ldg(p.ab_q + i);
+  // PML memory variables of the NV cells (radial: one vector per array;
+  // z: one value per cell inside the z PML), loaded before any arithmetic
+  const long long cr = rp ? ((long long)j * p.pml_r + (i - p.nr)) * NZp + k0 : 0;
+  const int pz = p.pml_z;
+  const long long czrow = ((long long)j * NR + i) * (2 * pz);
+  const bool zl = !LEAN && pz > 0 && (k0 < pz || k0 + NV - 1 >= NZ - pz);
+  float ur_vr[NV], uq_vr[NV], ur_vp[NV], uq_vp[NV], ur_vz[NV], uq_vz[NV];
+  if (PRE && rp) {
+    ldv(ur_vr, p.psr[R_VR] + cr);
+    ldv(uq_vr, p.psr[Q_VR] + cr);
+    ldv(ur_vp, p.psr[R_VP] + cr);
+    ldv(uq_vp, p.psr[Q_VP] + cr);
+    ldv(ur_vz, p.psr[R_VZ] + cr);
+    ldv(uq_vz, p.psr[Q_VZ] + cr);
+  }
+  float uz_vr[NV], uz_vp[NV], uz_vz[NV];
+  if (PRE && zl) {
+#pragma unroll
+    for (int e = 0; e < NV; e++) {
+      const int k = k0 + e;
+      if (k < NZ && (k < pz || k >= NZ - pz)) {
+        const long long q = czrow + (k < pz ? k : k - (NZ - 2 * pz));
+        uz_vr[e] = p.psz[Z_VR][q];
+        uz_vp[e] = p.psz[Z_VP][q];
+        uz_vz[e] = p.psz[Z_VZ][q];
+      }
+    }
+  }
 
   if (!k4) id_k4 = idc[NV - 1];
   float rho_c[NV + 1], rho_j[NV], rho_m[NV];
@@ -173,11 +237,7 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
   }
   rho_c[NV] = __ldg(p.m_rho + id_k4);
 
-  const long long cr = rp ? ((long long)j * p.pml_r + (i - p.nr)) * NZp + k0 : 0;
   const float dtv = p.dtv, idr = p.inv_dr, idz = p.inv_dz, idth = p.inv_dth;
-  const int pz = p.pml_z;
-  const long long czrow = ((long long)j * NR + i) * (2 * pz);
-  const bool zl = !LEAN && pz > 0 && (k0 < pz || k0 + NV - 1 >= NZ - pz);
 
   float out_r[NV], out_p[NV], out_z[NV];
 #pragma unroll
@@ -203,10 +263,10 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
                 inv_ri;
       float Dz = (srz_e - srz_m1) * idz;
       if (rp) {
-        Dr = stretch(p.psr[R_VR] + cr + e, abr.x, abr.y, Dr);
-        Q = stretch(p.psr[Q_VR] + cr + e, abq.x, abq.y, Q);
+        Dr = (PRE ? stretch_reg(ur_vr[e], abr.x, abr.y, Dr) : stretch(p.psr[R_VR] + cr + e, abr.x, abr.y, Dr));
+        Q = (PRE ? stretch_reg(uq_vr[e], abq.x, abq.y, Q) : stretch(p.psr[Q_VR] + cr + e, abq.x, abq.y, Q));
       }
-      if (zp) Dz = stretch(p.psz[Z_VR] + czrow + kz, abz.x, abz.y, Dz);
+      if (zp) Dz = (PRE ? stretch_reg(uz_vr[e], abz.x, abz.y, Dz) : stretch(p.psz[Z_VR] + czrow + kz, abz.x, abz.y, Dz));
       out_r[e] += vel_coef(dtv, rho_m[e] + rho_c[e]) * (Dr + Q + Dz);
     }
     // v_phi at (r_{i+1/2}, theta_{j+1/2}, z_k)
@@ -216,10 +276,10 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
       float Q = ((s1 + srp_e) + (jp_spp[e] - spp_e) * idth) * inv_rh;
       float Dz = (spz_e - spz_m1) * idz;
       if (rp) {
-        Dr = stretch(p.psr[R_VP] + cr + e, abr.z, abr.w, Dr);
-        Q = stretch(p.psr[Q_VP] + cr + e, abq.z, abq.w, Q);
+        Dr = (PRE ? stretch_reg(ur_vp[e], abr.z, abr.w, Dr) : stretch(p.psr[R_VP] + cr + e, abr.z, abr.w, Dr));
+        Q = (PRE ? stretch_reg(uq_vp[e], abq.z, abq.w, Q) : stretch(p.psr[Q_VP] + cr + e, abq.z, abq.w, Q));
       }
-      if (zp) Dz = stretch(p.psz[Z_VP] + czrow + kz, abz.x, abz.y, Dz);
+      if (zp) Dz = (PRE ? stretch_reg(uz_vp[e], abz.x, abz.y, Dz) : stretch(p.psz[Z_VP] + czrow + kz, abz.x, abz.y, Dz));
       out_p[e] += vel_coef(dtv, rho_c[e] + rho_j[e]) * (Dr + Q + Dz);
     }
     // v_z at (r_{i+1/2}, theta_j, z_{k+1/2}), k + 1 < NZ
@@ -229,19 +289,39 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
       float Q = (0.5f * (s1 + srz_e) + (spz_e - jm_spz[e]) * idth) * inv_rh;
       float Dz = ((e < NV - 1 ? a_szz[e + 1] : szz_k4) - szz_e) * idz;
       if (rp) {
-        Dr = stretch(p.psr[R_VZ] + cr + e, abr.z, abr.w, Dr);
-        Q = stretch(p.psr[Q_VZ] + cr + e, abq.z, abq.w, Q);
+        Dr = (PRE ? stretch_reg(ur_vz[e], abr.z, abr.w, Dr) : stretch(p.psr[R_VZ] + cr + e, abr.z, abr.w, Dr));
+        Q = (PRE ? stretch_reg(uq_vz[e], abq.z, abq.w, Q) : stretch(p.psr[Q_VZ] + cr + e, abq.z, abq.w, Q));
       }
-      if (zp) Dz = stretch(p.psz[Z_VZ] + czrow + kz, abz.z, abz.w, Dz);
+      if (zp) Dz = (PRE ? stretch_reg(uz_vz[e], abz.z, abz.w, Dz) : stretch(p.psz[Z_VZ] + czrow + kz, abz.z, abz.w, Dz));
       out_z[e] += vel_coef(dtv, rho_c[e] + rho_c[e + 1]) * (Dr + Q + Dz);
     }
   }
   if (im) Vec<T, NV>::st(vr + c, out_r);
   Vec<T, NV>::st(vp + c, out_p);
   Vec<T, NV>::st(vz + c, out_z);
+  if (PRE && rp) {  // cells the loop skipped keep the values loaded
+    stv(p.psr[R_VR] + cr, ur_vr);
+    stv(p.psr[Q_VR] + cr, uq_vr);
+    stv(p.psr[R_VP] + cr, ur_vp);
+    stv(p.psr[Q_VP] + cr, uq_vp);
+    stv(p.psr[R_VZ] + cr, ur_vz);
+    stv(p.psr[Q_VZ] + cr, uq_vz);
+  }
+  if (PRE && zl) {
+#pragma unroll
+    for (int e = 0; e < NV; e++) {
+      const int k = k0 + e;
+      if (k < NZ && (k < pz || k >= NZ - pz)) {
+        const long long q = czrow + (k < pz ? k : k - (NZ - 2 * pz));
+        p.psz[Z_VR][q] = uz_vr[e];
+        p.psz[Z_VP][q] = uz_vp[e];
+        p.psz[Z_VZ][q] = uz_vz[e];
+      }
+    }
+  }
 }
 
-template <typename T, int NV, bool LEAN>
+template <typename T, int NV, bool LEAN, bool PRE = false>
 __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, const int i, const int k0) {
   const int nth = p.nth, NR = p.NR, NZ = p.NZ;
   const long long NZp = p.NZp, pl = p.plane;
@@ -309,6 +389,33 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
   const bool rp = !LEAN && i >= p.nr;
   const float inv_ri = __ldg(p.inv_ri + i), inv_rh = __ldg(p.inv_rh + i);
   const float4 abr = __ldg(p.ab_r + i), abq = __ldg(p.ab_q + i);
+  // PML memory variables of the NV cells, loaded before any arithmetic
+  const long long cr = rp ? ((long long)j * p.pml_r + (i - p.nr)) * NZp + k0 : 0;
+  const int pz = p.pml_z;
+  const long long czrow = ((long long)j * NR + i) * (2 * pz);
+  const bool zl = !LEAN && pz > 0 && (k0 < pz || k0 + NV - 1 >= NZ - pz);
+  float ur_rr[NV], uq_pp[NV], ur_rp[NV], uq_rp[NV], ur_rz[NV], uq_pz[NV];
+  if (PRE && rp) {
+    ldv(ur_rr, p.psr[R_ERR] + cr);
+    ldv(uq_pp, p.psr[Q_EPP] + cr);
+    ldv(ur_rp, p.psr[R_GRP] + cr);
+    ldv(uq_rp, p.psr[Q_GRP] + cr);
+    ldv(ur_rz, p.psr[R_GRZ] + cr);
+    ldv(uq_pz, p.psr[Q_GPZ] + cr);
+  }
+  float uz_zz[NV], uz_rz[NV], uz_pz[NV];
+  if (PRE && zl) {
+#pragma unroll
+    for (int e = 0; e < NV; e++) {
+      const int k = k0 + e;
+      if (k < NZ && (k < pz || k >= NZ - pz)) {
+        const long long q = czrow + (k < pz ? k : k - (NZ - 2 * pz));
+        uz_zz[e] = p.psz[Z_EZZ][q];
+        uz_rz[e] = p.psz[Z_GRZ][q];
+        uz_pz[e] = p.psz[Z_GPZ][q];
+      }
+    }
+  }
   float src[NV] = {};
   if (i == p.src_i && (p.src_j < 0 || p.src_j == j) && p.src_k >= k0 && p.src_k < k0 + NV) {
     const int n = *p.step;
@@ -334,11 +441,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
   imu_j[NV] = __ldg(p.m_imu + idj4);
   imu_m[NV] = __ldg(p.m_imu + idm4);
 
-  const long long cr = rp ? ((long long)j * p.pml_r + (i - p.nr)) * NZp + k0 : 0;
   const float dts = p.dts, idr = p.inv_dr, idz = p.inv_dz, idth = p.inv_dth;
-  const int pz = p.pml_z;
-  const long long czrow = ((long long)j * NR + i) * (2 * pz);
-  const bool zl = !LEAN && pz > 0 && (k0 < pz || k0 + NV - 1 >= NZ - pz);
 
   float orr[NV], opp[NV], ozz[NV], orp[NV], opz[NV], orz[NV];
 #pragma unroll
@@ -367,10 +470,10 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
       float epp = ((vp_e - jm_vp[e]) * idth + 0.5f * (vr_e + vr1)) * inv_rh;
       float ezz = (vz_e - vz_m1) * idz;
       if (rp) {
-        err = stretch(p.psr[R_ERR] + cr + e, abr.z, abr.w, err);
-        epp = stretch(p.psr[Q_EPP] + cr + e, abq.z, abq.w, epp);
+        err = (PRE ? stretch_reg(ur_rr[e], abr.z, abr.w, err) : stretch(p.psr[R_ERR] + cr + e, abr.z, abr.w, err));
+        epp = (PRE ? stretch_reg(uq_pp[e], abq.z, abq.w, epp) : stretch(p.psr[Q_EPP] + cr + e, abq.z, abq.w, epp));
       }
-      if (zp) ezz = stretch(p.psz[Z_EZZ] + czrow + kz, abz.x, abz.y, ezz);
+      if (zp) ezz = (PRE ? stretch_reg(uz_zz[e], abz.x, abz.y, ezz) : stretch(p.psz[Z_EZZ] + czrow + kz, abz.x, abz.y, ezz));
       const float l = lam[e].x, l2m = lam[e].y;
       orr[e] += dts * (l2m * err + l * (epp + ezz)) + src[e];
       opp[e] += dts * (l2m * epp + l * (err + ezz)) + src[e];
@@ -382,8 +485,8 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
         float gr = (vp_e - m_vp[e]) * idr;
         float Q = ((jp_vr[e] - vr_e) * idth - 0.5f * (vp_e + m_vp[e])) * inv_ri;
         if (rp) {
-          gr = stretch(p.psr[R_GRP] + cr + e, abr.x, abr.y, gr);
-          Q = stretch(p.psr[Q_GRP] + cr + e, abq.x, abq.y, Q);
+          gr = (PRE ? stretch_reg(ur_rp[e], abr.x, abr.y, gr) : stretch(p.psr[R_GRP] + cr + e, abr.x, abr.y, gr));
+          Q = (PRE ? stretch_reg(uq_rp[e], abq.x, abq.y, Q) : stretch(p.psr[Q_GRP] + cr + e, abq.x, abq.y, Q));
         }
         const float mu = mu_harm(imu_m[e] + imu_c[e] + imu_jm[e] + imu_j[e]);
         orp[e] += dts * mu * (gr + Q);
@@ -392,8 +495,8 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
       if (LEAN || k + 1 < NZ) {
         float gz = (vr_e1 - vr_e) * idz;
         float gr = (vz_e - m_vz[e]) * idr;
-        if (zp) gz = stretch(p.psz[Z_GRZ] + czrow + kz, abz.z, abz.w, gz);
-        if (rp) gr = stretch(p.psr[R_GRZ] + cr + e, abr.x, abr.y, gr);
+        if (zp) gz = (PRE ? stretch_reg(uz_rz[e], abz.z, abz.w, gz) : stretch(p.psz[Z_GRZ] + czrow + kz, abz.z, abz.w, gz));
+        if (rp) gr = (PRE ? stretch_reg(ur_rz[e], abr.x, abr.y, gr) : stretch(p.psr[R_GRZ] + cr + e, abr.x, abr.y, gr));
         const float mu = mu_harm(imu_m[e] + imu_c[e] + imu_m[e + 1] + imu_c[e + 1]);
         orz[e] += dts * mu * (gz + gr);
       }
@@ -402,8 +505,8 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
     if (LEAN || k + 1 < NZ) {
       float Q = (jp_vz[e] - vz_e) * idth * inv_rh;
       float gz = (vp_e1 - vp_e) * idz;
-      if (rp) Q = stretch(p.psr[Q_GPZ] + cr + e, abq.z, abq.w, Q);
-      if (zp) gz = stretch(p.psz[Z_GPZ] + czrow + kz, abz.z, abz.w, gz);
+      if (rp) Q = (PRE ? stretch_reg(uq_pz[e], abq.z, abq.w, Q) : stretch(p.psr[Q_GPZ] + cr + e, abq.z, abq.w, Q));
+      if (zp) gz = (PRE ? stretch_reg(uz_pz[e], abz.z, abz.w, gz) : stretch(p.psz[Z_GPZ] + czrow + kz, abz.z, abz.w, gz));
       const float mu = mu_harm(imu_c[e] + imu_j[e] + imu_c[e + 1] + imu_j[e + 1]);
       opz[e] += dts * mu * (Q + gz);
     }
@@ -416,6 +519,26 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
     Vec<T, NV>::st(srz + c, orz);
   }
   Vec<T, NV>::st(spz + c, opz);
+  if (PRE && rp) {  // cells the loop skipped keep the values loaded
+    stv(p.psr[R_ERR] + cr, ur_rr);
+    stv(p.psr[Q_EPP] + cr, uq_pp);
+    stv(p.psr[R_GRP] + cr, ur_rp);
+    stv(p.psr[Q_GRP] + cr, uq_rp);
+    stv(p.psr[R_GRZ] + cr, ur_rz);
+    stv(p.psr[Q_GPZ] + cr, uq_pz);
+  }
+  if (PRE && zl) {
+#pragma unroll
+    for (int e = 0; e < NV; e++) {
+      const int k = k0 + e;
+      if (k < NZ && (k < pz || k >= NZ - pz)) {
+        const long long q = czrow + (k < pz ? k : k - (NZ - 2 * pz));
+        p.psz[Z_EZZ][q] = uz_zz[e];
+        p.psz[Z_GRZ][q] = uz_rz[e];
+        p.psz[Z_GPZ][q] = uz_pz[e];
+      }
+    }
+  }
 }
 
 template <int NV>
@@ -423,14 +546,17 @@ __device__ __forceinline__ bool lean_cells(const KParams &p, int i, int k0) {
   return i < p.nr && k0 >= p.pml_z && k0 + NV < p.NZ - p.pml_z;
 }
 
-template <typename T, int NV, bool VEL>
+// PRE: the general body loads the PML memory variables of its cells with the
+// fields and updates them in registers (for kernels with the registers to
+// spare); otherwise it reads and rewrites each one where it is used
+template <typename T, int NV, bool VEL, bool PRE = false>
 __device__ __forceinline__ void hoist_cells(const KParams &p, int j, int i, int k0) {
   if (lean_cells<NV>(p, i, k0)) {
     if (VEL) vel_hoist_body<T, NV, true>(p, j, i, k0);
     else str_hoist_body<T, NV, true>(p, j, i, k0);
   } else {
-    if (VEL) vel_hoist_body<T, NV, false>(p, j, i, k0);
-    else str_hoist_body<T, NV, false>(p, j, i, k0);
+    if (VEL) vel_hoist_body<T, NV, false, PRE>(p, j, i, k0);
+    else str_hoist_body<T, NV, false, PRE>(p, j, i, k0);
   }
 }
 
@@ -466,20 +592,25 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) str_hoist(const KParams p) {
 // blocks fit on an SM; the remaining tiles (radial-PML rows, the z ends) run
 // the per-thread lean / general dispatch.  Both walk theta fastest.
 struct Split2 {
-  int nrt_in;        // r tiles whose rows are all outside the radial PML
-  int zt_lo, zt_hi;  // interior z tiles: zt_lo <= zt < zt_hi
-  int nrt, nzt;      // all r and z tiles
+  int nrt_in;              // r tiles whose rows are all outside the radial PML
+  int zt_lo, zt_hi;        // interior z tiles: zt_lo <= zt < zt_hi (interior kernel's tiles)
+  int nrt;                 // all r tiles
+  int ez_lo, ez_hi, enzt;  // the same z bounds in the edge kernel's tiles; all edge z tiles
 };
 
-template <int NV>
+// NV: cells per thread of the interior kernel, NVE: of the edge kernel
+template <int NV, int NVE>
 Split2 split2(const KParams &p) {
-  const int W = NV * HB_X;
+  static_assert(NV % NVE == 0, "an interior tile spans whole edge tiles");
+  const int W = NV * HB_X, WE = NVE * HB_X;
   Split2 q;
   q.nrt = (p.NR + HB_Y - 1) / HB_Y;
-  q.nzt = (p.NZ + W - 1) / W;
   q.nrt_in = p.nr / HB_Y;
   q.zt_lo = (p.pml_z + W - 1) / W;
   q.zt_hi = std::max(q.zt_lo, (p.NZ - p.pml_z - 1) / W);  // (zt + 1) W <= NZ - pml_z - 1
+  q.ez_lo = q.zt_lo * (W / WE);
+  q.ez_hi = q.zt_hi * (W / WE);
+  q.enzt = (p.NZ + WE - 1) / WE;
   return q;
 }
 
@@ -491,86 +622,164 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_interior(const KParams
   else str_hoist_body<T, NV, true>(p, j, i, k0);
 }
 
-// edge tile t: first the r tiles nrt_in .. nrt-1 with every z tile, then the
-// interior r tiles with the z tiles below zt_lo and from zt_hi on
-template <typename T, int NV, int MINB, bool VEL>
-__global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_edge(const KParams p, Split2 q) {
-  const int j = blockIdx.x;
-  int t = blockIdx.y, rt, zt;
-  const int a = (q.nrt - q.nrt_in) * q.nzt;
+// edge tile t (in edge-kernel tiles of NV * HB_X cells along z): first the r
+// tiles nrt_in .. nrt-1 with every z tile, then the interior r tiles with the
+// z tiles below ez_lo and from ez_hi on
+__device__ __forceinline__ void edge_tile(const Split2 &q, int t, int &rt, int &zt) {
+  const int a = (q.nrt - q.nrt_in) * q.enzt;
   if (t < a) {
-    rt = q.nrt_in + t / q.nzt;
-    zt = t % q.nzt;
+    rt = q.nrt_in + t / q.enzt;
+    zt = t % q.enzt;
   } else {
     t -= a;
-    const int nlo = q.zt_lo, nz_edge = q.zt_lo + (q.nzt - q.zt_hi);
+    const int nz_edge = q.ez_lo + (q.enzt - q.ez_hi);
     rt = t / nz_edge;
     const int e = t % nz_edge;
-    zt = e < nlo ? e : q.zt_hi + (e - nlo);
+    zt = e < q.ez_lo ? e : q.ez_hi + (e - q.ez_lo);
   }
-  const int i = rt * HB_Y + threadIdx.y, k0 = (zt * HB_X + threadIdx.x) * NV;
-  if (i < p.NR && k0 < p.NZ) hoist_cells<T, NV, VEL>(p, j, i, k0);
 }
 
-// Batched scenarios: the blocks walk the work list of up to BATCH_MAX cases,
-// item = (case, theta, r tile, z tile), theta fastest inside a case so that
-// the theta neighbours a block reads are read by co-resident blocks too.  The
-// cases' parameters and the prefix sum of their items (start[c] = first item
-// of case c, start[n] = total) travel in the kernel's parameter space, so a
-// block reads its case's geometry and buffers from the constant bank.  The
-// index inside a case is 32-bit (checked on the host).
+inline long long edge_tiles(const Split2 &q) {
+  return (long long)(q.nrt - q.nrt_in) * q.enzt + (long long)q.nrt_in * (q.ez_lo + q.enzt - q.ez_hi);
+}
+
+template <typename T, int NV, int MINB, bool VEL>
+__global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_edge(const KParams p, Split2 q) {
+  int rt, zt;
+  edge_tile(q, blockIdx.y, rt, zt);
+  const int j = blockIdx.x, i = rt * HB_Y + threadIdx.y, k0 = (zt * HB_X + threadIdx.x) * NV;
+  if (i < p.NR && k0 < p.NZ) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
+}
+
+// Batched scenarios: each half step is two persistent launches over the work
+// lists of up to BATCH_MAX cases, one over every case's interior tiles (lean
+// body only) and one over their edge tiles (radial-PML rows and z ends,
+// general body); item = (case, theta, tile), theta fastest inside a case so
+// that the theta neighbours a block reads are read by co-resident blocks too.
+// The cases' parameters, their tile bounds and the prefix sum of the
+// launch's items (start[c] = first item of case c, start[n] = total) travel in
+// the kernel's parameter space, so a block reads its case's geometry and
+// buffers from the constant bank.  The index inside a case is 32-bit (checked
+// on the host).  Cells per thread and blocks per SM: the velocity half takes
+// interior (4, 5) and edge (4, 3), the stress half interior (4, 4) and edge
+// (2, 4), the split launches the tuner picks for the single well.
 struct BatchParams {
   KParams cases[BATCH_MAX];
+  Split2 q[BATCH_MAX];
   long long start[BATCH_MAX + 1];
   int n;
 };
 static_assert(sizeof(BatchParams) <= 32000, "batch parameters exceed the kernel parameter space");
 
-template <typename T, bool VEL, int MINB>
-__global__ void __launch_bounds__(HB_X *HB_Y, MINB) batch_hoist(const __grid_constant__ BatchParams bp) {
+constexpr int BATCH_NV = 4;
+template <bool VEL>
+struct BatchCfg;
+template <>
+struct BatchCfg<true> {
+  static constexpr int MINB_IN = 5, NVE = 4, MINB_E = 3;
+};
+template <>
+struct BatchCfg<false> {
+  static constexpr int MINB_IN = 4, NVE = 2, MINB_E = 4;
+};
+
+__device__ __forceinline__ int batch_case(const BatchParams &bp, long long item) {
+  int lo = 0, hi = bp.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bp.start[mid] <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, bool VEL>
+__global__ void __launch_bounds__(HB_X *HB_Y, BatchCfg<VEL>::MINB_IN)
+    batch_interior(const __grid_constant__ BatchParams bp) {
   const long long total = bp.start[bp.n];
   for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-    int lo = 0, hi = bp.n - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (bp.start[mid] <= item) lo = mid;
-      else hi = mid - 1;
-    }
-    const KParams &p = bp.cases[lo];
-    int q = (int)(item - bp.start[lo]);
-    const int nth = p.nth, nrt = (p.NR + HB_Y - 1) / HB_Y;
-    const int j = q % nth;
-    q /= nth;
-    const int i = (q % nrt) * HB_Y + threadIdx.y, k0 = ((q / nrt) * HB_X + threadIdx.x) * 4;
-    if (i < p.NR && k0 < p.NZ) hoist_cells<T, 4, VEL>(p, j, i, k0);
+    const int c = batch_case(bp, item);
+    const KParams &p = bp.cases[c];
+    const Split2 &q = bp.q[c];
+    int t = (int)(item - bp.start[c]);
+    const int j = t % p.nth;
+    t /= p.nth;
+    const int i = (t % q.nrt_in) * HB_Y + threadIdx.y;
+    const int k0 = ((q.zt_lo + t / q.nrt_in) * HB_X + threadIdx.x) * BATCH_NV;
+    if (VEL) vel_hoist_body<T, BATCH_NV, true>(p, j, i, k0);
+    else str_hoist_body<T, BATCH_NV, true>(p, j, i, k0);
   }
 }
 
-template <typename T, int NV, int MINB_IN, int MINB_EDGE, bool VEL>
+template <typename T, bool VEL>
+__global__ void __launch_bounds__(HB_X *HB_Y, BatchCfg<VEL>::MINB_E) batch_edge(const __grid_constant__ BatchParams bp) {
+  constexpr int NVE = BatchCfg<VEL>::NVE;
+  const long long total = bp.start[bp.n];
+  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    const int c = batch_case(bp, item);
+    const KParams &p = bp.cases[c];
+    int t = (int)(item - bp.start[c]), rt, zt;
+    const int j = t % p.nth;
+    edge_tile(bp.q[c], t / p.nth, rt, zt);
+    const int i = rt * HB_Y + threadIdx.y, k0 = (zt * HB_X + threadIdx.x) * NVE;
+    if (i < p.NR && k0 < p.NZ) hoist_cells<T, NVE, VEL, true>(p, j, i, k0);
+  }
+}
+
+template <typename T, bool VEL>
+cudaError_t launch_batch_t(const KParams *cases, int n_cases, int grid, cudaStream_t s) {
+  using C = BatchCfg<VEL>;
+  dim3 blk(HB_X, HB_Y);
+  static thread_local BatchParams bp;  // large: kept off the stack
+  for (int c0 = 0; c0 < n_cases; c0 += BATCH_MAX) {
+    const int n = std::min(BATCH_MAX, n_cases - c0);
+    bp.n = n;
+    for (int c = 0; c < n; c++) {
+      bp.cases[c] = cases[c0 + c];
+      bp.q[c] = split2<BATCH_NV, C::NVE>(cases[c0 + c]);
+    }
+    // interior tiles
+    bp.start[0] = 0;
+    for (int c = 0; c < n; c++) {
+      const Split2 &q = bp.q[c];
+      bp.start[c + 1] = bp.start[c] + (long long)bp.cases[c].nth * q.nrt_in * (q.zt_hi - q.zt_lo);
+    }
+    if (bp.start[n] > 0)
+      batch_interior<T, VEL><<<(int)std::min<long long>(grid, bp.start[n]), blk, 0, s>>>(bp);
+    // edge tiles
+    for (int c = 0; c < n; c++) bp.start[c + 1] = bp.start[c] + (long long)bp.cases[c].nth * edge_tiles(bp.q[c]);
+    if (bp.start[n] > 0) batch_edge<T, VEL><<<(int)std::min<long long>(grid, bp.start[n]), blk, 0, s>>>(bp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T, int NV, int MINB_IN, int NVE, int MINB_E, bool VEL>
 cudaError_t launch_split2_half(const KParams &p, const Split2 &q, cudaStream_t s) {
   dim3 blk(HB_X, HB_Y);
   const int nin = q.zt_hi - q.zt_lo;
   if (q.nrt_in > 0 && nin > 0)
     hoist_interior<T, NV, MINB_IN, VEL><<<dim3(p.nth, q.nrt_in, nin), blk, 0, s>>>(p, q.zt_lo);
-  const long long nedge = (long long)(q.nrt - q.nrt_in) * q.nzt + (long long)q.nrt_in * (q.zt_lo + q.nzt - q.zt_hi);
+  const long long nedge = (long long)(q.nrt - q.nrt_in) * q.enzt + (long long)q.nrt_in * (q.ez_lo + q.enzt - q.ez_hi);
   if (nedge > 65535 || p.nth > 65535) return cudaErrorInvalidValue;
-  if (nedge > 0) hoist_edge<T, NV, MINB_EDGE, VEL><<<dim3(p.nth, (unsigned)nedge), blk, 0, s>>>(p, q);
+  if (nedge > 0) hoist_edge<T, NVE, MINB_E, VEL><<<dim3(p.nth, (unsigned)nedge), blk, 0, s>>>(p, q);
   return cudaGetLastError();
 }
 
-template <typename T, int NV, int MINB_IN, int MINB_EDGE>
+template <typename T, int NV, int MINB_IN, int NVE, int MINB_E>
 cudaError_t launch_split2_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
-  const Split2 q = split2<NV>(p);
+  const Split2 q = split2<NV, NVE>(p);
   if (q.zt_hi - q.zt_lo > 65535) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   if (parts & 1) {
     if (ev) cudaEventRecord(ev[0], s);
-    e = launch_split2_half<T, NV, MINB_IN, MINB_EDGE, true>(p, q, s);
+    e = launch_split2_half<T, NV, MINB_IN, NVE, MINB_E, true>(p, q, s);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
   }
   if (parts & 2) {
-    e = launch_split2_half<T, NV, MINB_IN, MINB_EDGE, false>(p, q, s);
+    e = launch_split2_half<T, NV, MINB_IN, NVE, MINB_E, false>(p, q, s);
     if (ev) cudaEventRecord(ev[2], s);
   }
   return e;
@@ -595,14 +804,20 @@ cudaError_t launch_hoist_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev, in
 }
 
 template <typename T>
-cudaError_t launch_hoist_st(int nv, int minb, bool zf, bool split, const KParams &p, cudaStream_t s, cudaEvent_t *ev,
-                            int parts) {
-  if (split) {  // interior kernel compiled for minb blocks per SM, edge kernel for the general body's budget
-    switch (nv * 10 + minb) {
-      case 44: return launch_split2_t<T, 4, 4, 4>(p, s, ev, parts);
-      case 45: return launch_split2_t<T, 4, 5, 4>(p, s, ev, parts);
-      case 26: return launch_split2_t<T, 2, 6, 6>(p, s, ev, parts);
-      case 28: return launch_split2_t<T, 2, 8, 6>(p, s, ev, parts);
+cudaError_t launch_hoist_st(int nv, int minb, bool zf, bool split, int edge, const KParams &p, cudaStream_t s,
+                            cudaEvent_t *ev, int parts) {
+  if (split) {  // interior kernel for minb blocks per SM; edge kernel config c (cells per thread, blocks per SM)
+    switch (edge * 10 + minb) {
+      case 4: return launch_split2_t<T, 4, 4, 4, 4>(p, s, ev, parts);
+      case 5: return launch_split2_t<T, 4, 5, 4, 4>(p, s, ev, parts);
+      case 16: return launch_split2_t<T, 2, 6, 2, 6>(p, s, ev, parts);
+      case 18: return launch_split2_t<T, 2, 8, 2, 6>(p, s, ev, parts);
+      case 24: return launch_split2_t<T, 4, 4, 2, 4>(p, s, ev, parts);
+      case 25: return launch_split2_t<T, 4, 5, 2, 4>(p, s, ev, parts);
+      case 34: return launch_split2_t<T, 4, 4, 2, 6>(p, s, ev, parts);
+      case 35: return launch_split2_t<T, 4, 5, 2, 6>(p, s, ev, parts);
+      case 44: return launch_split2_t<T, 4, 4, 4, 3>(p, s, ev, parts);
+      case 45: return launch_split2_t<T, 4, 5, 4, 3>(p, s, ev, parts);
     }
     return cudaErrorInvalidValue;
   }
@@ -625,49 +840,31 @@ cudaError_t launch_hoist_st(int nv, int minb, bool zf, bool split, const KParams
 
 }  // namespace
 
-long long split_items(int nth, int NR, int NZ) {
-  return (long long)nth * ((NR + HB_Y - 1) / HB_Y) * ((NZ + 4 * HB_X - 1) / (4 * HB_X));
+long long split_items(int nth, int NR, int NZ) {  // bound on the items of either list: two-cell tiles
+  return (long long)nth * ((NR + HB_Y - 1) / HB_Y) * ((NZ + 2 * HB_X - 1) / (2 * HB_X));
 }
 
-constexpr int BATCH_MINB = 4;  // the load-first bodies at four resident blocks per SM
-
-cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, const long long *start, int n_cases,
-                               int grid, cudaStream_t s) {
-  dim3 blk(HB_X, HB_Y);
+cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, int n_cases, int grid, cudaStream_t s) {
   if (grid < 1 || n_cases < 1) return cudaErrorInvalidValue;
-  static thread_local BatchParams bp;  // large: kept off the stack
-  for (int c0 = 0; c0 < n_cases; c0 += BATCH_MAX) {
-    const int n = std::min(BATCH_MAX, n_cases - c0);
-    bp.n = n;
-    for (int c = 0; c < n; c++) {
-      bp.cases[c] = cases[c0 + c];
-      bp.start[c] = start[c0 + c] - start[c0];
-    }
-    bp.start[n] = start[c0 + n] - start[c0];
-    if (bp.start[n] < 1) continue;
-    const int g = (int)std::min<long long>(grid, bp.start[n]);
-    switch (storage * 2 + (vel ? 1 : 0)) {
-      case 0: batch_hoist<float, false, BATCH_MINB><<<g, blk, 0, s>>>(bp); break;
-      case 1: batch_hoist<float, true, BATCH_MINB><<<g, blk, 0, s>>>(bp); break;
-      case 2: batch_hoist<__nv_bfloat16, false, BATCH_MINB><<<g, blk, 0, s>>>(bp); break;
-      case 3: batch_hoist<__nv_bfloat16, true, BATCH_MINB><<<g, blk, 0, s>>>(bp); break;
-      case 4: batch_hoist<__half, false, BATCH_MINB><<<g, blk, 0, s>>>(bp); break;
-      case 5: batch_hoist<__half, true, BATCH_MINB><<<g, blk, 0, s>>>(bp); break;
-      default: return cudaErrorInvalidValue;
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+  switch (storage * 2 + (vel ? 1 : 0)) {
+    case 0: return launch_batch_t<float, false>(cases, n_cases, grid, s);
+    case 1: return launch_batch_t<float, true>(cases, n_cases, grid, s);
+    case 2: return launch_batch_t<__nv_bfloat16, false>(cases, n_cases, grid, s);
+    case 3: return launch_batch_t<__nv_bfloat16, true>(cases, n_cases, grid, s);
+    case 4: return launch_batch_t<__half, false>(cases, n_cases, grid, s);
+    case 5: return launch_batch_t<__half, true>(cases, n_cases, grid, s);
   }
-  return cudaSuccess;
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
   const int minb = hoist_blocks(code), nv = hoist_cells_per_thread(code);
   const bool zf = hoist_zfast(code), split = hoist_split(code);
+  const int edge = (code / 10) % 10;
   switch (storage) {
-    case 0: return launch_hoist_st<float>(nv, minb, zf, split, p, s, ev, parts);
-    case 1: return launch_hoist_st<__nv_bfloat16>(nv, minb, zf, split, p, s, ev, parts);
-    case 2: return launch_hoist_st<__half>(nv, minb, zf, split, p, s, ev, parts);
+    case 0: return launch_hoist_st<float>(nv, minb, zf, split, edge, p, s, ev, parts);
+    case 1: return launch_hoist_st<__nv_bfloat16>(nv, minb, zf, split, edge, p, s, ev, parts);
+    case 2: return launch_hoist_st<__half>(nv, minb, zf, split, edge, p, s, ev, parts);
   }
   return cudaErrorInvalidValue;
 }
