@@ -2,9 +2,10 @@
 
 Only the test-suite, the smoke check and the CPU-baseline leg of the benchmark
 use this package; the CUDA simulator never imports, links or runs it.  The
-numerical work lives in `cwell_oracle.c` (plain loops, FP64); this module
-compiles it with gcc and exposes it through ctypes, plus the few closed forms
-the tests pin it with.
+numerical work lives in `cwell_oracle.c` (plain loops, FP64) and, for the
+azimuthally refined grid, `cwell_refine.c`; this module compiles them with gcc
+and exposes them through ctypes, plus the few closed forms the tests pin them
+with.
 
 Field order (Sec. 2 of the paper): v_r, v_phi, v_z, s_rr, s_phiphi, s_zz,
 s_rphi, s_phiz, s_rz; each is a float64 array [theta][r][z], z fastest.
@@ -19,7 +20,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "cwell_oracle.c")
+_SRCS = [os.path.join(_HERE, "cwell_oracle.c"), os.path.join(_HERE, "cwell_refine.c")]
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -32,9 +33,9 @@ PSI = ("vr_r", "vp_r", "vz_r", "vr_z", "vp_z", "vz_z", "err_r", "grp_r", "grz_r"
 def build(force: bool = False) -> str:
     """Compile the oracle (gcc, FP64, OpenMP, no FMA contraction)."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _OUT + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _OUT)
     return _OUT
@@ -77,6 +78,28 @@ def lib():
             L.or_stress_update.argtypes = [p]
             L.or_inject_source.argtypes = [p, i]
             L.or_sample.argtypes = [p, i]
+            ip = ctypes.POINTER(i)
+            L.or_ref_create.restype = p
+            L.or_ref_create.argtypes = [i, i, i, i, i, d, d, i, ip, i, dp, dp, dp, p, d, d, i,
+                                        i, d, d, d, d, d, i, dp, dp, dp, i, ip]
+            L.or_ref_step.argtypes = [p, i]
+            L.or_ref_step.restype = i
+            L.or_ref_destroy.argtypes = [p]
+            L.or_ref_dt.argtypes = [p]
+            L.or_ref_dt.restype = d
+            L.or_ref_steps_done.argtypes = [p]
+            L.or_ref_steps_done.restype = i
+            L.or_ref_field.argtypes = [p, i]
+            L.or_ref_field.restype = dp
+            L.or_ref_traces.argtypes = [p]
+            L.or_ref_traces.restype = dp
+            L.or_ref_set_threads.argtypes = [p, i]
+            L.or_ref_zone.argtypes = [p, i, ip, ip, ip, ctypes.POINTER(ctypes.c_longlong)]
+            L.or_ref_matrix.argtypes = [p, i, i]
+            L.or_ref_matrix.restype = dp
+            L.or_ref_interp.argtypes = [dp, i, i, i, dp]
+            L.or_ref_velocity_update.argtypes = [p]
+            L.or_ref_stress_update.argtypes = [p]
             _lib = L
     return _lib
 
@@ -201,3 +224,108 @@ def cfl_dt(medium, cfl: float) -> float:
     vp = np.ascontiguousarray(medium.vp, dtype=np.float64)
     cid = np.ascontiguousarray(medium.cell_id, dtype=np.uint16)
     return float(lib().or_cfl_dt(g.nth, g.NR, g.NZ, g.dr, g.dz, cid.ctypes.data, _dp(vp), float(cfl)))
+
+
+def fft_interp(a, nb: int, half: bool) -> np.ndarray:
+    """The coarse-to-fine azimuthal interpolation of the refined grid (the
+    paper's three FFT steps, Sec. 3), applied by the oracle to samples `a`."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    out = np.zeros(nb)
+    lib().or_ref_interp(_dp(a), len(a), int(nb), int(bool(half)), _dp(out))
+    return out
+
+
+class RefinedOracle:
+    """One oracle run on the azimuthally refined grid: `rows` are the rows
+    where zones 1 .. M-1 start; zone m has nth / 2^(M-1-m) azimuthal nodes.
+    The medium is given on the finest azimuthal grid (the scenario's)."""
+
+    def __init__(self, scenario, rows, *, max_steps: int | None = None, dt: float = 0.0,
+                 pml_on: bool | None = None, threads: int = 0):
+        L = lib()
+        m = scenario.medium
+        g = m.grid
+        src = scenario.source
+        rec = scenario.receivers
+        self.grid = g
+        self.rows = [int(r) for r in rows]
+        self.M = len(self.rows) + 1
+        self._row0 = (ctypes.c_int * max(1, len(self.rows)))(*self.rows)
+        self._rho = np.ascontiguousarray(m.rho, dtype=np.float64)
+        self._vp = np.ascontiguousarray(m.vp, dtype=np.float64)
+        self._vs = np.ascontiguousarray(m.vs, dtype=np.float64)
+        self._id = np.ascontiguousarray(m.cell_id, dtype=np.uint16)
+        self._rr = np.ascontiguousarray(rec.r, dtype=np.float64)
+        self._rt = np.ascontiguousarray(rec.theta, dtype=np.float64)
+        self._rz = np.ascontiguousarray(rec.z, dtype=np.float64)
+        on = scenario.pml_on if pml_on is None else pml_on
+        cap = int(scenario.steps if max_steps is None else max_steps)
+        err = ctypes.c_int(0)
+        h = L.or_ref_create(g.nr, g.nth, g.nz, g.pml_r, g.pml_z, g.dr, g.dz, self.M, self._row0,
+                            len(self._rho), _dp(self._rho), _dp(self._vp), _dp(self._vs), self._id.ctypes.data,
+                            float(scenario.cfl), float(dt), int(bool(on)),
+                            int(src.kind), float(src.r), float(src.theta), float(src.z), float(src.f0),
+                            float(src.amplitude), len(self._rr), _dp(self._rr), _dp(self._rt), _dp(self._rz),
+                            cap, ctypes.byref(err))
+        if not h:
+            raise OracleError(f"or_ref_create failed with code {err.value}")
+        self._h = ctypes.c_void_p(h)
+        self._L = L
+        self.n_rec = len(self._rr)
+        self.cap = cap
+        self.zones = []  # (first row, rows, nth, element offset)
+        for z in range(self.M):
+            row, rows, nth, off = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+            L.or_ref_zone(self._h, z, ctypes.byref(row), ctypes.byref(rows), ctypes.byref(nth), ctypes.byref(off))
+            self.zones.append((row.value, rows.value, nth.value, off.value))
+        if threads:
+            L.or_ref_set_threads(self._h, int(threads))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._L.or_ref_destroy(h)
+            self._h = None
+
+    @property
+    def dt(self) -> float:
+        return float(self._L.or_ref_dt(self._h))
+
+    @property
+    def steps_done(self) -> int:
+        return int(self._L.or_ref_steps_done(self._h))
+
+    def step(self, n: int = 1):
+        rc = self._L.or_ref_step(self._h, int(n))
+        if rc != 0:
+            raise OracleError(f"or_ref_step failed with code {rc}")
+        return self
+
+    def velocity_update(self):
+        self._L.or_ref_velocity_update(self._h)
+
+    def stress_update(self):
+        self._L.or_ref_stress_update(self._h)
+
+    def field(self, name: str, zone: int) -> np.ndarray:
+        """Writable view of a field on one zone, shape [nth_zone][rows][NZ]."""
+        q = FIELDS.index(name)
+        row, rows, nth, off = self.zones[zone]
+        NZ = self.grid.NZ
+        last = self.zones[-1]
+        total = last[3] + last[1] * last[2] * NZ
+        full = np.ctypeslib.as_array(self._L.or_ref_field(self._h, q), shape=(total,))
+        return full[off:off + rows * nth * NZ].reshape(rows, nth, NZ).transpose(1, 0, 2)
+
+    def matrix(self, interface: int, half: bool) -> np.ndarray:
+        """Coarse-to-fine matrix of interface m (zone m-1 -> zone m)."""
+        nb, na = self.zones[interface][2], self.zones[interface - 1][2]
+        ptr = self._L.or_ref_matrix(self._h, int(interface), int(bool(half)))
+        return np.ctypeslib.as_array(ptr, shape=(nb, na)).copy()
+
+    def traces(self) -> np.ndarray:
+        n = min(self.steps_done, self.cap)
+        if self.n_rec == 0 or self.cap == 0:
+            return np.zeros((self.n_rec, n))
+        full = np.ctypeslib.as_array(self._L.or_ref_traces(self._h), shape=(self.n_rec, self.cap))
+        return full[:, :n].copy()

@@ -151,7 +151,7 @@ double or_cfl_dt(int nth, int NR, int NZ, double dr, double dz, const uint16_t *
 }
 
 /* recursive-convolution coefficients for damping d and frequency shift alpha */
-static void cpml_ab(double d, double al, double dt, double *a, double *b) {
+void cpml_ab(double d, double al, double dt, double *a, double *b) {
   if (!(d > 0.0)) {
     *a = 0.0;
     *b = 1.0;
@@ -162,13 +162,13 @@ static void cpml_ab(double d, double al, double dt, double *a, double *b) {
 }
 
 /* profile d(x) = d0 (x/L)^2 at depth x into a layer of thickness L */
-static double pml_d(double x, double L, double d0) {
+double pml_d(double x, double L, double d0) {
   if (x <= 0.0 || L <= 0.0) return 0.0;
   return d0 * (x / L) * (x / L);
 }
 
 /* dbar(r) = (1/r) int_0^x d, the damping of the stretched radius r~ */
-static double pml_dbar(double x, double r, double L, double d0) {
+double pml_dbar(double x, double r, double L, double d0) {
   if (x <= 0.0 || L <= 0.0 || r <= 0.0) return 0.0;
   return d0 * x * x * x / (3.0 * L * L) / r;
 }

@@ -59,8 +59,16 @@ def weights(grid):
 def energy(coef, grid, v_old, v_new, s):
     """E^n = 1/2 sum w rho v^{n-1/2}.v^{n+1/2} + sum w W(s^n)."""
     wi, wh = weights(grid)
+    return energy_terms(coef, wi, wh, v_old, v_new, s, axis=True)
+
+
+def energy_terms(coef, wi, wh, v_old, v_new, s, axis):
+    """The same sum over one block of rows with node weights wi (r_i nodes)
+    and wh (r_{i+1/2} nodes); `axis`: the block's first row is ring 0, whose
+    v_r is not an unknown."""
     kin = 0.0
-    a = v_old["vr"][:, 1:, :] * v_new["vr"][:, 1:, :] * coef["rho_vr"][:, 1:, :] * wi[:, 1:, :]
+    a0 = 1 if axis else 0
+    a = v_old["vr"][:, a0:, :] * v_new["vr"][:, a0:, :] * coef["rho_vr"][:, a0:, :] * wi[:, a0:, :]
     kin += a.sum()
     kin += (v_old["vp"] * v_new["vp"] * coef["rho_vp"] * wh).sum()
     kin += (v_old["vz"][:, :, :-1] * v_new["vz"][:, :, :-1] * coef["rho_vz"][:, :, :-1] * wh).sum()
@@ -108,3 +116,57 @@ def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64).ravel()
     b = np.asarray(b, dtype=np.float64).ravel()
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ----------------------------------------------------------- refined grid
+def zone_blocks(medium, rows):
+    """The zones of the azimuthally refined grid whose zones 1 .. M-1 start at
+    `rows`: (first row, rows, nth, cell IDs [nth][rows][NZ] with, below zone
+    m > 0, the coarse zone's last row seen from the fine nodes (fine node j ->
+    coarse cell floor(j/2)) prepended).  Zone m samples the finest grid at its
+    own nodes."""
+    g = medium.grid
+    M = len(rows) + 1
+    row0 = [0] + list(rows) + [g.NR]
+    out = []
+    for m in range(M):
+        nth = g.nth >> (M - 1 - m)
+        cid = medium.cell_id[:: g.nth // nth, row0[m]:row0[m + 1], :]
+        if m > 0:
+            stride_a = g.nth // (nth // 2)
+            ghost = medium.cell_id[(np.arange(nth) // 2) * stride_a, row0[m] - 1, :]
+            cid = np.concatenate([ghost[:, None, :], cid], axis=1)
+        out.append((row0[m], row0[m + 1] - row0[m], nth, cid))
+    return out
+
+
+class _Block:
+    def __init__(self, medium, nth, cid):
+        self.rho, self.vp, self.vs = medium.rho, medium.vp, medium.vs
+        self.cell_id = cid
+        self.grid = type("G", (), {"shape": cid.shape})()
+
+
+def refined_coefficients(medium, rows):
+    """Per zone: node coefficients of its own rows (R5 with the ghost cells of R14)."""
+    out = []
+    for row, n, nth, cid in zone_blocks(medium, rows):
+        c = node_coefficients(_Block(medium, nth, cid))
+        if cid.shape[1] > n:
+            c = {k: v[:, 1:, :] for k, v in c.items()}
+        out.append((row, n, nth, c))
+    return out
+
+
+def energy_refined(grid, zcoef, v_old, v_new, s):
+    """Energy of the refined grid: the sum over zones, each with its own
+    azimuthal step; fields are dicts of per-zone arrays."""
+    E = 0.0
+    for m, (row, n, nth, c) in enumerate(zcoef):
+        ri = (row + np.arange(n)) * grid.dr
+        rh = (row + np.arange(n) + 0.5) * grid.dr
+        dv = grid.dr * (2 * np.pi / nth) * grid.dz
+        pick = lambda d: {k: v[m] for k, v in d.items()}
+        E += energy_terms(c, ri[None, :, None] * dv, rh[None, :, None] * dv, pick(v_old), pick(v_new), pick(s),
+                          axis=row == 0)
+    return E

@@ -1,0 +1,181 @@
+"""Pins of the oracle's azimuthally refined grid (Sec. 3, "Azimuth grid
+refinement"; reading R14), each against something other than the oracle's
+own code:
+
+* the interpolation reproduces band-limited trigonometric polynomials
+  exactly at the fine nodes, for both azimuthal staggerings (the exactness
+  the paper cites FFT interpolation for);
+* its matrix keeps constants and the coarse values at coinciding nodes;
+* a grid of one zone is the uniform grid: the pinned uniform oracle's
+  fields, to rounding;
+* an axisymmetric problem does not depend on the azimuthal step at all, so
+  the refined grid reproduces the uniform one at every node it has;
+* the discrete energy of the scheme (tests/helpers.py, written from the
+  definition) stays constant across interfaces: the fine-to-coarse map is
+  the adjoint of the coarse-to-fine one;
+* a dipole (m = 1) source on a refined grid stays close to the uniform
+  fine grid.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_13907_gb300 import workloads as W
+from tests.helpers import energy_refined, refined_coefficients, rel_l2
+
+FIELDS = oracle.FIELDS
+HALF = ("vp", "srp", "spz")
+
+
+@pytest.mark.parametrize("na", [4, 8, 16, 32])
+@pytest.mark.parametrize("half", [False, True])
+def test_interpolation_exact_on_trig_polynomials(na, half):
+    nb = 2 * na
+    rng = np.random.default_rng(na + 100 * half)
+    off = 0.5 if half else 0.0
+    ta = (np.arange(na) + off) * 2 * np.pi / na
+    tb = (np.arange(nb) + off) * 2 * np.pi / nb
+    for m in range(0, na // 2):
+        a0, b0 = rng.standard_normal(2)
+        f = lambda t: a0 * np.cos(m * t) + b0 * np.sin(m * t)
+        got = oracle.fft_interp(f(ta), nb, half)
+        assert np.abs(got - f(tb)).max() < 1e-12 * max(1.0, abs(a0) + abs(b0)), (m, half)
+
+
+def test_interpolation_nyquist_mode_is_the_cosine():
+    """The Nyquist coefficient is split evenly, so the coarse grid-scale
+    oscillation (-1)^j interpolates to cos(N/2 theta)."""
+    na = 8
+    got = oracle.fft_interp((-1.0) ** np.arange(na), 2 * na, False)
+    want = np.cos(na / 2 * np.arange(2 * na) * 2 * np.pi / (2 * na))
+    assert np.abs(got - want).max() < 1e-13
+
+
+def _scenario(nr=24, nth=16, nz=40, pml_r=4, pml_z=4, kind=0, axis=True, seed=None, steps=120):
+    g = W.Grid(nr=nr, nth=nth, nz=nz, pml_r=pml_r, pml_z=pml_z, dr=0.004, dz=0.004)
+    med = W.cased_well(g, z_top=0.08)
+    if seed is not None:  # a non-axisymmetric medium outside ring 0
+        rng = np.random.default_rng(seed)
+        mats = [W.FLUID, W.STEEL, W.CEMENT, W.ROCK]
+        cid = rng.integers(0, len(mats), size=g.shape).astype(np.uint16)
+        cid[:, 0, :] = 0
+        med = W.Medium(g, cid, np.array([m[0] for m in mats]), np.array([m[1] for m in mats]),
+                       np.array([m[2] for m in mats]))
+    src = W.Source(r=0.0 if axis else 0.0305, theta=0.7, z=0.08, f0=60e3, kind=kind)
+    rec = W.Receivers(r=np.array([0.0, 0.021, 0.061]), theta=np.array([0.0, 0.4, 2.0]),
+                      z=np.array([0.05, 0.1, 0.12]))
+    return W.Scenario("refine", med, src, rec, steps=steps)
+
+
+def test_matrix_keeps_constants_and_coinciding_nodes():
+    o = oracle.RefinedOracle(_scenario(), rows=[6, 12])
+    for m in (1, 2):
+        Pi, Ph = o.matrix(m, False), o.matrix(m, True)
+        assert np.abs(Pi.sum(axis=1) - 1).max() < 1e-13
+        assert np.abs(Ph.sum(axis=1) - 1).max() < 1e-13
+        na = Pi.shape[1]
+        assert np.abs(Pi[0::2] - np.eye(na)).max() < 1e-13  # even fine nodes are coarse nodes
+
+
+@pytest.mark.parametrize("kind,axis", [(0, False), (1, True), (1, False)])
+def test_single_zone_is_the_uniform_oracle(kind, axis):
+    sc = _scenario(kind=kind, axis=axis, seed=3)
+    u = oracle.Oracle(sc)
+    r = oracle.RefinedOracle(sc, rows=[])
+    assert r.dt == u.dt
+    u.step(80)
+    r.step(80)
+    for n in FIELDS:
+        a, b = r.field(n, 0), u.field(n)
+        assert np.abs(a - b).max() <= 1e-13 * max(np.abs(b).max(), 1e-300), n
+    assert np.abs(r.traces() - u.traces()).max() <= 1e-13 * np.abs(u.traces()).max()
+
+
+def test_axisymmetric_problem_reproduced_on_every_zone():
+    """Monopole on the axis in an axisymmetric well: nothing depends on theta,
+    so the coarse zones must carry exactly the uniform grid's values."""
+    sc = _scenario(kind=0, axis=True)
+    dt = oracle.Oracle(sc).dt
+    u = oracle.Oracle(sc, dt=dt)
+    r = oracle.RefinedOracle(sc, rows=[6, 12], dt=dt)
+    u.step(150)
+    r.step(150)
+    vscale = max(np.abs(u.field(n)).max() for n in ("vr", "vz"))
+    sscale = max(np.abs(u.field(n)).max() for n in ("srr", "spp", "szz", "srz"))
+    for n in FIELDS:
+        b = u.field(n)
+        scale = vscale if n in ("vr", "vp", "vz") else sscale  # v_phi, s_rphi, s_phiz vanish
+        for z, (row, rows, nth, _) in enumerate(r.zones):
+            a = r.field(n, z)
+            want = b[:: sc.medium.grid.nth // nth, row:row + rows, :]
+            assert np.abs(a - want).max() <= 1e-11 * scale, (n, z, np.abs(a - want).max() / scale)
+    assert rel_l2(r.traces(), u.traces()) < 1e-11
+
+
+def test_cfl_uses_each_zone_azimuthal_step():
+    """64 azimuthal nodes: the axis cells set the uniform grid's dt; with 8
+    nodes in the innermost zone the steel casing sets it."""
+    sc = _scenario(nth=64)
+    u = oracle.Oracle(sc)
+    r = oracle.RefinedOracle(sc, rows=[3, 6, 12])
+    assert r.dt > 1.5 * u.dt, (r.dt, u.dt)
+    assert r.dt == oracle.RefinedOracle(sc, rows=[3, 6, 12], pml_on=False).dt
+
+
+def _admissible_zones(o, zcoef, seed):
+    rng = np.random.default_rng(seed)
+    NZ = o.grid.NZ
+    for z, (row, n, nth, c) in enumerate(zcoef):
+        f = {k: rng.standard_normal((nth, n, NZ)) for k in FIELDS}
+        for k in ("vr", "vp", "vz"):
+            f[k] *= 1e-3
+        if row == 0:
+            f["vr"][:, 0, :] = 0
+        f["vz"][:, :, -1] = 0
+        fluid = c["mu"] == 0
+        f["spp"][fluid] = f["srr"][fluid]
+        f["szz"][fluid] = f["srr"][fluid]
+        f["srp"][c["mu_rp"] == 0] = 0
+        f["srz"][c["mu_rz"] == 0] = 0
+        f["spz"][c["mu_pz"] == 0] = 0
+        for k in FIELDS:
+            o.field(k, z)[...] = f[k]
+
+
+@pytest.mark.parametrize("rows,nth", [([4, 10], 16), ([3, 7, 14], 32)])
+def test_energy_conserved_across_interfaces(rows, nth):
+    """PML off, random admissible state in every zone, 800 leapfrog steps:
+    the discrete energy is constant to rounding."""
+    sc = _scenario(nr=24, nth=nth, nz=40, pml_r=0, pml_z=0, seed=5)
+    o = oracle.RefinedOracle(sc, rows=rows, max_steps=0, pml_on=False)
+    zcoef = refined_coefficients(sc.medium, rows)
+    _admissible_zones(o, zcoef, seed=11)
+    M = o.M
+    get = lambda names: {n: [o.field(n, z).copy() for z in range(M)] for n in names}
+    E = []
+    v_old = get(("vr", "vp", "vz"))
+    for it in range(800):
+        s_now = get(("srr", "spp", "szz", "srp", "spz", "srz"))
+        o.velocity_update()
+        v_new = get(("vr", "vp", "vz"))
+        if it % 100 == 0 or it == 799:
+            E.append(energy_refined(sc.medium.grid, zcoef, v_old, v_new, s_now))
+        o.stress_update()
+        v_old = v_new
+    E = np.array(E)
+    assert E[0] > 0
+    assert np.max(np.abs(E - E[0])) / E[0] < 1e-12, np.max(np.abs(E - E[0])) / E[0]
+
+
+def test_dipole_on_refined_grid_close_to_uniform():
+    """Transverse force on the axis (an m = 1 field): the refined grid's
+    traces at off-axis receivers stay within a few per cent of the uniform
+    fine grid's (the coarse zones have fewer azimuthal nodes near the axis)."""
+    sc = _scenario(nr=30, nth=32, nz=60, kind=1, axis=True, steps=400)
+    u = oracle.Oracle(sc)
+    r = oracle.RefinedOracle(sc, rows=[4, 8, 16], dt=u.dt)
+    u.step(400)
+    r.step(400)
+    tu, tr = u.traces(), r.traces()
+    for q in (1, 2):
+        assert rel_l2(tr[q], tu[q]) < 0.08, (q, rel_l2(tr[q], tu[q]))
