@@ -248,6 +248,53 @@ void simb_destroy(simb_t *b);
 const char *simb_last_error(const simb_t *b);
 
 /* ------------------------------------------------------------------------
+ * Azimuthally refined grid (paper Sec. 3, "Azimuth grid refinement": the
+ * azimuthal step halves each time the radius doubles).  The rows form
+ * n_zones radial zones; zone m starts at row row0[m - 1] (zone 0 at row 0)
+ * and has grid.nth / 2^(n_zones - 1 - m) azimuthal nodes, so the outermost
+ * zone has grid.nth.  Inside a zone the scheme is the uniform grid's.  Where
+ * a stencil crosses an interface it reads the other zone's row at its own
+ * nodes: coarse -> fine by trigonometric (FFT zero-padding) interpolation,
+ * the Nyquist coefficient split; fine -> coarse by its adjoint
+ * (dtheta_fine / dtheta_coarse) P^T, which keeps the discrete energy exact.
+ * dt follows the CFL rule with each row's own azimuthal step, so coarse
+ * zones near the axis allow a larger dt than the uniform grid.
+ *
+ * Arguments as sim_create; the medium is given on the finest azimuthal grid
+ * [grid.nth][nr + pml_r][nz + 2 pml_z] and zone m samples it at its nodes
+ * (cell j of zone m = cell j 2^(n_zones - 1 - m)).  Restrictions (SIM_EINVAL
+ * or SIM_EUNSUPPORTED): 1 to 5 zones; with interfaces grid.nth in {8, 16, 32,
+ * 64} and nth / 2^(n_zones - 1) >= 4; interface rows increasing, at least two
+ * rows per zone, the radial PML inside the last zone (row0 <= nr - 2); FP32
+ * storage; source kind 0 or 1 (kind 1 off the axis not on a zone's first row).
+ * Ownership and errors as sim_create; simr_last_error(NULL) after a failed create.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int n_zones;
+  const int *row0; /* n_zones - 1 interface rows */
+} simr_zones_t;
+typedef struct simr_s simr_t;
+
+int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, const sim_medium_t *medium,
+                const sim_source_t *source, const sim_receivers_t *receivers, const sim_opts_t *opts, simr_t **out);
+/* Enqueue nsteps leapfrog steps (CUDA-graph chunks of opts.graph_chunk steps). */
+int simr_step(simr_t *h, int nsteps);
+/* Wait; SIM_EUNSTABLE if a receiver sample was not finite. */
+int simr_sync(simr_t *h);
+/* Traces [n_rec][n_steps] in the order of the receivers given at create. */
+int simr_traces(simr_t *h, float *out, size_t cap, int *n_rec, int *n_steps);
+/* Zone geometry: first row, rows, azimuthal nodes. */
+int simr_zone(const simr_t *h, int zone, int *row, int *rows, int *nth);
+/* Field (F order of sim_read_field) of one zone: [nth_zone][rows][nz + 2 pml_z] FP32, n floats. */
+int simr_read_field(simr_t *h, int field, int zone, float *out, size_t n);
+double simr_dt(const simr_t *h);
+int simr_steps_done(const simr_t *h);
+/* Cells updated per step (every zone's own rows). */
+size_t simr_cells(const simr_t *h);
+void simr_destroy(simr_t *h);
+const char *simr_last_error(const simr_t *h);
+
+/* ------------------------------------------------------------------------
  * Trace surrogate: maps the six case parameters of a cement-hardening
  * scenario to its 8 receiver traces over the reflected window.  The paper
  * has no learned component; this network is trained on traces the simulator

@@ -48,6 +48,10 @@ class SimOpts(ctypes.Structure):
                 ("kernel", ctypes.c_int), ("timing", ctypes.c_int), ("device", ctypes.c_int), ("tile", ctypes.c_int)]
 
 
+class SimZones(ctypes.Structure):
+    _fields_ = [("n_zones", ctypes.c_int), ("row0", ctypes.POINTER(ctypes.c_int))]
+
+
 _lib = None
 
 
@@ -112,6 +116,30 @@ def lib(path: str | None = None):
         L.simb_destroy.restype = None
         L.simb_last_error.argtypes = [p]
         L.simb_last_error.restype = ctypes.c_char_p
+        L.simr_create.argtypes = [ctypes.POINTER(SimGrid), ctypes.POINTER(SimZones), ctypes.POINTER(SimMedium),
+                                  ctypes.POINTER(SimSource), ctypes.POINTER(SimReceivers), ctypes.POINTER(SimOpts),
+                                  ctypes.POINTER(p)]
+        L.simr_create.restype = i
+        L.simr_step.argtypes = [p, i]
+        L.simr_step.restype = i
+        L.simr_sync.argtypes = [p]
+        L.simr_sync.restype = i
+        L.simr_traces.argtypes = [p, ctypes.POINTER(ctypes.c_float), sz, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.simr_traces.restype = i
+        L.simr_zone.argtypes = [p, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.simr_zone.restype = i
+        L.simr_read_field.argtypes = [p, i, i, ctypes.POINTER(ctypes.c_float), sz]
+        L.simr_read_field.restype = i
+        L.simr_dt.argtypes = [p]
+        L.simr_dt.restype = d
+        L.simr_steps_done.argtypes = [p]
+        L.simr_steps_done.restype = i
+        L.simr_cells.argtypes = [p]
+        L.simr_cells.restype = sz
+        L.simr_destroy.argtypes = [p]
+        L.simr_destroy.restype = None
+        L.simr_last_error.argtypes = [p]
+        L.simr_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -320,6 +348,79 @@ class BatchSimulation:
         n, w, g = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
         self._chk(self.L.simb_config(self.h, ctypes.byref(n), ctypes.byref(w), ctypes.byref(g)))
         return n.value, w.value, g.value
+
+
+class RefinedSimulation:
+    """One well on the azimuthally refined grid (simr_create ... simr_destroy):
+    zones 1 .. M-1 start at `rows`; zone m has nth / 2^(M-1-m) azimuthal nodes."""
+
+    def __init__(self, scenario, rows, **kw):
+        self.L = lib()
+        (grid, med, src, rec, opts), self._keep = make_structs(scenario, **kw)
+        self._rows = (ctypes.c_int * max(1, len(rows)))(*[int(r) for r in rows])
+        zones = SimZones(len(rows) + 1, self._rows)
+        self.grid = scenario.medium.grid
+        h = ctypes.c_void_p()
+        rc = self.L.simr_create(ctypes.byref(grid), ctypes.byref(zones), ctypes.byref(med), ctypes.byref(src),
+                                ctypes.byref(rec), ctypes.byref(opts), ctypes.byref(h))
+        if rc != SIM_OK:
+            raise SimError(rc, self.L.simr_last_error(None).decode())
+        self.h = h
+        self.M = len(rows) + 1
+        self.zones = []
+        for z in range(self.M):
+            a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            self._chk(self.L.simr_zone(self.h, z, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+            self.zones.append((a.value, b.value, c.value))  # first row, rows, nth
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.simr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _chk(self, rc):
+        if rc != SIM_OK:
+            raise SimError(rc, self.L.simr_last_error(self.h).decode())
+
+    @property
+    def dt(self) -> float:
+        return float(self.L.simr_dt(self.h))
+
+    @property
+    def cells(self) -> int:
+        return int(self.L.simr_cells(self.h))
+
+    def step(self, n: int):
+        self._chk(self.L.simr_step(self.h, int(n)))
+        return self
+
+    def sync(self):
+        self._chk(self.L.simr_sync(self.h))
+
+    def traces(self) -> np.ndarray:
+        nr, ns = ctypes.c_int(), ctypes.c_int()
+        self._chk(self.L.simr_traces(self.h, None, 0, ctypes.byref(nr), ctypes.byref(ns)))
+        out = np.zeros((nr.value, ns.value), np.float32)
+        self._chk(self.L.simr_traces(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size,
+                                     ctypes.byref(nr), ctypes.byref(ns)))
+        return out
+
+    def field(self, name: str, zone: int) -> np.ndarray:
+        """[nth_zone][rows][NZ] of one zone."""
+        row, rows, nth = self.zones[zone]
+        out = np.zeros((nth, rows, self.grid.NZ), np.float32)
+        self._chk(self.L.simr_read_field(self.h, FIELDS.index(name), int(zone),
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size))
+        return out
 
 
 # ------------------------------------------------------------------ surrogate

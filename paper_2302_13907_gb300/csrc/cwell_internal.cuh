@@ -51,6 +51,7 @@ struct KParams {
   int n_wav;
   int src_i, src_j, src_k;  // src_j < 0: all ring-0 cells
   int *step;                // device step counter
+  int i_lo, i_hi;           // rows updated: i_lo <= i < i_hi (the rest are interface ghost rows)
 };
 
 // Point forces and the torsion ring (source kinds 1-3): entry e adds
@@ -199,6 +200,24 @@ long long split_items(int nth, int NR, int NZ);
 constexpr int BATCH_MAX = 64;
 cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, int n_cases, int grid, cudaStream_t s);
 cudaError_t launch_batch_receivers(int storage, const RParams *rp, int n_cases, cudaStream_t s);
+
+// Azimuthally refined grid: ghost rows filled from the neighbouring zone's
+// row through a dense [n_out][n_in] interpolation matrix along theta, for
+// every z cell: dst[jo * dst_plane + k] = sum_ji mat[jo][ji] src[ji * src_plane + k]
+// (FP32 storage only).
+constexpr int XFER_MAX = 24;
+struct XferDesc {
+  const float *src;
+  float *dst;
+  const float *mat;
+  int n_in, n_out;
+  long long src_plane, dst_plane;
+};
+struct XferParams {
+  XferDesc d[XFER_MAX];
+  int n, NZ;
+};
+cudaError_t launch_xfer(const XferParams &p, cudaStream_t s);
 int fused_box_x(int storage);
 cudaError_t launch_fused4(int storage, int rt, const FusedMaps &maps, const FusedParams &fp, cudaStream_t s);
 size_t fused4_smem_bytes(int storage, int rt);

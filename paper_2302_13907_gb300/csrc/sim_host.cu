@@ -37,13 +37,13 @@ static int dev_alloc(sim_t *h, void **p, size_t bytes) {
 }
 
 // Ricker pulse, dominant frequency f0, delay 2/f0 (Sec. 2 of the paper)
-static double ricker(double t, double f0) {
+double cwell::ricker(double t, double f0) {
   double a = M_PI * f0 * (t - 2.0 / f0);
   a = a * a;
   return (1.0 - 2.0 * a) * exp(-a);
 }
 
-static void cpml(double d, double al, double dt, float *a, float *b) {
+void cwell::cpml(double d, double al, double dt, float *a, float *b) {
   if (!(d > 0.0)) {
     *a = 0.f;
     *b = 1.f;
@@ -660,6 +660,8 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   p.src_j = js;
   p.src_k = (int)ks;
   p.step = h->step;
+  p.i_lo = 0;
+  p.i_hi = NR;
   h->ip.n = (int)ifld.size();
   h->ip.fld = d_ifld;
   h->ip.off = d_ioff;

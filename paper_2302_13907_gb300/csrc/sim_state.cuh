@@ -85,6 +85,10 @@ inline int cuda_fail(sim_t *h, cudaError_t e, const char *what) {
 int validate_inputs(const sim_grid_t *g, const sim_medium_t *m, const sim_source_t *s, const sim_receivers_t *r,
                     const sim_opts_t *o);
 
+// Ricker pulse with delay 2/f0 (Sec. 2) and the C-PML recursion coefficients
+double ricker(double t, double f0);
+void cpml(double d, double al, double dt, float *a, float *b);
+
 // steps enqueued on the handle (the batch advances its cases directly)
 inline void sim_advance(sim_t *h, int n) { h->steps_done += n; }
 

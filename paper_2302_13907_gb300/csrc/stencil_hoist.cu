@@ -660,7 +660,9 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_edge(const KParams p, 
 // launch's items (start[c] = first item of case c, start[n] = total) travel in
 // the kernel's parameter space, so a block reads its case's geometry and
 // buffers from the constant bank.  The index inside a case is 32-bit (checked
-// on the host).  Cells per thread and blocks per SM: the velocity half takes
+// on the host); rows outside [i_lo, i_hi) are left alone (the ghost rows of
+// an azimuthally refined grid's zones, which run as cases).  Cells per
+// thread and blocks per SM: the velocity half takes
 // interior (4, 5) and edge (4, 3), the stress half interior (4, 4) and edge
 // (2, 4), the split launches the tuner picks for the single well.
 struct BatchParams {
@@ -706,6 +708,7 @@ __global__ void __launch_bounds__(HB_X *HB_Y, BatchCfg<VEL>::MINB_IN)
     t /= p.nth;
     const int i = (t % q.nrt_in) * HB_Y + threadIdx.y;
     const int k0 = ((q.zt_lo + t / q.nrt_in) * HB_X + threadIdx.x) * BATCH_NV;
+    if (i < p.i_lo || i >= p.i_hi) continue;
     if (VEL) vel_hoist_body<T, BATCH_NV, true>(p, j, i, k0);
     else str_hoist_body<T, BATCH_NV, true>(p, j, i, k0);
   }
@@ -722,7 +725,7 @@ __global__ void __launch_bounds__(HB_X *HB_Y, BatchCfg<VEL>::MINB_E) batch_edge(
     const int j = t % p.nth;
     edge_tile(bp.q[c], t / p.nth, rt, zt);
     const int i = rt * HB_Y + threadIdx.y, k0 = (zt * HB_X + threadIdx.x) * NVE;
-    if (i < p.NR && k0 < p.NZ) hoist_cells<T, NVE, VEL, true>(p, j, i, k0);
+    if (i >= p.i_lo && i < p.i_hi && k0 < p.NZ) hoist_cells<T, NVE, VEL, true>(p, j, i, k0);
   }
 }
 

@@ -424,6 +424,24 @@ def config2(noise_seed: int = 20230227, nz: int = 8192) -> Scenario:
                     receivers=on_axis_receivers(zr), cfl=0.5, steps=20000)
 
 
+def refinement_rows(grid: Grid, min_nth: int = 4) -> list:
+    """Interface rows of the azimuthal refinement of the paper (Sec. 3): the
+    azimuthal step halves each time the radius doubles, so going inward from
+    the outer radius the node count halves each time the radius halves, from
+    grid.nth down to min_nth: zone boundaries at rows NR / 2^k.  A boundary
+    that would leave a zone under two rows, or fall inside the radial PML,
+    is dropped (the zones keep their node counts from the outside in)."""
+    K = 0
+    while (grid.nth >> (K + 1)) >= min_nth and (grid.nth >> (K + 1)) % 2 == 0:
+        K += 1
+    rows = []
+    for k in range(K, 0, -1):
+        r = int(round(grid.NR / 2 ** k))
+        if r >= (rows[-1] if rows else 0) + 2 and r <= grid.nr - 2:
+            rows.append(r)
+    return rows
+
+
 def config3_crop(full: Optional[Scenario] = None) -> Scenario:
     """Nz=1024 crop z in [8.0, 10.56) m of the full 20 m well (same noise)."""
     full = full or config2()

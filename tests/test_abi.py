@@ -20,7 +20,7 @@ def declared_symbols():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         txt = open(h).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-        for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b((?:sim|simb|sur|cw)_\w+)\s*\(", txt, flags=re.M):
+        for m in re.finditer(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b((?:sim|simb|simr|sur|cw)_\w+)\s*\(", txt, flags=re.M):
             names.add(m.group(1))
     return sorted(names)
 
@@ -29,7 +29,7 @@ def test_library_builds_and_exports_every_declared_symbol():
     path = Bld.build()
     L = ctypes.CDLL(path)
     names = declared_symbols()
-    assert "sim_create" in names and "sim_step" in names and "sim_traces" in names
+    assert "sim_create" in names and "sim_step" in names and "sim_traces" in names and "simr_create" in names
     missing = [n for n in names if not hasattr(L, n)]
     assert not missing, missing
 
@@ -86,3 +86,39 @@ def test_error_strings():
     L = B.lib()
     for c in (0, -1, -2, -3, -4, -5, -6):
         assert L.sim_error_string(c)
+
+
+def _refined(nth=16, nr=16):
+    g = W.Grid(nr=nr, nth=nth, nz=16, pml_r=2, pml_z=2, dr=0.005, dz=0.005)
+    return W.Scenario("tiny", W.cased_well(g, z_top=0.04, casing_in=0.02, casing_t=0.005, cement_out=0.03),
+                      W.Source(z=0.03), W.on_axis_receivers([0.05]), steps=10)
+
+
+@pytest.mark.parametrize("rows,kw,code", [
+    ([4, 8], dict(storage="bf16"), B.SIM_EUNSUPPORTED),   # FP32 only
+    ([4, 8], dict(kernel="fused"), B.SIM_EUNSUPPORTED),   # split kernels only
+    ([8, 4], {}, B.SIM_EINVAL),                           # interface rows not increasing
+    ([1, 8], {}, B.SIM_EINVAL),                           # one-row zone
+    ([4, 15], {}, B.SIM_EINVAL),                          # interface inside the radial PML
+    ([2, 4, 8], {}, B.SIM_EINVAL),                        # 16 / 2^3 = 2 nodes in zone 0
+    ([4, 8], dict(source_kind=2), B.SIM_EUNSUPPORTED),    # longitudinal force not on this grid
+    ([4, 8], dict(nth=24), B.SIM_EINVAL),                 # nth not a power of two
+    ([4, 8], dict(source_kind=1, source_r=0.02), B.SIM_EUNSUPPORTED),  # force node on a zone's first row
+])
+def test_refined_grid_host_validation(rows, kw, code):
+    """simr_create checks its zones, storage, kernel and source on the host
+    before any device call."""
+    kw = dict(kw)
+    sc = _refined(nth=kw.pop("nth", 16))
+    sc.source.kind = kw.pop("source_kind", 0)
+    sc.source.r = kw.pop("source_r", 0.0)
+    L = B.lib()
+    (g, m, s, r, o), keep = B.make_structs(sc, **kw)
+    arr = (ctypes.c_int * len(rows))(*rows)
+    z = B.SimZones(len(rows) + 1, arr)
+    h = ctypes.c_void_p()
+    rc = L.simr_create(ctypes.byref(g), ctypes.byref(z), ctypes.byref(m), ctypes.byref(s), ctypes.byref(r),
+                       ctypes.byref(o), ctypes.byref(h))
+    assert rc == code, L.simr_last_error(None)
+    assert not h.value
+    assert L.simr_last_error(None)
