@@ -190,7 +190,9 @@ size_t sim_device_bytes(const sim_t *h);
  * 2100 + b for two z cells per thread (b = 6, 8), 2200 + 10 c + b for interior /
  * edge split launches (a kernel with the interior body only on the tiles away
  * from every PML and end, compiled for b blocks per SM, and the general kernel
- * on the rest; c = 0: four cells per thread, b = 4, 5; c = 1: two, b = 6, 8);
+ * on the rest; interior four cells per thread, b = 4, 5, with edge c = 0 (four
+ * cells, 4 blocks/SM), 2 (two, 4), 3 (two, 6), 4 (four, 3); interior two
+ * cells, b = 6, 8, with edge c = 1 (two, 6) or 5 (two, 4));
  * v * 10000 + s (a pair code) for the velocity kernel of split code v with the
  * stress kernel of split code s.  opts.tile accepts every code listed here. */
 int sim_config(const sim_t *h, int *kernel, int *tile_rows);

@@ -244,7 +244,8 @@ size_t march_smem_bytes(int storage, int code);
 // in both (b = 6 or 8; edge for 6 blocks per SM); otherwise four cells per
 // thread in the interior (b = 4 or 5) and an edge kernel with c = 0: four cells,
 // 4 blocks per SM; c = 2: two cells, 4 blocks; c = 3: two cells, 6 blocks;
-// c = 4: four cells, 3 blocks.  A pair code
+// c = 4: four cells, 3 blocks; c = 5: two cells in both (interior b = 6 or 8,
+// edge for 4 blocks per SM).  A pair code
 // v * 10000 + s runs the velocity kernel of split code v and the stress kernel
 // of split code s (the autotuner times the two apart).
 constexpr int SPLIT_CODE = 2000;
@@ -260,7 +261,8 @@ inline int hoist_blocks(int code) { return code % 10; }
 inline bool hoist_split(int code) { return (code / 100) % 10 == 2; }
 inline bool hoist_zfast(int code) { return !hoist_split(code) && (code / 10) % 10 == 1; }
 inline int hoist_cells_per_thread(int code) {
-  return ((code / 100) % 10 == 1 || (hoist_split(code) && (code / 10) % 10 == 1)) ? 2 : 4;
+  const int c = (code / 10) % 10;
+  return ((code / 100) % 10 == 1 || (hoist_split(code) && (c == 1 || c == 5))) ? 2 : 4;
 }
 cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts = 3);
 // BF16 GEMM on the tcgen05 tensor cores (gemm_tc.cu); status bit 0: a

@@ -821,6 +821,8 @@ cudaError_t launch_hoist_st(int nv, int minb, bool zf, bool split, int edge, con
       case 35: return launch_split2_t<T, 4, 5, 2, 6>(p, s, ev, parts);
       case 44: return launch_split2_t<T, 4, 4, 4, 3>(p, s, ev, parts);
       case 45: return launch_split2_t<T, 4, 5, 4, 3>(p, s, ev, parts);
+      case 56: return launch_split2_t<T, 2, 6, 2, 4>(p, s, ev, parts);
+      case 58: return launch_split2_t<T, 2, 8, 2, 4>(p, s, ev, parts);
     }
     return cudaErrorInvalidValue;
   }
