@@ -622,6 +622,77 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_interior(const KParams
   else str_hoist_body<T, NV, true>(p, j, i, k0);
 }
 
+// Persistent interior kernel with an L2 prefetch of the tile DIST steps
+// ahead: one wave of resident blocks walks the interior tiles in the order
+// above (theta fastest); before computing its tile a block asks L2 for every
+// row that later tile will load (one prefetch per 128-byte line), so its
+// loads find their lines in L2.  No register or shared memory holds the
+// prefetched data.
+__device__ __forceinline__ void prefetch_l2(const void *a) { asm volatile("prefetch.global.L2 [%0];" ::"l"(a)); }
+
+template <typename T, int NV, bool VEL>
+__device__ __forceinline__ void prefetch_tile(const KParams &p, int j, int i, int k0) {
+  constexpr int LANES = 128 / (NV * (int)sizeof(T));  // threads per 128-byte line of a field row
+  constexpr int LANES_ID = 128 / (NV * 2);
+  const long long pl = p.plane, NZp = p.NZp;
+  const int jm = j == 0 ? p.nth - 1 : j - 1, jp = j == p.nth - 1 ? 0 : j + 1;
+  const long long c = (long long)j * pl + i * NZp + k0, cjm = (long long)jm * pl + i * NZp + k0,
+                  cjp = (long long)jp * pl + i * NZp + k0;
+  const bool im = i >= 1, ip = i + 1 < p.NR;
+  if ((threadIdx.x & (LANES - 1)) == 0) {
+    const T *const *f = (const T *const *)p.f;
+    if (VEL) {
+      for (int q = F_VR; q <= F_VZ; q++) prefetch_l2(f[q] + c);
+      prefetch_l2(f[F_SRR] + c), prefetch_l2(f[F_SPP] + c), prefetch_l2(f[F_SZZ] + c);
+      prefetch_l2(f[F_SRP] + c), prefetch_l2(f[F_SPZ] + c), prefetch_l2(f[F_SRZ] + c);
+      if (im) prefetch_l2(f[F_SRR] + c - NZp), prefetch_l2(f[F_SPP] + c - NZp);
+      if (ip) prefetch_l2(f[F_SRP] + c + NZp), prefetch_l2(f[F_SRZ] + c + NZp);
+      prefetch_l2(f[F_SRP] + cjm), prefetch_l2(f[F_SPZ] + cjm), prefetch_l2(f[F_SPP] + cjp);
+    } else {
+      for (int q = F_SRR; q <= F_SRZ; q++) prefetch_l2(f[q] + c);
+      prefetch_l2(f[F_VR] + c), prefetch_l2(f[F_VP] + c), prefetch_l2(f[F_VZ] + c);
+      if (ip) prefetch_l2(f[F_VR] + c + NZp);
+      if (im) prefetch_l2(f[F_VP] + c - NZp), prefetch_l2(f[F_VZ] + c - NZp);
+      prefetch_l2(f[F_VP] + cjm), prefetch_l2(f[F_VR] + cjp), prefetch_l2(f[F_VZ] + cjp);
+    }
+  }
+  if ((threadIdx.x & (LANES_ID - 1)) == 0) {
+    prefetch_l2(p.id + c);
+    prefetch_l2(p.id + cjp);
+    if (im) {
+      prefetch_l2(p.id + c - NZp);
+      if (!VEL) prefetch_l2(p.id + cjp - NZp);
+    }
+  }
+}
+
+template <typename T, int NV, int MINB, bool VEL, int DIST>
+__global__ void __launch_bounds__(HB_X *HB_Y, MINB)
+    hoist_interior_pf(const KParams p, int zt_lo, int nrt_in, int ntiles) {
+  auto cell = [&](int t, int &j, int &i, int &k0) {
+    j = t % p.nth;
+    t /= p.nth;
+    i = (t % nrt_in) * HB_Y + threadIdx.y;
+    k0 = ((zt_lo + t / nrt_in) * HB_X + threadIdx.x) * NV;
+  };
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int j, i, k0;
+    if (t == (int)blockIdx.x)  // the first DIST - 1 tiles ahead, then one per iteration
+      for (int d = 1; d < DIST; d++)
+        if (t + d * (int)gridDim.x < ntiles) {
+          cell(t + d * gridDim.x, j, i, k0);
+          prefetch_tile<T, NV, VEL>(p, j, i, k0);
+        }
+    if (t + DIST * (int)gridDim.x < ntiles) {
+      cell(t + DIST * gridDim.x, j, i, k0);
+      prefetch_tile<T, NV, VEL>(p, j, i, k0);
+    }
+    cell(t, j, i, k0);
+    if (VEL) vel_hoist_body<T, NV, true>(p, j, i, k0);
+    else str_hoist_body<T, NV, true>(p, j, i, k0);
+  }
+}
+
 // edge tile t (in edge-kernel tiles of NV * HB_X cells along z): first the r
 // tiles nrt_in .. nrt-1 with every z tile, then the interior r tiles with the
 // z tiles below ez_lo and from ez_hi on
@@ -758,31 +829,50 @@ cudaError_t launch_batch_t(const KParams *cases, int n_cases, int grid, cudaStre
   return cudaSuccess;
 }
 
-template <typename T, int NV, int MINB_IN, int NVE, int MINB_E, bool VEL>
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n < 1) n = 1;
+  }
+  return n;
+}
+
+template <typename T, int NV, int MINB_IN, int NVE, int MINB_E, bool VEL, int PF>
 cudaError_t launch_split2_half(const KParams &p, const Split2 &q, cudaStream_t s) {
   dim3 blk(HB_X, HB_Y);
   const int nin = q.zt_hi - q.zt_lo;
-  if (q.nrt_in > 0 && nin > 0)
-    hoist_interior<T, NV, MINB_IN, VEL><<<dim3(p.nth, q.nrt_in, nin), blk, 0, s>>>(p, q.zt_lo);
+  if (q.nrt_in > 0 && nin > 0) {
+    if constexpr (PF > 0) {  // one wave of resident blocks, prefetch distance PF
+      const long long tiles = (long long)p.nth * q.nrt_in * nin;
+      if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+      const int grid = (int)std::min<long long>(tiles, (long long)sm_count() * MINB_IN);
+      hoist_interior_pf<T, NV, MINB_IN, VEL, (PF > 0 ? PF : 1)><<<grid, blk, 0, s>>>(p, q.zt_lo, q.nrt_in, (int)tiles);
+    } else {
+      hoist_interior<T, NV, MINB_IN, VEL><<<dim3(p.nth, q.nrt_in, nin), blk, 0, s>>>(p, q.zt_lo);
+    }
+  }
   const long long nedge = (long long)(q.nrt - q.nrt_in) * q.enzt + (long long)q.nrt_in * (q.ez_lo + q.enzt - q.ez_hi);
   if (nedge > 65535 || p.nth > 65535) return cudaErrorInvalidValue;
   if (nedge > 0) hoist_edge<T, NVE, MINB_E, VEL><<<dim3(p.nth, (unsigned)nedge), blk, 0, s>>>(p, q);
   return cudaGetLastError();
 }
 
-template <typename T, int NV, int MINB_IN, int NVE, int MINB_E>
+template <typename T, int NV, int MINB_IN, int NVE, int MINB_E, int PF = 0>
 cudaError_t launch_split2_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
   const Split2 q = split2<NV, NVE>(p);
   if (q.zt_hi - q.zt_lo > 65535) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   if (parts & 1) {
     if (ev) cudaEventRecord(ev[0], s);
-    e = launch_split2_half<T, NV, MINB_IN, NVE, MINB_E, true>(p, q, s);
+    e = launch_split2_half<T, NV, MINB_IN, NVE, MINB_E, true, PF>(p, q, s);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
   }
   if (parts & 2) {
-    e = launch_split2_half<T, NV, MINB_IN, NVE, MINB_E, false>(p, q, s);
+    e = launch_split2_half<T, NV, MINB_IN, NVE, MINB_E, false, PF>(p, q, s);
     if (ev) cudaEventRecord(ev[2], s);
   }
   return e;
@@ -823,6 +913,12 @@ cudaError_t launch_hoist_st(int nv, int minb, bool zf, bool split, int edge, con
       case 45: return launch_split2_t<T, 4, 5, 4, 3>(p, s, ev, parts);
       case 56: return launch_split2_t<T, 2, 6, 2, 4>(p, s, ev, parts);
       case 58: return launch_split2_t<T, 2, 8, 2, 4>(p, s, ev, parts);
+      case 64: return launch_split2_t<T, 4, 4, 2, 4, 1>(p, s, ev, parts);
+      case 65: return launch_split2_t<T, 4, 5, 2, 4, 1>(p, s, ev, parts);
+      case 74: return launch_split2_t<T, 4, 4, 4, 3, 1>(p, s, ev, parts);
+      case 75: return launch_split2_t<T, 4, 5, 4, 3, 1>(p, s, ev, parts);
+      case 84: return launch_split2_t<T, 4, 4, 2, 4, 2>(p, s, ev, parts);
+      case 94: return launch_split2_t<T, 4, 4, 4, 3, 2>(p, s, ev, parts);
     }
     return cudaErrorInvalidValue;
   }

@@ -358,6 +358,71 @@ def cased_well(grid: Grid, *, z_top: float, ramp: float = 0.0, top_frac: float =
     return Medium(grid=grid, cell_id=cell_id, rho=rho, vp=vp, vs=vs)
 
 
+# casing steel with the shear speed the paper quotes for its casings (Sec. 6)
+PAPER_STEEL = (7850.0, 5900.0, 3220.0)
+
+
+def realistic_well(grid: Grid, *, z0: float = 0.0, H_target: float = 202.0, ID_prev: float = 0.22916,
+                   H_toc: float = 200.0, H_spacer: float = 200.0, L_joint: float = 12.0, L_collar: float = 0.184,
+                   OD_target: float = 0.1778, OD_collar: float = 0.1945, t_target: float = 0.00919,
+                   t_prev: float = 0.01105, fluid=FLUID, steel=PAPER_STEEL, cement=CEMENT,
+                   rock=ROCK) -> Medium:
+    """The paper's realistic cased well (Sec. 6) from its printed dimensions:
+    an interior (target) casing of outer diameter OD_target down to depth
+    H_target, built of joints L_joint long whose collars (L_collar long,
+    outer diameter OD_collar) sit at every joint boundary, inside an exterior
+    (previous) casing of inner diameter ID_prev; the annulus between them
+    holds the spacer (drilling fluid) down to H_spacer and cement from H_toc
+    down (the cement top).  The figure with the rest of the geometry is
+    missing, so these are readings: the wall thicknesses t_target and t_prev
+    (not printed), the collars centred on the joint boundaries n L_joint, the
+    spacer a drilling fluid (the paper's annulus liquid has zero shear
+    speed), rock outside the exterior casing, and liquid inside the interior
+    casing (also below its shoe).  Depth is measured down from the top of
+    the well; grid z = 0 (its first interior cell) sits at depth z0, so a
+    grid can hold a section of the well.  A cell's material is decided by
+    its centre."""
+    nth, NR, NZ = grid.shape
+    r = grid.r_centre()[:, None]
+    depth = z0 + grid.z_centre()[None, :]
+    r_tin, r_tout, r_col = OD_target / 2 - t_target, OD_target / 2, OD_collar / 2
+    r_pin, r_pout = ID_prev / 2, ID_prev / 2 + t_prev
+    in_target = depth < H_target
+    n = np.round(depth / L_joint)
+    collar = in_target & (n >= 1) & (np.abs(depth - n * L_joint) < L_collar / 2)
+    reg = _Registry()
+    F, S, C, R = reg.id(fluid), reg.id(steel), reg.id(cement), reg.id(rock)
+    id2 = np.full((NR, NZ), F, dtype=np.uint16)
+    annulus = (r >= r_tout) & (r < r_pin)
+    id2 = np.where(annulus & (depth >= H_toc), C, id2)
+    id2 = np.where(annulus & (depth < H_spacer), F, id2)
+    id2 = np.where((r >= r_tin) & (r < r_tout) & in_target, S, id2)
+    id2 = np.where((r >= r_tout) & (r < r_col) & collar, S, id2)
+    id2 = np.where((r >= r_pin) & (r < r_pout), S, id2)
+    id2 = np.where(r >= r_pout, R, id2).astype(np.uint16)
+    rho, vp, vs = reg.arrays()
+    return Medium(grid=grid, cell_id=np.broadcast_to(id2, (nth, NR, NZ)).copy(), rho=rho, vp=vp, vs=vs)
+
+
+def realistic_well_section(z0: float = 100.0, length: float = 20.0, *, nth: int = 8, nr: int = 64, pml_r: int = 16,
+                           pml_z: int = 16, dr: float = 0.0025, dz: float = 0.0025, f0: float = 8e3,
+                           source_depth: Optional[float] = None, steps: int = 1000) -> Scenario:
+    """A section [z0, z0 + length) of the realistic well with the paper's
+    torsion source (Sec. 6): a ring one cell inside the outer wall of the
+    casing that carries the collars (the target casing, liquid on both
+    sides) at source_depth (default 5 m into the section), and pressure
+    receivers on the axis at a quarter and three quarters of the section (a
+    torsion field has no pressure: they record zeros)."""
+    g = Grid(nr=nr, nth=nth, nz=int(round(length / dz)), pml_r=pml_r, pml_z=pml_z, dr=dr, dz=dz)
+    med = realistic_well(g, z0=z0)
+    r_src = 0.1778 / 2 - dr
+    zs = (source_depth if source_depth is not None else z0 + 5.0) - z0
+    return Scenario(name=f"realistic well {z0:g}-{z0 + length:g} m", medium=med,
+                    source=Source(kind=SOURCE_TORSION, r=r_src, theta=0.0, z=zs, f0=f0),
+                    receivers=on_axis_receivers(np.array([0.25, 0.75]) * length), cfl=0.5, steps=steps,
+                    params={"z_origin": z0})
+
+
 def homogeneous(grid: Grid, mat=FLUID) -> Medium:
     return Medium(grid=grid, cell_id=np.zeros(grid.shape, dtype=np.uint16),
                   rho=np.array([mat[0]]), vp=np.array([mat[1]]), vs=np.array([mat[2]]))

@@ -144,3 +144,37 @@ def test_small_cement_case_draws_and_geometry():
         assert 0.9 * W.CEMENT[2] <= x[4] <= 1.1 * W.CEMENT[2] and 0.9 * W.ROCK[2] <= x[5] <= 1.1 * W.ROCK[2]
         assert sc.source.z == pytest.approx(x[0] - 0.075)
         assert np.all(sc.medium.vs[sc.medium.cell_id[:, 0, :]] == 0)
+
+
+def test_realistic_well_matches_the_printed_dimensions():
+    """The paper's realistic well (Sec. 6) at the printed dimensions: interior
+    casing OD 0.1778 m to 202 m, collars OD 0.1945 m, 0.184 m long at every
+    12 m joint boundary, exterior casing ID 0.22916 m, spacer (liquid) above
+    200 m and cement below in the annulus, casing Vs 3220 m/s."""
+    g = W.Grid(nr=64, nth=4, nz=2000, pml_r=4, pml_z=4, dr=0.0025, dz=0.0025)
+    med = W.realistic_well(g, z0=11.0)  # depths 11 .. 16 m: the collar at 12 m
+    vs = med.vs[med.cell_id[0]]  # [NR][NZ]
+    rc = g.r_centre()
+    depth = 11.0 + g.z_centre()
+
+    def col(d):
+        return vs[:, int(np.argmin(np.abs(depth - d)))]
+
+    plain, collar = col(13.0), col(12.0)
+    steel = np.flatnonzero(plain == 3220.0)
+    inner = steel[rc[steel] < 0.1]
+    outer = steel[rc[steel] > 0.1]
+    assert rc[inner[0]] >= 0.1778 / 2 - 0.00919 - 1e-12 and rc[inner[-1]] < 0.1778 / 2
+    assert rc[outer[0]] >= 0.22916 / 2 and rc[outer[-1]] < 0.22916 / 2 + 0.01105
+    assert np.all(plain[rc < 0.1778 / 2 - 0.00919] == 0)  # liquid inside
+    assert np.all(plain[(rc >= 0.1778 / 2) & (rc < 0.22916 / 2)] == 0)  # spacer
+    on_collar = (rc >= 0.1778 / 2) & (rc < 0.1945 / 2)
+    assert np.all(collar[on_collar] == 3220.0) and np.all(plain[on_collar] == 0)
+    at = np.flatnonzero(vs[on_collar.nonzero()[0][0]] == 3220.0)
+    assert abs(depth[at].mean() - 12.0) < g.dz and abs(len(at) * g.dz - 0.184) <= g.dz
+    deep = W.realistic_well(g, z0=199.0)
+    dv = deep.vs[deep.cell_id[0]]
+    ann = (rc >= 0.1778 / 2 + 0.01) & (rc < 0.22916 / 2)  # away from collars
+    ddepth = 199.0 + g.z_centre()
+    assert np.all(dv[ann][:, ddepth < 200.0] == 0) and np.all(dv[ann][:, ddepth >= 200.0] > 0)
+    assert np.all(med.vs[med.cell_id[:, 0, :]] == 0)  # ring 0 liquid
