@@ -193,8 +193,9 @@ size_t sim_device_bytes(const sim_t *h);
  * on the rest; interior four cells per thread, b = 4, 5, with edge c = 0 (four
  * cells, 4 blocks/SM), 2 (two, 4), 3 (two, 6), 4 (four, 3); interior two
  * cells, b = 6, 8, with edge c = 1 (two, 6) or 5 (two, 4); c = 6, 7 as 2, 4
- * with a persistent interior kernel prefetching its next tile into L2, and
- * c = 8, 9 (b = 4) prefetching two tiles ahead);
+ * with a persistent interior kernel prefetching its next tile into L2; c = 8
+ * as 4 and c = 9 as 6, each with the edge tiles walked by a persistent
+ * prefetching kernel);
  * v * 10000 + s (a pair code) for the velocity kernel of split code v with the
  * stress kernel of split code s.  opts.tile accepts every code listed here. */
 int sim_config(const sim_t *h, int *kernel, int *tile_rows);

@@ -246,8 +246,10 @@ size_t march_smem_bytes(int storage, int code);
 // 4 blocks per SM; c = 2: two cells, 4 blocks; c = 3: two cells, 6 blocks;
 // c = 4: four cells, 3 blocks; c = 5: two cells in both (interior b = 6 or 8,
 // edge for 4 blocks per SM); c = 6 / 7: as c = 2 / 4 with a persistent
-// interior kernel that prefetches its next tile into L2; c = 8 / 9: the same
-// prefetching two tiles ahead (b = 4).  A pair code
+// interior kernel that prefetches its next tile into L2; c = 8: plain
+// interior, edge (four cells, 3 blocks) walked by a persistent prefetching
+// kernel; c = 9: prefetching interior and prefetching edge (two cells, 4
+// blocks).  A pair code
 // v * 10000 + s runs the velocity kernel of split code v and the stress kernel
 // of split code s (the autotuner times the two apart).
 constexpr int SPLIT_CODE = 2000;

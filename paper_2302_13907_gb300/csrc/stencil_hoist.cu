@@ -622,12 +622,11 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_interior(const KParams
   else str_hoist_body<T, NV, true>(p, j, i, k0);
 }
 
-// Persistent interior kernel with an L2 prefetch of the tile DIST steps
-// ahead: one wave of resident blocks walks the interior tiles in the order
-// above (theta fastest); before computing its tile a block asks L2 for every
-// row that later tile will load (one prefetch per 128-byte line), so its
-// loads find their lines in L2.  No register or shared memory holds the
-// prefetched data.
+// Persistent interior kernel with an L2 prefetch of its next tile: one wave
+// of resident blocks walks the interior tiles in the order above (theta
+// fastest); before computing its tile a block asks L2 for every row its next
+// tile will load (one prefetch per 128-byte line), so those loads find their
+// lines in L2.  No register or shared memory holds the prefetched data.
 __device__ __forceinline__ void prefetch_l2(const void *a) { asm volatile("prefetch.global.L2 [%0];" ::"l"(a)); }
 
 template <typename T, int NV, bool VEL>
@@ -666,7 +665,7 @@ __device__ __forceinline__ void prefetch_tile(const KParams &p, int j, int i, in
   }
 }
 
-template <typename T, int NV, int MINB, bool VEL, int DIST>
+template <typename T, int NV, int MINB, bool VEL>
 __global__ void __launch_bounds__(HB_X *HB_Y, MINB)
     hoist_interior_pf(const KParams p, int zt_lo, int nrt_in, int ntiles) {
   auto cell = [&](int t, int &j, int &i, int &k0) {
@@ -677,14 +676,8 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB)
   };
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int j, i, k0;
-    if (t == (int)blockIdx.x)  // the first DIST - 1 tiles ahead, then one per iteration
-      for (int d = 1; d < DIST; d++)
-        if (t + d * (int)gridDim.x < ntiles) {
-          cell(t + d * gridDim.x, j, i, k0);
-          prefetch_tile<T, NV, VEL>(p, j, i, k0);
-        }
-    if (t + DIST * (int)gridDim.x < ntiles) {
-      cell(t + DIST * gridDim.x, j, i, k0);
+    if (t + (int)gridDim.x < ntiles) {
+      cell(t + gridDim.x, j, i, k0);
       prefetch_tile<T, NV, VEL>(p, j, i, k0);
     }
     cell(t, j, i, k0);
@@ -722,6 +715,37 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_edge(const KParams p, 
   if (i < p.NR && k0 < p.NZ) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
 }
 
+// the same edge tiles walked by one wave of resident blocks, each prefetching
+// its next tile's rows into L2 (radial-PML memory variables included); only
+// cells inside the grid are prefetched
+template <typename T, int NV, int MINB, bool VEL>
+__global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_edge_pf(const KParams p, Split2 q, int ntiles) {
+  auto cell = [&](int t, int &j, int &i, int &k0) {
+    int rt, zt;
+    j = t % p.nth;
+    edge_tile(q, t / p.nth, rt, zt);
+    i = rt * HB_Y + threadIdx.y;
+    k0 = (zt * HB_X + threadIdx.x) * NV;
+  };
+  constexpr int LANES = 128 / (NV * 4);
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int j, i, k0;
+    if (t + (int)gridDim.x < ntiles) {
+      cell(t + gridDim.x, j, i, k0);
+      if (i < p.NR && k0 < p.NZ) {
+        prefetch_tile<T, NV, VEL>(p, j, i, k0);
+        if (i >= p.nr && (threadIdx.x & (LANES - 1)) == 0) {
+          const long long cr = ((long long)j * p.pml_r + (i - p.nr)) * p.NZp + k0;
+          const int q0 = VEL ? R_VR : R_ERR, q1 = VEL ? Q_VR : Q_EPP;
+          for (int u = 0; u < 3; u++) prefetch_l2(p.psr[q0 + u] + cr), prefetch_l2(p.psr[q1 + u] + cr);
+        }
+      }
+    }
+    cell(t, j, i, k0);
+    if (i < p.NR && k0 < p.NZ) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
+  }
+}
+
 // Batched scenarios: each half step is two persistent launches over the work
 // lists of up to BATCH_MAX cases, one over every case's interior tiles (lean
 // body only) and one over their edge tiles (radial-PML rows and z ends,
@@ -750,10 +774,14 @@ struct BatchCfg;
 template <>
 struct BatchCfg<true> {
   static constexpr int MINB_IN = 5, NVE = 4, MINB_E = 3;
+  static constexpr bool PF = false;
 };
 template <>
 struct BatchCfg<false> {
   static constexpr int MINB_IN = 4, NVE = 2, MINB_E = 4;
+  // an L2 prefetch of the next item, which pays off in the one-wave interior
+  // kernel, is slower here: the tuned grid is several waves deep
+  static constexpr bool PF = false;
 };
 
 __device__ __forceinline__ int batch_case(const BatchParams &bp, long long item) {
@@ -770,15 +798,23 @@ template <typename T, bool VEL>
 __global__ void __launch_bounds__(HB_X *HB_Y, BatchCfg<VEL>::MINB_IN)
     batch_interior(const __grid_constant__ BatchParams bp) {
   const long long total = bp.start[bp.n];
-  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-    const int c = batch_case(bp, item);
-    const KParams &p = bp.cases[c];
+  auto cell = [&](long long item, int &c, int &j, int &i, int &k0) {
+    c = batch_case(bp, item);
     const Split2 &q = bp.q[c];
     int t = (int)(item - bp.start[c]);
-    const int j = t % p.nth;
-    t /= p.nth;
-    const int i = (t % q.nrt_in) * HB_Y + threadIdx.y;
-    const int k0 = ((q.zt_lo + t / q.nrt_in) * HB_X + threadIdx.x) * BATCH_NV;
+    j = t % bp.cases[c].nth;
+    t /= bp.cases[c].nth;
+    i = (t % q.nrt_in) * HB_Y + threadIdx.y;
+    k0 = ((q.zt_lo + t / q.nrt_in) * HB_X + threadIdx.x) * BATCH_NV;
+  };
+  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    int c, j, i, k0;
+    if (BatchCfg<VEL>::PF && item + gridDim.x < total) {
+      cell(item + gridDim.x, c, j, i, k0);
+      prefetch_tile<T, BATCH_NV, VEL>(bp.cases[c], j, i, k0);
+    }
+    cell(item, c, j, i, k0);
+    const KParams &p = bp.cases[c];
     if (i < p.i_lo || i >= p.i_hi) continue;
     if (VEL) vel_hoist_body<T, BATCH_NV, true>(p, j, i, k0);
     else str_hoist_body<T, BATCH_NV, true>(p, j, i, k0);
@@ -840,39 +876,47 @@ int sm_count() {
   return n;
 }
 
-template <typename T, int NV, int MINB_IN, int NVE, int MINB_E, bool VEL, int PF>
+template <typename T, int NV, int MINB_IN, int NVE, int MINB_E, bool VEL, bool PF, bool PFE>
 cudaError_t launch_split2_half(const KParams &p, const Split2 &q, cudaStream_t s) {
   dim3 blk(HB_X, HB_Y);
   const int nin = q.zt_hi - q.zt_lo;
   if (q.nrt_in > 0 && nin > 0) {
-    if constexpr (PF > 0) {  // one wave of resident blocks, prefetch distance PF
+    if constexpr (PF) {  // one wave of resident blocks
       const long long tiles = (long long)p.nth * q.nrt_in * nin;
       if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
       const int grid = (int)std::min<long long>(tiles, (long long)sm_count() * MINB_IN);
-      hoist_interior_pf<T, NV, MINB_IN, VEL, (PF > 0 ? PF : 1)><<<grid, blk, 0, s>>>(p, q.zt_lo, q.nrt_in, (int)tiles);
+      hoist_interior_pf<T, NV, MINB_IN, VEL><<<grid, blk, 0, s>>>(p, q.zt_lo, q.nrt_in, (int)tiles);
     } else {
       hoist_interior<T, NV, MINB_IN, VEL><<<dim3(p.nth, q.nrt_in, nin), blk, 0, s>>>(p, q.zt_lo);
     }
   }
   const long long nedge = (long long)(q.nrt - q.nrt_in) * q.enzt + (long long)q.nrt_in * (q.ez_lo + q.enzt - q.ez_hi);
   if (nedge > 65535 || p.nth > 65535) return cudaErrorInvalidValue;
-  if (nedge > 0) hoist_edge<T, NVE, MINB_E, VEL><<<dim3(p.nth, (unsigned)nedge), blk, 0, s>>>(p, q);
+  if (nedge > 0) {
+    if constexpr (PFE) {
+      const long long tiles = (long long)p.nth * nedge;
+      const int grid = (int)std::min<long long>(tiles, (long long)sm_count() * MINB_E);
+      hoist_edge_pf<T, NVE, MINB_E, VEL><<<grid, blk, 0, s>>>(p, q, (int)tiles);
+    } else {
+      hoist_edge<T, NVE, MINB_E, VEL><<<dim3(p.nth, (unsigned)nedge), blk, 0, s>>>(p, q);
+    }
+  }
   return cudaGetLastError();
 }
 
-template <typename T, int NV, int MINB_IN, int NVE, int MINB_E, int PF = 0>
+template <typename T, int NV, int MINB_IN, int NVE, int MINB_E, bool PF = false, bool PFE = false>
 cudaError_t launch_split2_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
   const Split2 q = split2<NV, NVE>(p);
   if (q.zt_hi - q.zt_lo > 65535) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   if (parts & 1) {
     if (ev) cudaEventRecord(ev[0], s);
-    e = launch_split2_half<T, NV, MINB_IN, NVE, MINB_E, true, PF>(p, q, s);
+    e = launch_split2_half<T, NV, MINB_IN, NVE, MINB_E, true, PF, PFE>(p, q, s);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
   }
   if (parts & 2) {
-    e = launch_split2_half<T, NV, MINB_IN, NVE, MINB_E, false, PF>(p, q, s);
+    e = launch_split2_half<T, NV, MINB_IN, NVE, MINB_E, false, PF, PFE>(p, q, s);
     if (ev) cudaEventRecord(ev[2], s);
   }
   return e;
@@ -913,12 +957,14 @@ cudaError_t launch_hoist_st(int nv, int minb, bool zf, bool split, int edge, con
       case 45: return launch_split2_t<T, 4, 5, 4, 3>(p, s, ev, parts);
       case 56: return launch_split2_t<T, 2, 6, 2, 4>(p, s, ev, parts);
       case 58: return launch_split2_t<T, 2, 8, 2, 4>(p, s, ev, parts);
-      case 64: return launch_split2_t<T, 4, 4, 2, 4, 1>(p, s, ev, parts);
-      case 65: return launch_split2_t<T, 4, 5, 2, 4, 1>(p, s, ev, parts);
-      case 74: return launch_split2_t<T, 4, 4, 4, 3, 1>(p, s, ev, parts);
-      case 75: return launch_split2_t<T, 4, 5, 4, 3, 1>(p, s, ev, parts);
-      case 84: return launch_split2_t<T, 4, 4, 2, 4, 2>(p, s, ev, parts);
-      case 94: return launch_split2_t<T, 4, 4, 4, 3, 2>(p, s, ev, parts);
+      case 64: return launch_split2_t<T, 4, 4, 2, 4, true>(p, s, ev, parts);
+      case 65: return launch_split2_t<T, 4, 5, 2, 4, true>(p, s, ev, parts);
+      case 74: return launch_split2_t<T, 4, 4, 4, 3, true>(p, s, ev, parts);
+      case 75: return launch_split2_t<T, 4, 5, 4, 3, true>(p, s, ev, parts);
+      case 84: return launch_split2_t<T, 4, 4, 4, 3, false, true>(p, s, ev, parts);
+      case 85: return launch_split2_t<T, 4, 5, 4, 3, false, true>(p, s, ev, parts);
+      case 94: return launch_split2_t<T, 4, 4, 2, 4, true, true>(p, s, ev, parts);
+      case 95: return launch_split2_t<T, 4, 5, 2, 4, true, true>(p, s, ev, parts);
     }
     return cudaErrorInvalidValue;
   }
