@@ -35,6 +35,32 @@ METRIC = "Gcell-updates/s"
 L2_BYTES = 129 * 2 ** 20
 
 
+def shard(n, rank, ws):
+    """Units (cases) rank `rank` of `ws` takes: round robin, so every rank's
+    share has the same mix of sizes.  No data-path collective is needed."""
+    return list(range(rank, n, ws))
+
+
+def max_over_ranks(x, pg, device="cuda"):
+    """The largest x over all ranks (the whole job's time); x without a group."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, pg, device="cuda"):
+    """The sum of x over all ranks (the whole job's units); x without a group."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -188,17 +214,20 @@ def cpu_sample(sc, seconds=15.0, nz=128):
                        f"({cells} cells), {n} steps, {t1 - t0:.1f} s"), (cells, o)
 
 
-def bench_batch(stream, n_cases=64, steps=60, warm=8):
+def bench_batch(stream, n_cases=64, steps=60, warm=8, rank=0, ws=1, pg=None):
     """Batched scenarios (the 64 cement-hardening cases, uneven Nz) in one
     persistent launch per kernel per step, against the same cases run one
     after another with the single-well path.  Throughput is reported in full
-    6000-step scenarios per second, measured over `steps` steps."""
+    6000-step scenarios per second, measured over `steps` steps.  Under
+    torchrun the cases are sharded round robin over the ranks (weak in
+    cases per rank, no collective on the data path); times are the max over
+    ranks."""
     import torch
     from paper_2302_13907_gb300 import workloads as W
     from paper_2302_13907_gb300.binding import BatchSimulation, Simulation
 
-    cases = [W.scenario_case(s) for s in range(1, n_cases + 1)]
-    cells = sum(c.grid.cells for c in cases)
+    cases = [W.scenario_case(s + 1) for s in shard(n_cases, rank, ws)]
+    cells = sum_over_ranks(sum(c.grid.cells for c in cases), pg)
     full = cases[0].steps
     b = BatchSimulation(cases, graph_chunk=steps // 2, stream=stream.cuda_stream, max_steps=steps + warm)
     _, items, grid = b.config()
@@ -224,23 +253,26 @@ def bench_batch(stream, n_cases=64, steps=60, warm=8):
         torch.cuda.synchronize()
         tp += e0.elapsed_time(e1) / 1e3
         s.close()
+    tb, tp = max_over_ranks(tb, pg), max_over_ranks(tp, pg)
     return {"metric": "scenarios/s", "value": n_cases * steps / full / tb, "plain": n_cases * steps / full / tp,
             "speedup_vs_plain": tp / tb, "gcell_updates_per_s": cells * steps / tb / 1e9,
             "plain_gcell_updates_per_s": cells * steps / tp / 1e9, "cases": n_cases, "cells": cells,
             "steps_timed": steps, "steps_per_scenario": full, "work_items": items, "persistent_blocks": grid,
             "error": "each batched case equals its single run (rel-L2 <= 1e-6, tested); FP32 vs FP64 oracle <= 1e-4",
-            "workload": "64 cement-hardening cases: 136 x 32 x Nz, Nz in {2080, 3104, 4128, 6176} with PML, FP32"}
+            "workload": "64 cement-hardening cases: 136 x 32 x Nz, Nz in {2080, 3104, 4128, 6176} with PML, FP32",
+            "sharding": f"cases round robin over {ws} rank(s)"}
 
 
-def bench_batch_small(stream, n_cases=64, steps=400, warm=8):
+def bench_batch_small(stream, n_cases=64, steps=400, warm=8, rank=0, ws=1, pg=None):
     """The batching machinery on small wells, where one case cannot fill the
     GPU: 64 miniature cement cases (44 x 8 x 256 cells each) batched against
-    the same cases run one after another; full 1200-step scenarios per second."""
+    the same cases run one after another; full 1200-step scenarios per second
+    (cases sharded over the ranks as bench_batch)."""
     import torch
     from paper_2302_13907_gb300 import workloads as W
     from paper_2302_13907_gb300.binding import BatchSimulation, Simulation
 
-    cases = [W.small_cement_case(s) for s in range(n_cases)]
+    cases = [W.small_cement_case(s) for s in shard(n_cases, rank, ws)]
     full = cases[0].steps
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with BatchSimulation(cases, graph_chunk=steps // 2, stream=stream.cuda_stream, max_steps=steps + warm) as b:
@@ -261,6 +293,7 @@ def bench_batch_small(stream, n_cases=64, steps=400, warm=8):
             e1.record(stream)
             torch.cuda.synchronize()
             tp += e0.elapsed_time(e1) / 1e3
+    tb, tp = max_over_ranks(tb, pg), max_over_ranks(tp, pg)
     return {"metric": "scenarios/s", "value": n_cases * steps / full / tb, "plain": n_cases * steps / full / tp,
             "speedup_vs_plain": tp / tb, "cases": n_cases, "steps_timed": steps, "steps_per_scenario": full,
             "workload": "64 miniature cement cases: 44 x 8 x 256 cells with PML, FP32"}
@@ -416,10 +449,7 @@ def main():
     uniform_dt = sim.dt
     sim.close()
     del sim
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, pg)
     value = ws * cells * T * K / (ms / 1e3) / 1e9
 
     # ---------------- roofline: per-kernel CUDA events on the launching stream
@@ -477,10 +507,7 @@ def main():
         s2.close()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([wall], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            wall = float(t.item())
+        wall = max_over_ranks(wall, pg)
         h2d = sc.medium.cell_id.nbytes + sc.medium.rho.nbytes * 4
         e2e = {"value": ws * cells * T * K / wall / 1e9, "unit": METRIC, "h2d_bytes_per_step": h2d / K,
                "d2h_bytes_per_step": tr.nbytes / K,
@@ -488,8 +515,8 @@ def main():
 
     batch = None
     if not args.no_batch:
-        batch = bench_batch(stream)
-        batch["small_cases"] = bench_batch_small(stream)
+        batch = bench_batch(stream, rank=rank, ws=ws, pg=pg)
+        batch["small_cases"] = bench_batch_small(stream, rank=rank, ws=ws, pg=pg)
     refined = None
     if not args.no_refined and args.storage == "f32" and args.nz == 8192:
         refined = bench_refined(stream, sc, value / ws, uniform_dt)

@@ -275,15 +275,6 @@ cudaError_t gemm_tcgen05(bool ta, bool tb, int M, int N, int K, const __nv_bfloa
                          const __nv_bfloat16 *B, int ldb, float *C, int ldc, float alpha, float beta,
                          cudaStream_t s);
 cudaError_t gemm_tcgen05_status(int *out, cudaStream_t s);
-// batched marching kernels: one well's descriptors, parameters and status word
-struct MarchCase {
-  FusedMaps maps;
-  KParams k;
-  int *status;
-};
-long long march_items(int code, int nth, int NR, int NZ);
-cudaError_t launch_march_batch(int storage, int code, bool vel, const MarchCase *cases, const long long *start,
-                               int n_cases, long long total, cudaStream_t s);
 int march_box_x(int storage);
 int march_box_id();
 }  // namespace cwell

@@ -492,40 +492,6 @@ __global__ void __launch_bounds__(MSmem<T, RT, VEL>::NT) march_step(const __grid
   march_block<T, RT, VEL>(maps, p, nj, status, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// many wells in one launch: block b takes work item b, item = (case, theta
-// run, r tile, z tile), theta run fastest; start[c] = first item of case c
-// (start[n] = total).  The block copies its case's parameters to shared
-// memory; the case's TMA descriptors stay in global memory.
-__device__ __forceinline__ int case_of(const long long *start, int n, long long item) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(start + mid) <= item) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-template <typename T, int RT, bool VEL>
-__global__ void __launch_bounds__(MSmem<T, RT, VEL>::NT) march_batch(const MarchCase *cases, const long long *start,
-                                                                      int n_cases, int nj) {
-  __shared__ __align__(16) KParams sp;
-  const long long item = blockIdx.x;
-  const int c = case_of(start, n_cases, item);
-  {
-    static_assert(sizeof(KParams) % 8 == 0, "KParams is copied as 8-byte words");
-    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&cases[c].k);
-    for (int w = threadIdx.x; w < (int)(sizeof(KParams) / 8); w += blockDim.x)
-      reinterpret_cast<unsigned long long *>(&sp)[w] = __ldg(src + w);
-  }
-  __syncthreads();
-  long long q = item - __ldg(start + c);
-  const int nseg = (sp.nth + nj - 1) / nj, nrt = (sp.NR + RT - 1) / RT;
-  const int seg = (int)(q % nseg);
-  q /= nseg;
-  march_block<T, RT, VEL>(cases[c].maps, sp, nj, cases[c].status, seg, (int)(q % nrt), (int)(q / nrt));
-}
-
 template <typename T, int RT, bool VEL>
 cudaError_t launch_march_t(const FusedMaps &maps, const KParams &p, int nj, int *status, cudaStream_t s) {
   using SM = MSmem<T, RT, VEL>;
@@ -583,66 +549,7 @@ size_t march_bytes_t(int rt) {
   return 0;
 }
 
-template <typename T, int RT>
-cudaError_t launch_batch_t(bool vel, const MarchCase *cases, const long long *start, int n, long long total, int nj,
-                           cudaStream_t s) {
-  static bool attr_done[16][2] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
-  if (total < 1 || total > 0x7fffffffLL) return cudaErrorInvalidValue;
-  if (vel) {
-    using SM = MSmem<T, RT, true>;
-    if (!attr_done[dev][1]) {
-      cudaError_t e = cudaFuncSetAttribute(march_batch<T, RT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)SM::BYTES);
-      if (e != cudaSuccess) return e;
-      attr_done[dev][1] = true;
-    }
-    march_batch<T, RT, true><<<(unsigned)total, SM::NT, SM::BYTES, s>>>(cases, start, n, nj);
-  } else {
-    using SM = MSmem<T, RT, false>;
-    if (!attr_done[dev][0]) {
-      cudaError_t e = cudaFuncSetAttribute(march_batch<T, RT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)SM::BYTES);
-      if (e != cudaSuccess) return e;
-      attr_done[dev][0] = true;
-    }
-    march_batch<T, RT, false><<<(unsigned)total, SM::NT, SM::BYTES, s>>>(cases, start, n, nj);
-  }
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_batch_st(int rt, bool vel, const MarchCase *cases, const long long *start, int n, long long total,
-                            int nj, cudaStream_t s) {
-  switch (rt) {
-    case 2: return launch_batch_t<T, 2>(vel, cases, start, n, total, nj, s);
-    case 4: return launch_batch_t<T, 4>(vel, cases, start, n, total, nj, s);
-    case 8: return launch_batch_t<T, 8>(vel, cases, start, n, total, nj, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
 }  // namespace
-
-long long march_items(int code, int nth, int NR, int NZ) {
-  const int rt = march_rows(code), nj = march_planes(code);
-  if (rt < 1 || nj < 1) return 0;
-  return (long long)((nth + nj - 1) / nj) * ((NR + rt - 1) / rt) * ((NZ + MZT - 1) / MZT);
-}
-
-cudaError_t launch_march_batch(int storage, int code, bool vel, const MarchCase *cases, const long long *start,
-                               int n_cases, long long total, cudaStream_t s) {
-  const int rt = march_rows(code), nj = march_planes(code);
-  if (nj < 1) return cudaErrorInvalidValue;
-  switch (storage) {
-    case 0: return launch_batch_st<float>(rt, vel, cases, start, n_cases, total, nj, s);
-    case 1: return launch_batch_st<__nv_bfloat16>(rt, vel, cases, start, n_cases, total, nj, s);
-    case 2: return launch_batch_st<__half>(rt, vel, cases, start, n_cases, total, nj, s);
-  }
-  return cudaErrorInvalidValue;
-}
 
 cudaError_t launch_march(int storage, int code, const FusedMaps &maps, const KParams &p, int *status, cudaStream_t s,
                          cudaEvent_t *ev, int parts) {
