@@ -5,11 +5,11 @@
 // with one ghost row below (m > 0: the coarser zone's last row at this zone's
 // nodes) and one above (m < M-1: the finer zone's first row at this zone's
 // nodes).  A step is
-//   velocity half of every zone (the batched load-first kernels, zones as
-//   cases, ghost rows excluded) -> point force -> ghost rows of the
-//   velocities -> stress half of every zone (volumetric source inside) ->
-//   ghost rows of the stresses -> receivers (one block per zone, which also
-//   advances the zone's step counter).
+//   velocity half of every zone (the single well's interior / edge split
+//   launches, zone by zone, ghost rows excluded) -> point force -> ghost rows
+//   of the velocities -> stress half of every zone (volumetric source
+//   inside) -> ghost rows of the stresses -> receivers (one block per zone,
+//   which also advances the zone's step counter).
 // Ghost rows: coarse -> fine by the trigonometric interpolant (the paper's
 // FFT zero-padding, here as its matrix: the periodic Dirichlet kernel with
 // the Nyquist term halved), fine -> coarse by its adjoint
@@ -53,7 +53,7 @@ struct simr_s {
   sim_grid_t grid{};
   int NR = 0, NZ = 0, NZp = 0, M = 0;
   double dt = 0;
-  int n_rec = 0, cap = 0, steps_done = 0, graph_chunk = 64, grid_blocks = 0, src_kind = 0;
+  int n_rec = 0, cap = 0, steps_done = 0, graph_chunk = 64, src_kind = 0;
   std::vector<RZone> z;
   std::vector<int> trace_row;  // device trace row of each receiver
   std::vector<KParams> kps;
@@ -118,14 +118,21 @@ double dirichlet(int N, double t) {
 
 bool pow2_in(int n) { return n == 4 || n == 8 || n == 16 || n == 32 || n == 64; }
 
+// split codes each zone's halves run with: the single-well tuner's pair on the
+// 20 m well (plain interior + prefetching edge for the velocities, prefetching
+// interior and edge for the stresses)
+constexpr int REFINED_VEL_CODE = 2285, REFINED_STR_CODE = 2294;
+
 cudaError_t enqueue_refined_step(simr_t *h) {
-  const int M = (int)h->z.size();
-  cudaError_t e = launch_batch_split(0, true, h->kps.data(), M, h->grid_blocks, h->stream);
+  cudaError_t e = cudaSuccess;
+  for (size_t m = 0; m < h->kps.size() && e == cudaSuccess; m++)
+    e = launch_hoist(0, REFINED_VEL_CODE, h->kps[m], h->stream, nullptr, 1);
   if (e == cudaSuccess && h->src_kind == 1) e = launch_inject(0, h->ip, h->stream);
   if (e == cudaSuccess) e = launch_xfer(h->xv, h->stream);
-  if (e == cudaSuccess) e = launch_batch_split(0, false, h->kps.data(), M, h->grid_blocks, h->stream);
+  for (size_t m = 0; m < h->kps.size() && e == cudaSuccess; m++)
+    e = launch_hoist(0, REFINED_STR_CODE, h->kps[m], h->stream, nullptr, 2);
   if (e == cudaSuccess) e = launch_xfer(h->xs, h->stream);
-  if (e == cudaSuccess) e = launch_batch_receivers(0, h->d_rp, M, h->stream);
+  if (e == cudaSuccess) e = launch_batch_receivers(0, h->d_rp, (int)h->kps.size(), h->stream);
   return e;
 }
 
@@ -543,38 +550,6 @@ extern "C" int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, co
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return bail(rcuda(h, e, "upload"));
 
-  // --- persistent grid of the batched launches: time a few on the zero state (sources off)
-  {
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    std::vector<KParams> dry = h->kps;
-    for (auto &p : dry) p.src_i = -1;
-    cudaEvent_t t0, t1;
-    cudaEventCreate(&t0);
-    cudaEventCreate(&t1);
-    float best = INFINITY;
-    int pick = sms * 12;
-    for (int mult : {6, 12, 24, 48}) {
-      const int gb = sms * mult;
-      e = launch_batch_split(0, true, dry.data(), M, gb, h->stream);
-      if (e == cudaSuccess) e = launch_batch_split(0, false, dry.data(), M, gb, h->stream);
-      cudaEventRecord(t0, h->stream);
-      for (int w = 0; w < 2 && e == cudaSuccess; w++) {
-        e = launch_batch_split(0, true, dry.data(), M, gb, h->stream);
-        if (e == cudaSuccess) e = launch_batch_split(0, false, dry.data(), M, gb, h->stream);
-      }
-      cudaEventRecord(t1, h->stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-      if (e != cudaSuccess) break;
-      float ms = 0;
-      cudaEventElapsedTime(&ms, t0, t1);
-      if (ms < best) best = ms, pick = gb;
-    }
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
-    if (e != cudaSuccess) return bail(rcuda(h, e, "refined grid autotune"));
-    h->grid_blocks = pick;
-  }
   *out = h;
   return SIM_OK;
 }

@@ -618,6 +618,7 @@ template <typename T, int NV, int MINB, bool VEL>
 __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_interior(const KParams p, int zt_lo) {
   const int j = blockIdx.x, i = blockIdx.y * HB_Y + threadIdx.y;
   const int k0 = ((zt_lo + blockIdx.z) * HB_X + threadIdx.x) * NV;
+  if (i < p.i_lo || i >= p.i_hi) return;
   if (VEL) vel_hoist_body<T, NV, true>(p, j, i, k0);
   else str_hoist_body<T, NV, true>(p, j, i, k0);
 }
@@ -681,6 +682,7 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB)
       prefetch_tile<T, NV, VEL>(p, j, i, k0);
     }
     cell(t, j, i, k0);
+    if (i < p.i_lo || i >= p.i_hi) continue;
     if (VEL) vel_hoist_body<T, NV, true>(p, j, i, k0);
     else str_hoist_body<T, NV, true>(p, j, i, k0);
   }
@@ -712,7 +714,7 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_edge(const KParams p, 
   int rt, zt;
   edge_tile(q, blockIdx.y, rt, zt);
   const int j = blockIdx.x, i = rt * HB_Y + threadIdx.y, k0 = (zt * HB_X + threadIdx.x) * NV;
-  if (i < p.NR && k0 < p.NZ) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
+  if (i >= p.i_lo && i < p.i_hi && k0 < p.NZ) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
 }
 
 // the same edge tiles walked by one wave of resident blocks, each prefetching
@@ -742,7 +744,7 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_edge_pf(const KParams 
       }
     }
     cell(t, j, i, k0);
-    if (i < p.NR && k0 < p.NZ) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
+    if (i >= p.i_lo && i < p.i_hi && k0 < p.NZ) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
   }
 }
 
@@ -755,8 +757,8 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_edge_pf(const KParams 
 // launch's items (start[c] = first item of case c, start[n] = total) travel in
 // the kernel's parameter space, so a block reads its case's geometry and
 // buffers from the constant bank.  The index inside a case is 32-bit (checked
-// on the host); rows outside [i_lo, i_hi) are left alone (the ghost rows of
-// an azimuthally refined grid's zones, which run as cases).  Cells per
+// on the host); rows outside [i_lo, i_hi) are left alone (as in every
+// split kernel: the ghost rows of an azimuthally refined grid's zones).  Cells per
 // thread and blocks per SM: the velocity half takes
 // interior (4, 5) and edge (4, 3), the stress half interior (4, 4) and edge
 // (2, 4), the split launches the tuner picks for the single well.
