@@ -179,3 +179,43 @@ def test_dipole_on_refined_grid_close_to_uniform():
     tu, tr = u.traces(), r.traces()
     for q in (1, 2):
         assert rel_l2(tr[q], tu[q]) < 0.08, (q, rel_l2(tr[q], tu[q]))
+
+
+def _dirichlet(n, t):
+    """Textbook periodic interpolation kernel of n (even) samples, Nyquist
+    term halved: (1/n) [1 + 2 sum_{m=1}^{n/2-1} cos(m t) + cos(n t / 2)]."""
+    m = np.arange(1, n // 2)
+    return (1.0 + 2.0 * np.cos(np.outer(t, m)).sum(axis=1) + np.cos(0.5 * n * t)) / n
+
+
+@pytest.mark.parametrize("na", [4, 8, 16, 32])
+def test_interpolation_matrix_is_the_closed_form_kernel(na):
+    """The oracle builds its coarse-to-fine matrix by running the three DFT
+    steps on unit vectors; it must equal the closed-form interpolation kernel
+    evaluated at the node offsets (integer nodes: (j' - 2j) h_B; half-integer
+    nodes: (j' - 2j - 1/2) h_B)."""
+    nb = 2 * na
+    hb = 2 * np.pi / nb
+    for half in (False, True):
+        got = np.stack([oracle.fft_interp(np.eye(na)[j], nb, half) for j in range(na)], axis=1)
+        jb, ja = np.meshgrid(np.arange(nb), np.arange(na), indexing="ij")
+        want = _dirichlet(na, ((jb - 2 * ja - (0.5 if half else 0.0)) * hb).ravel()).reshape(nb, na)
+        assert np.abs(got - want).max() < 1e-13, (na, half)
+
+
+def test_zoning_rule_halves_the_step_each_time_the_radius_doubles():
+    """workloads.refinement_rows: going inward from the outer radius, zone
+    boundaries where the radius halves, node counts halving down to 4."""
+    g = W.Grid(nr=180, nth=64, nz=8, pml_r=16, pml_z=2, dr=0.0025, dz=0.0025)
+    rows = W.refinement_rows(g)
+    assert rows == [12, 24, 49, 98]
+    edges = [0] + rows + [g.NR]
+    nths = [g.nth >> (len(rows) - m) for m in range(len(rows) + 1)]
+    assert nths == [4, 8, 16, 32, 64]
+    for m in range(1, len(rows)):
+        assert abs(edges[m + 1] / edges[m] - 2.0) < 0.1  # each zone spans one doubling of the radius
+    # every zone's azimuthal cell size at its outer edge is within 2x of the
+    # outer zone's at its inner edge (the purpose of the rule)
+    size = [(edges[m + 1] * g.dr) * 2 * np.pi / nths[m] for m in range(len(nths))]
+    assert max(size) / min(size) < 2.2
+    assert W.refinement_rows(W.Grid(nr=20, nth=8, nz=8, pml_r=4, pml_z=2, dr=0.003, dz=0.003)) == [12]
