@@ -151,12 +151,13 @@ def split_kernel_name(tile, vel):
 def launches_per_step(kind, tile):
     """Kernel launches of one leapfrog step (volumetric source): the fused
     kernel or the two halves, plus the receiver kernel; an interior / edge
-    split half (22xx) is two launches."""
+    split half (22xx) is two launches, a three-way split half (23xx) three."""
     if kind == 2:
         return 2
     if kind == 4:
         return 3
-    return 1 + sum(2 if split_half_code(tile, v) // 100 == 22 else 1 for v in (True, False))
+    per_half = {22: 2, 23: 3}  # interior + edge; interior + radial + ends
+    return 1 + sum(per_half.get(split_half_code(tile, v) // 100, 1) for v in (True, False))
 
 
 def kernel_label(kind, tile):

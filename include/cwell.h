@@ -195,7 +195,10 @@ size_t sim_device_bytes(const sim_t *h);
  * cells, b = 6, 8, with edge c = 1 (two, 6) or 5 (two, 4); c = 6, 7 as 2, 4
  * with a persistent interior kernel prefetching its next tile into L2; c = 8
  * as 4 and c = 9 as 6, each with the edge tiles walked by a persistent
- * prefetching kernel);
+ * prefetching kernel); 2300 + 10 c + b for a three-way split (interior; the
+ * radial-PML rows' interior z tiles with a body for interior z; the z ends),
+ * interior b = 5 plain or 4 prefetching, c = 0 to 3 the radial / end kernels'
+ * cells per thread and blocks per SM;
  * v * 10000 + s (a pair code) for the velocity kernel of split code v with the
  * stress kernel of split code s.  opts.tile accepts every code listed here. */
 int sim_config(const sim_t *h, int *kernel, int *tile_rows);

@@ -249,7 +249,11 @@ size_t march_smem_bytes(int storage, int code);
 // interior kernel that prefetches its next tile into L2; c = 8: plain
 // interior, edge (four cells, 3 blocks) walked by a persistent prefetching
 // kernel; c = 9: prefetching interior and prefetching edge (two cells, 4
-// blocks).  A pair code
+// blocks); 2300 + 10 c + b = three-way split (interior, radial-PML rows with a
+// body for interior z, z ends with the general body; persistent prefetching
+// kernels for the last two): interior b = 5 plain, 4 prefetching, and c = 0:
+// radial (four cells, 4 blocks per SM) + ends (four, 3); 1: (two, 5) + (two,
+// 4); 2: (two, 4) + (two, 4); 3: (four, 3) + (four, 3).  A pair code
 // v * 10000 + s runs the velocity kernel of split code v and the stress kernel
 // of split code s (the autotuner times the two apart).
 constexpr int SPLIT_CODE = 2000;
@@ -262,11 +266,11 @@ inline int split_vel_code(int code) { return code >= 10000 ? code / 10000 : code
 inline int split_str_code(int code) { return code >= 10000 ? code % 10000 : code; }
 inline bool is_hoist(int code) { return code > 2000 && code < 3000; }
 inline int hoist_blocks(int code) { return code % 10; }
-inline bool hoist_split(int code) { return (code / 100) % 10 == 2; }
+inline bool hoist_split(int code) { return (code / 100) % 10 == 2 || (code / 100) % 10 == 3; }
 inline bool hoist_zfast(int code) { return !hoist_split(code) && (code / 10) % 10 == 1; }
 inline int hoist_cells_per_thread(int code) {
   const int c = (code / 10) % 10;
-  return ((code / 100) % 10 == 1 || (hoist_split(code) && (c == 1 || c == 5))) ? 2 : 4;
+  return ((code / 100) % 10 == 1 || ((code / 100) % 10 == 2 && (c == 1 || c == 5))) ? 2 : 4;
 }
 cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts = 3);
 // BF16 GEMM on the tcgen05 tensor cores (gemm_tc.cu); status bit 0: a

@@ -235,7 +235,7 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
   const int cand[] = {2,    4,    6,    8,    106,  110,  114,  1216, 1232, 1264, 1416, 1432, 1464, 1816, 1832,
                       1864, 2003, 2004, 2005, 2013, 2014, 2106, 2108, 2204, 2205, 2216, 2218, 2224, 2225,
                       2234, 2235, 2244, 2245, 2256, 2258, 2264, 2265, 2274, 2275,
-                      2284, 2285, 2294, 2295, SPLIT_CODE};
+                      2284, 2285, 2294, 2295, 2304, 2305, 2314, 2315, 2324, 2325, 2334, 2335, SPLIT_CODE};
   cudaEvent_t a, b, c3;
   CK(h, cudaEventCreate(&a));
   CK(h, cudaEventCreate(&b));

@@ -133,10 +133,12 @@ __device__ __forceinline__ void zero_ids(int (&o)[NV]) {
   for (int e = 0; e < NV; e++) o[e] = 0;
 }
 
-// NV cells per thread (4 or 2).  LEAN: the NV cells are interior (no PML
+// NV cells per thread (4 or 2).  ZIN: the NV cells and their +1 z neighbours
+// lie inside NZ and outside the z PML (no z memory variable, no z bound
+// check); by default the same as LEAN.  LEAN: the NV cells are interior (no PML
 // memory variable, all inside NZ, k0 + NV < NZ); the kernels pick the lean
 // body per thread, or run it alone on the interior tiles.
-template <typename T, int NV, bool LEAN, bool PRE = false>
+template <typename T, int NV, bool LEAN, bool PRE = false, bool ZIN = LEAN>
 __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, const int i, const int k0) {
   const int nth = p.nth, NR = p.NR, NZ = p.NZ;
   const long long NZp = p.NZp, pl = p.plane;
@@ -147,7 +149,7 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
   const T *srr = (const T *)p.f[F_SRR], *spp = (const T *)p.f[F_SPP], *szz = (const T *)p.f[F_SZZ];
   const T *srp = (const T *)p.f[F_SRP], *spz = (const T *)p.f[F_SPZ], *srz = (const T *)p.f[F_SRZ];
   T *vr = (T *)p.f[F_VR], *vp = (T *)p.f[F_VP], *vz = (T *)p.f[F_VZ];
-  const bool im = i >= 1, ip = i + 1 < NR, k4 = LEAN || k0 + NV < NZ, km = k0 > 0;
+  const bool im = i >= 1, ip = i + 1 < NR, k4 = ZIN || k0 + NV < NZ, km = k0 > 0;
 
   // ---- every load
   float a_srr[NV];
@@ -203,7 +205,7 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
   const long long cr = rp ? ((long long)j * p.pml_r + (i - p.nr)) * NZp + k0 : 0;
   const int pz = p.pml_z;
   const long long czrow = ((long long)j * NR + i) * (2 * pz);
-  const bool zl = !LEAN && pz > 0 && (k0 < pz || k0 + NV - 1 >= NZ - pz);
+  const bool zl = !ZIN && pz > 0 && (k0 < pz || k0 + NV - 1 >= NZ - pz);
   float ur_vr[NV], uq_vr[NV], ur_vp[NV], uq_vp[NV], ur_vz[NV], uq_vz[NV];
   if (PRE && rp) {
     ldv(ur_vr, p.psr[R_VR] + cr);
@@ -249,7 +251,7 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
 #pragma unroll
   for (int e = 0; e < NV; e++) {
     const int k = k0 + e;
-    if (!LEAN && k >= NZ) break;
+    if (!ZIN && k >= NZ) break;
     const bool zp = zl && (k < pz || k >= NZ - pz);
     const int kz = k < pz ? k : k - (NZ - 2 * pz);
     const float4 abz = zp ? __ldg(p.ab_z + k) : z4();
@@ -283,7 +285,7 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
       out_p[e] += vel_coef(dtv, rho_c[e] + rho_j[e]) * (Dr + Q + Dz);
     }
     // v_z at (r_{i+1/2}, theta_j, z_{k+1/2}), k + 1 < NZ
-    if (LEAN || k + 1 < NZ) {
+    if (ZIN || k + 1 < NZ) {
       const float s1 = p_srz[e];
       float Dr = (s1 - srz_e) * idr;
       float Q = (0.5f * (s1 + srz_e) + (spz_e - jm_spz[e]) * idth) * inv_rh;
@@ -321,7 +323,7 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
   }
 }
 
-template <typename T, int NV, bool LEAN, bool PRE = false>
+template <typename T, int NV, bool LEAN, bool PRE = false, bool ZIN = LEAN>
 __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, const int i, const int k0) {
   const int nth = p.nth, NR = p.NR, NZ = p.NZ;
   const long long NZp = p.NZp, pl = p.plane;
@@ -332,7 +334,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
   const T *vr = (const T *)p.f[F_VR], *vp = (const T *)p.f[F_VP], *vz = (const T *)p.f[F_VZ];
   T *srr = (T *)p.f[F_SRR], *spp = (T *)p.f[F_SPP], *szz = (T *)p.f[F_SZZ];
   T *srp = (T *)p.f[F_SRP], *spz = (T *)p.f[F_SPZ], *srz = (T *)p.f[F_SRZ];
-  const bool im = i >= 1, ip = i + 1 < NR, k4 = LEAN || k0 + NV < NZ, km = k0 > 0;
+  const bool im = i >= 1, ip = i + 1 < NR, k4 = ZIN || k0 + NV < NZ, km = k0 > 0;
 
   // ---- every load
   float a_vr[NV];
@@ -393,7 +395,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
   const long long cr = rp ? ((long long)j * p.pml_r + (i - p.nr)) * NZp + k0 : 0;
   const int pz = p.pml_z;
   const long long czrow = ((long long)j * NR + i) * (2 * pz);
-  const bool zl = !LEAN && pz > 0 && (k0 < pz || k0 + NV - 1 >= NZ - pz);
+  const bool zl = !ZIN && pz > 0 && (k0 < pz || k0 + NV - 1 >= NZ - pz);
   float ur_rr[NV], uq_pp[NV], ur_rp[NV], uq_rp[NV], ur_rz[NV], uq_pz[NV];
   if (PRE && rp) {
     ldv(ur_rr, p.psr[R_ERR] + cr);
@@ -456,7 +458,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
 #pragma unroll
   for (int e = 0; e < NV; e++) {
     const int k = k0 + e;
-    if (!LEAN && k >= NZ) break;
+    if (!ZIN && k >= NZ) break;
     const bool zp = zl && (k < pz || k >= NZ - pz);
     const int kz = k < pz ? k : k - (NZ - 2 * pz);
     const float4 abz = zp ? __ldg(p.ab_z + k) : z4();
@@ -492,7 +494,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
         orp[e] += dts * mu * (gr + Q);
       }
       // s_rz at (r_i, theta_j, z_{k+1/2})
-      if (LEAN || k + 1 < NZ) {
+      if (ZIN || k + 1 < NZ) {
         float gz = (vr_e1 - vr_e) * idz;
         float gr = (vz_e - m_vz[e]) * idr;
         if (zp) gz = (PRE ? stretch_reg(uz_rz[e], abz.z, abz.w, gz) : stretch(p.psz[Z_GRZ] + czrow + kz, abz.z, abz.w, gz));
@@ -502,7 +504,7 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
       }
     }
     // s_phiz at (r_{i+1/2}, theta_{j+1/2}, z_{k+1/2})
-    if (LEAN || k + 1 < NZ) {
+    if (ZIN || k + 1 < NZ) {
       float Q = (jp_vz[e] - vz_e) * idth * inv_rh;
       float gz = (vp_e1 - vp_e) * idz;
       if (rp) Q = (PRE ? stretch_reg(uq_pz[e], abq.z, abq.w, Q) : stretch(p.psr[Q_GPZ] + cr + e, abq.z, abq.w, Q));
@@ -748,6 +750,66 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_edge_pf(const KParams 
   }
 }
 
+// Three-way split of a half step: interior tiles (above), the z-interior
+// tiles of the other rows (in a well, the radial PML) with a body compiled
+// for "radial PML, interior z" (no z memory variable, no z bound check), and
+// the z-end tiles of every row with the general body.  Both walk their tiles
+// as one wave of resident blocks that prefetch the next tile into L2.
+template <typename T, int NV, bool VEL>
+__device__ __forceinline__ void prefetch_edge_tile(const KParams &p, int j, int i, int k0) {
+  constexpr int LANES = 128 / (NV * 4);
+  if (i >= p.NR || k0 >= p.NZ) return;
+  prefetch_tile<T, NV, VEL>(p, j, i, k0);
+  if (i >= p.nr && (threadIdx.x & (LANES - 1)) == 0) {
+    const long long cr = ((long long)j * p.pml_r + (i - p.nr)) * p.NZp + k0;
+    const int q0 = VEL ? R_VR : R_ERR, q1 = VEL ? Q_VR : Q_EPP;
+    for (int u = 0; u < 3; u++) prefetch_l2(p.psr[q0 + u] + cr), prefetch_l2(p.psr[q1 + u] + cr);
+  }
+}
+
+template <typename T, int NV, int MINB, bool VEL>
+__global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_radial_pf(const KParams p, Split2 q, int ntiles) {
+  const int nrr = q.nrt - q.nrt_in;
+  auto cell = [&](int t, int &j, int &i, int &k0) {
+    j = t % p.nth;
+    t /= p.nth;
+    i = (q.nrt_in + t % nrr) * HB_Y + threadIdx.y;
+    k0 = ((q.ez_lo + t / nrr) * HB_X + threadIdx.x) * NV;
+  };
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int j, i, k0;
+    if (t + (int)gridDim.x < ntiles) {
+      cell(t + gridDim.x, j, i, k0);
+      prefetch_edge_tile<T, NV, VEL>(p, j, i, k0);
+    }
+    cell(t, j, i, k0);
+    if (i < p.i_lo || i >= p.i_hi) continue;
+    if (VEL) vel_hoist_body<T, NV, false, true, true>(p, j, i, k0);
+    else str_hoist_body<T, NV, false, true, true>(p, j, i, k0);
+  }
+}
+
+template <typename T, int NV, int MINB, bool VEL>
+__global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_ends_pf(const KParams p, Split2 q, int ntiles) {
+  const int nzend = q.ez_lo + (q.enzt - q.ez_hi);
+  auto cell = [&](int t, int &j, int &i, int &k0) {
+    j = t % p.nth;
+    t /= p.nth;
+    const int e = t % nzend, zt = e < q.ez_lo ? e : q.ez_hi + (e - q.ez_lo);
+    i = (t / nzend) * HB_Y + threadIdx.y;
+    k0 = (zt * HB_X + threadIdx.x) * NV;
+  };
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int j, i, k0;
+    if (t + (int)gridDim.x < ntiles) {
+      cell(t + gridDim.x, j, i, k0);
+      prefetch_edge_tile<T, NV, VEL>(p, j, i, k0);
+    }
+    cell(t, j, i, k0);
+    if (i >= p.i_lo && i < p.i_hi && k0 < p.NZ) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
+  }
+}
+
 // Batched scenarios: each half step is two persistent launches over the work
 // lists of up to BATCH_MAX cases, one over every case's interior tiles (lean
 // body only) and one over their edge tiles (radial-PML rows and z ends,
@@ -906,6 +968,51 @@ cudaError_t launch_split2_half(const KParams &p, const Split2 &q, cudaStream_t s
   return cudaGetLastError();
 }
 
+// three-way split half step: interior (plain or prefetching), radial tiles
+// (NVE cells per thread, MINB_R blocks per SM), z-end tiles (NVE, MINB_E)
+template <typename T, int NV, int MINB_IN, bool PF, int NVE, int MINB_R, int MINB_E, bool VEL>
+cudaError_t launch_split3_half(const KParams &p, const Split2 &q, cudaStream_t s) {
+  dim3 blk(HB_X, HB_Y);
+  const int nin = q.zt_hi - q.zt_lo;
+  if (q.nrt_in > 0 && nin > 0) {
+    if constexpr (PF) {
+      const long long tiles = (long long)p.nth * q.nrt_in * nin;
+      if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+      const int grid = (int)std::min<long long>(tiles, (long long)sm_count() * MINB_IN);
+      hoist_interior_pf<T, NV, MINB_IN, VEL><<<grid, blk, 0, s>>>(p, q.zt_lo, q.nrt_in, (int)tiles);
+    } else {
+      hoist_interior<T, NV, MINB_IN, VEL><<<dim3(p.nth, q.nrt_in, nin), blk, 0, s>>>(p, q.zt_lo);
+    }
+  }
+  const long long rad = (long long)p.nth * (q.nrt - q.nrt_in) * (q.ez_hi - q.ez_lo);
+  const long long ends = (long long)p.nth * q.nrt * (q.ez_lo + q.enzt - q.ez_hi);
+  if (rad > 0x7fffffffLL || ends > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (rad > 0)
+    hoist_radial_pf<T, NVE, MINB_R, VEL>
+        <<<(int)std::min<long long>(rad, (long long)sm_count() * MINB_R), blk, 0, s>>>(p, q, (int)rad);
+  if (ends > 0)
+    hoist_ends_pf<T, NVE, MINB_E, VEL>
+        <<<(int)std::min<long long>(ends, (long long)sm_count() * MINB_E), blk, 0, s>>>(p, q, (int)ends);
+  return cudaGetLastError();
+}
+
+template <typename T, int NV, int MINB_IN, bool PF, int NVE, int MINB_R, int MINB_E>
+cudaError_t launch_split3_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
+  const Split2 q = split2<NV, NVE>(p);
+  cudaError_t e = cudaSuccess;
+  if (parts & 1) {
+    if (ev) cudaEventRecord(ev[0], s);
+    e = launch_split3_half<T, NV, MINB_IN, PF, NVE, MINB_R, MINB_E, true>(p, q, s);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], s);
+  }
+  if (parts & 2) {
+    e = launch_split3_half<T, NV, MINB_IN, PF, NVE, MINB_R, MINB_E, false>(p, q, s);
+    if (ev) cudaEventRecord(ev[2], s);
+  }
+  return e;
+}
+
 template <typename T, int NV, int MINB_IN, int NVE, int MINB_E, bool PF = false, bool PFE = false>
 cudaError_t launch_split2_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
   const Split2 q = split2<NV, NVE>(p);
@@ -944,7 +1051,20 @@ cudaError_t launch_hoist_t(const KParams &p, cudaStream_t s, cudaEvent_t *ev, in
 
 template <typename T>
 cudaError_t launch_hoist_st(int nv, int minb, bool zf, bool split, int edge, const KParams &p, cudaStream_t s,
-                            cudaEvent_t *ev, int parts) {
+                            cudaEvent_t *ev, int parts, bool split3 = false) {
+  if (split3) {  // interior b = 5 plain, 4 prefetching; c = radial / ends configuration
+    switch (edge * 10 + minb) {
+      case 4: return launch_split3_t<T, 4, 4, true, 4, 4, 3>(p, s, ev, parts);
+      case 5: return launch_split3_t<T, 4, 5, false, 4, 4, 3>(p, s, ev, parts);
+      case 14: return launch_split3_t<T, 4, 4, true, 2, 5, 4>(p, s, ev, parts);
+      case 15: return launch_split3_t<T, 4, 5, false, 2, 5, 4>(p, s, ev, parts);
+      case 24: return launch_split3_t<T, 4, 4, true, 2, 4, 4>(p, s, ev, parts);
+      case 25: return launch_split3_t<T, 4, 5, false, 2, 4, 4>(p, s, ev, parts);
+      case 34: return launch_split3_t<T, 4, 4, true, 4, 3, 3>(p, s, ev, parts);
+      case 35: return launch_split3_t<T, 4, 5, false, 4, 3, 3>(p, s, ev, parts);
+    }
+    return cudaErrorInvalidValue;
+  }
   if (split) {  // interior kernel for minb blocks per SM; edge kernel config c (cells per thread, blocks per SM)
     switch (edge * 10 + minb) {
       case 4: return launch_split2_t<T, 4, 4, 4, 4>(p, s, ev, parts);
@@ -1008,12 +1128,12 @@ cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, int 
 
 cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
   const int minb = hoist_blocks(code), nv = hoist_cells_per_thread(code);
-  const bool zf = hoist_zfast(code), split = hoist_split(code);
+  const bool zf = hoist_zfast(code), split = hoist_split(code), split3 = (code / 100) % 10 == 3;
   const int edge = (code / 10) % 10;
   switch (storage) {
-    case 0: return launch_hoist_st<float>(nv, minb, zf, split, edge, p, s, ev, parts);
-    case 1: return launch_hoist_st<__nv_bfloat16>(nv, minb, zf, split, edge, p, s, ev, parts);
-    case 2: return launch_hoist_st<__half>(nv, minb, zf, split, edge, p, s, ev, parts);
+    case 0: return launch_hoist_st<float>(nv, minb, zf, split, edge, p, s, ev, parts, split3);
+    case 1: return launch_hoist_st<__nv_bfloat16>(nv, minb, zf, split, edge, p, s, ev, parts, split3);
+    case 2: return launch_hoist_st<__half>(nv, minb, zf, split, edge, p, s, ev, parts, split3);
   }
   return cudaErrorInvalidValue;
 }

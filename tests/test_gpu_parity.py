@@ -293,7 +293,8 @@ def test_march_every_tile_fields_elementwise(tile):
 
 
 SPLIT_TILES = (2000, 2003, 2004, 2005, 2013, 2014, 2106, 2108, 2204, 2205, 2216, 2218, 2224, 2225, 2234, 2235,
-               2244, 2245, 2256, 2258, 2264, 2265, 2274, 2275, 2284, 2285, 2294, 2295)
+               2244, 2245, 2256, 2258, 2264, 2265, 2274, 2275, 2284, 2285, 2294, 2295,
+               2304, 2305, 2314, 2315, 2324, 2325, 2334, 2335)
 
 
 @pytest.mark.parametrize("tile", SPLIT_TILES)
@@ -318,7 +319,7 @@ def test_split_variants_fields_elementwise(tile):
         assert rel_l2(s.traces(), o.traces()) <= TRACE_TOL
 
 
-@pytest.mark.parametrize("tile", (2204, 2205, 2216, 2218, 2224, 2235, 2244, 2258, 2264, 2275, 2285, 2294))
+@pytest.mark.parametrize("tile", (2204, 2205, 2216, 2218, 2224, 2235, 2244, 2258, 2264, 2275, 2285, 2294, 2305, 2314))
 def test_interior_edge_split_on_config1(tile):
     """The interior / edge split launches on the cased-well geometry, where
     most tiles are interior: traces and fields against the oracle."""
