@@ -486,8 +486,10 @@ def main():
     if os.path.exists(tj):
         d = json.load(open(tj))
         ent = d.get("kernels", {}).get(names[qd])
-        if ent and d.get("kernel_hash") == kernel_hash() and ent.get("cells"):
-            traffic = ent["dram_bytes_per_launch"] * cells / ent["cells"]
+        # captured on the full well: reported for that workload only (a crop has
+        # another share of edge cells, so scaling by the cell count would mislead)
+        if ent and d.get("kernel_hash") == kernel_hash() and ent.get("cells") == cells:
+            traffic = ent["dram_bytes_per_launch"]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": names[qd], "peak_source": f"{peak_kind} hbm_gbs (copy)",
             "alg_bytes_per_cell": per_cell, "tile_rows": tile,
