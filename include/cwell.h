@@ -221,16 +221,19 @@ const char *sim_error_string(int code);
 
 /* ------------------------------------------------------------------------
  * Batched scenarios: n independent wells (e.g. cement-hardening cases of
- * uneven length) advanced together, one launch per kernel per step for all
- * of them.  Each case is defined exactly as for sim_create (grid, medium,
- * source, receivers; shapes may differ between cases); opts is shared
- * (storage, stream, device, mem_cap applied to the batch total, graph_chunk,
- * max_steps; opts.kernel and opts.tile are ignored).  The cases run the
- * load-first split bodies (tile code 2004 of sim_config) driven by blocks that
- * walk a work list of (case, theta, r tile, z tile) items; the number of
- * blocks is chosen by timing candidates at create time.  A case computes
- * exactly what its own sim_create handle with kernel SIM_KERNEL_SPLIT and
- * tile 2004 computes.  SIM_EINVAL for a case of more than 2^31 - 1 items.
+ * uneven length) advanced together in one stream and one captured graph.
+ * Each case is defined exactly as for sim_create (grid, medium, source,
+ * receivers; shapes may differ between cases); opts is shared (storage,
+ * stream, device, mem_cap applied to the batch total, graph_chunk,
+ * max_steps; opts.kernel and opts.tile are ignored).  Cases of fewer than
+ * 4 Mi cells share one interior and one edge launch per half step of the
+ * load-first split bodies, driven by blocks that walk a work list of (case,
+ * theta, r tile, z tile) items; the number of blocks is chosen by timing
+ * candidates at create time.  A larger case fills the GPU alone and runs its
+ * own split launches with the code its tuner picks (as sim_create with kernel
+ * SIM_KERNEL_SPLIT).  Every case computes what its own sim_create handle on
+ * the split path computes, to FP32 rounding.  SIM_EINVAL for a shared case
+ * of more than 2^31 - 1 items.
  * ------------------------------------------------------------------------ */
 typedef struct simb_s simb_t;
 
@@ -249,7 +252,7 @@ int simb_sync(simb_t *b);
 int simb_traces(simb_t *b, int which, float *out, size_t cap, int *n_rec, int *n_steps);
 int simb_read_field(simb_t *b, int which, int field, float *out, size_t n);
 
-/* Number of cases, work items per kernel launch, persistent blocks per launch. */
+/* Number of cases, work items of the shared launches, persistent blocks per shared launch. */
 int simb_config(const simb_t *b, int *n_cases, long long *work_items, int *grid_blocks);
 
 void simb_destroy(simb_t *b);

@@ -1,9 +1,9 @@
-// Batched scenarios: many wells advanced by one launch per kernel per step.
-// Every case is a regular simulator handle (same validation and set-up as
-// sim_create, buffers updated in place by the load-first split bodies, in an
-// interior and an edge launch per half step); the batch holds their kernel
-// parameters (a host array: they travel as kernel parameters, in launches of up
-// to 64 cases), and captures its steps in a CUDA graph.
+// Batched scenarios: many wells advanced together.  Every case is a regular
+// simulator handle (same validation and set-up as sim_create, buffers updated
+// in place by the load-first split bodies).  Small cases share one interior
+// and one edge launch per half step (their kernel parameters travel as kernel
+// parameters, up to 64 cases per launch); a case large enough to fill the GPU
+// runs its own tuned split launches.  The steps are captured in a CUDA graph.
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -16,8 +16,9 @@ struct simb_s {
   bool own_stream = false;
   std::vector<sim_t *> cases;
   std::vector<KParams> kp;        // the cases' kernel parameters (host: they travel as kernel parameters)
+  std::vector<int> shared, own;   // cases in the shared persistent launches / on their own tuned launches
   RParams *d_rp = nullptr;
-  long long total = 0;  // bound on the items of one work list of all cases
+  long long total = 0;  // bound on the items of one work list of the shared cases
   int grid = 0, graph_chunk = 64, steps_done = 0;
   cudaGraphExec_t gexec = nullptr;
   int gsteps = 0;
@@ -45,10 +46,21 @@ static void brelease(simb_t *b) {
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
+// Small cases share the persistent batched launches (one case cannot fill the
+// GPU); a case of at least OWN_CELLS cells fills it alone and runs its own
+// split launches with the code its tuner chose (the prefetching kernels), in
+// the same stream and graph.
+constexpr long long OWN_CELLS = 4LL << 20;
+
 static cudaError_t batch_step(simb_t *b, const KParams *cases) {
-  const int n = (int)b->cases.size();
-  cudaError_t e = launch_batch_split(b->storage, true, cases, n, b->grid, b->stream);
-  if (e == cudaSuccess) e = launch_batch_split(b->storage, false, cases, n, b->grid, b->stream);
+  cudaError_t e = cudaSuccess;
+  std::vector<KParams> sh;
+  for (int c : b->shared) sh.push_back(cases[c]);
+  for (int half = 1; half <= 2 && e == cudaSuccess; half++) {
+    if (!sh.empty()) e = launch_batch_split(b->storage, half == 1, sh.data(), (int)sh.size(), b->grid, b->stream);
+    for (size_t q = 0; q < b->own.size() && e == cudaSuccess; q++)
+      e = sim_split_halves(b->cases[b->own[q]], cases[b->own[q]], b->stream, half);
+  }
   return e;
 }
 
@@ -126,22 +138,26 @@ extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *m
   }
   sim_opts_t o = *opts;
   o.kernel = SIM_KERNEL_SPLIT;
-  o.tile = SPLIT_CODE;  // the batch drives the plain split bodies: no per-case tuning
   o.cuda_stream = b->stream;
   o.graph_chunk = -1;
   o.timing = 0;
   size_t used = 0;
   for (int c = 0; c < n; c++) {
     if (opts->mem_cap) o.mem_cap = opts->mem_cap > used ? opts->mem_cap - used : 1;
+    const long long cells =
+        (long long)grids[c].nth * (grids[c].nr + grids[c].pml_r) * (grids[c].nz + 2 * grids[c].pml_z);
+    const bool own = cells >= OWN_CELLS;
+    o.tile = own ? 0 : SPLIT_CODE;  // a large case is tuned (split family); the shared ones take the plain code
+    (own ? b->own : b->shared).push_back(c);
     sim_t *h = nullptr;
     int rc = sim_create(&grids[c], &media[c], &sources[c], &receivers[c], &o, &h);
     if (rc) return bail(bfail(b, rc, "case " + std::to_string(c) + ": " + sim_last_error(nullptr)));
     b->cases.push_back(h);
     used += sim_device_bytes(h);
     const long long items = split_items(grids[c].nth, grids[c].nr + grids[c].pml_r, grids[c].nz + 2 * grids[c].pml_z);
-    if (items > 0x7fffffffLL)
+    if (!own && items > 0x7fffffffLL)
       return bail(bfail(b, SIM_EINVAL, "case " + std::to_string(c) + ": more work items than a 32-bit index holds"));
-    b->total += items;
+    if (!own) b->total += items;  // work items of the shared launches
   }
   b->kp.resize(n);
   std::vector<RParams> rp(n);

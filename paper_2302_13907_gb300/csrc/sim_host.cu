@@ -218,6 +218,13 @@ static cudaError_t launch_split_family(int storage, int code, const KParams &p, 
   return e;
 }
 
+// one or both halves of a handle's step with the split code its tuner chose
+// (the batch drives its large cases this way, on the batch's stream)
+cudaError_t cwell::sim_split_halves(const sim_t *h, const KParams &p, cudaStream_t s, int parts) {
+  if (!is_split_family(h->tile_rt)) return cudaErrorInvalidValue;
+  return launch_split_family(h->storage, h->tile_rt, p, s, nullptr, parts);
+}
+
 static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
   const bool allow_split = kernel == SIM_KERNEL_AUTO || kernel == SIM_KERNEL_SPLIT;
   int dev = h->device, maxsm = 0;

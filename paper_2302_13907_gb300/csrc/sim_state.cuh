@@ -89,6 +89,10 @@ int validate_inputs(const sim_grid_t *g, const sim_medium_t *m, const sim_source
 double ricker(double t, double f0);
 void cpml(double d, double al, double dt, float *a, float *b);
 
+// the split halves (parts: 1 velocity, 2 stress) of a handle on the split
+// path with its chosen code, parameters p, on stream s
+cudaError_t sim_split_halves(const sim_t *h, const KParams &p, cudaStream_t s, int parts);
+
 // steps enqueued on the handle (the batch advances its cases directly)
 inline void sim_advance(sim_t *h, int n) { h->steps_done += n; }
 
