@@ -77,13 +77,15 @@ def _peaks():
 
 
 def kernel_hash() -> str:
-    """Hash of the uniform-grid stencil sources (the kernels the stored DRAM
-    traffic was captured on; the refined grid's interface kernel is not one),
+    """Hash of the uniform-grid stencil sources and the two device headers they
+    include (the kernels the stored DRAM traffic was captured on; the refined
+    grid's interface kernel is not one, nor is the host-side state header),
     comments and blank space removed, so that only a change of code voids it."""
     import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2302_13907_gb300", "csrc")
-    files = glob.glob(os.path.join(csrc, "stencil_*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))
+    files = glob.glob(os.path.join(csrc, "stencil_*.cu")) + [os.path.join(csrc, "cwell_internal.cuh"),
+                                                             os.path.join(csrc, "tma_util.cuh")]
     for f in sorted(f for f in files if os.path.basename(f) != "stencil_refine.cu"):
         code = re.sub(r"/\*.*?\*/", " ", open(f).read(), flags=re.S)
         code = re.sub(r"//[^\n]*", " ", code)
