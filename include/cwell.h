@@ -277,7 +277,9 @@ const char *simb_last_error(const simb_t *b);
  * or SIM_EUNSUPPORTED): 1 to 5 zones; with interfaces grid.nth in {8, 16, 32,
  * 64} and nth / 2^(n_zones - 1) >= 4; interface rows increasing, at least two
  * rows per zone, the radial PML inside the last zone (row0 <= nr - 2); FP32
- * storage; source kind 0 or 1 (kind 1 off the axis not on a zone's first row).
+ * storage; any source kind, placed on the nodes of the zone that holds it
+ * (the transverse force off the axis and the torsion ring not on a zone's
+ * first row, SIM_EUNSUPPORTED).
  * Ownership and errors as sim_create; simr_last_error(NULL) after a failed create.
  * ------------------------------------------------------------------------ */
 typedef struct {

@@ -35,9 +35,11 @@
  *      floor(j / 2).  Zone m samples the medium given on the finest azimuthal
  *      grid at its own nodes: cell j of zone m is finest cell j 2^(M-1-m).
  *      dt: reading R7 with each row's own azimuthal step.
- *      The radial PML lies in the outermost zone.  Sources: the volumetric
- *      source (kind 0) and the transverse point force (kind 1); the force's
- *      v_r node must not be the first row of a zone other than zone 0.
+ *      The radial PML lies in the outermost zone.  Sources: all four kinds,
+ *      on the nodes of the zone holding the source row; the transverse
+ *      force's v_r node and the torsion ring's s_rphi row must not be the
+ *      first row of a zone other than zone 0 (their cells would straddle
+ *      the interface).
  *
  * Storage: every field is a ragged array, row i holding Ntheta(i) x NZ
  * values (theta, then z fastest) from offset off[i]; zone m is therefore a
@@ -256,7 +258,7 @@ ref_sim *or_ref_create(int nr, int nth, int nz, int pml_r, int pml_z, double dr,
   *err = OR_EINVAL;
   const int NR = nr + pml_r, NZ = nz + 2 * pml_z;
   if (nr < 1 || nth < 4 || (nth & 1) || nz < 2 || pml_r < 0 || pml_z < 0 || !(dr > 0) || !(dz > 0) || M < 1 ||
-      n_mat < 1 || n_rec < 0 || max_steps < 0 || (src_kind != 0 && src_kind != 1))
+      n_mat < 1 || n_rec < 0 || max_steps < 0 || src_kind < 0 || src_kind > 3)
     return NULL;
   if ((nth >> (M - 1)) < 4 || ((nth >> (M - 1)) << (M - 1)) != nth || ((nth >> (M - 1)) & 1)) return NULL;
   for (int m = 0; m + 1 < M; m++) {
@@ -386,6 +388,36 @@ ref_sim *or_ref_create(int nr, int nth, int nz, int pml_r, int pml_z, double dr,
         const int js = (int)(((long)lround(src_theta / dth) % N + N) % N);
         s->src_field[n] = F_SRR; s->src_cell[n] = RX(i, js, k);
         s->src_w[n++] = src_amp / ((i + 0.5) * dr * dr * dth * dz);
+      }
+    } else if (src_kind == 2) { /* longitudinal force, R12: v_z nodes, cells of one row */
+      if (k + 1 >= NZ) bad = 1;
+      else if (axis) {
+        for (int j = 0; j < s->ntz[0]; j++) {
+          s->src_field[n] = F_VZ; s->src_cell[n] = RX(0, j, k);
+          s->src_w[n++] = src_amp / (rho2(s, s->id[RX(0, j, k)], s->id[RX(0, j, k + 1)]) * M_PI * dr * dr * dz);
+        }
+      } else {
+        const int i = (int)floor(src_r / dr), N = s->ntz[s->zone[i]];
+        const double dth = 2.0 * M_PI / N;
+        const int js = (int)(((long)lround(src_theta / dth) % N + N) % N);
+        s->src_field[n] = F_VZ; s->src_cell[n] = RX(i, js, k);
+        s->src_w[n++] = src_amp / (rho2(s, s->id[RX(i, js, k)], s->id[RX(i, js, k + 1)]) * (i + 0.5) * dr * dr * dth * dz);
+      }
+    } else if (src_kind == 3) { /* torsion ring, R13, on every node of its zone */
+      const int i = (int)lround(src_r / dr), ih = (int)floor(src_r / dr);
+      if (axis || i < 1 || i >= NR || ih + 1 > NR || k + 1 >= NZ || s->zone[i - 1] != s->zone[i]) bad = 1;
+      const int N = bad ? 0 : s->ntz[s->zone[i]];
+      for (int j = 0; j < N && !bad; j++) {
+        const int jp = (j + 1) % N;
+        if (muh4(s, s->id[RX(i - 1, j, k)], s->id[RX(i, j, k)], s->id[RX(i - 1, jp, k)], s->id[RX(i, jp, k)]) == 0.0 ||
+            muh4(s, s->id[RX(ih, j, k)], s->id[RX(ih, jp, k)], s->id[RX(ih, j, k + 1)], s->id[RX(ih, jp, k + 1)]) == 0.0) {
+          bad = 1;
+          break;
+        }
+        s->src_field[n] = F_SRP; s->src_cell[n] = RX(i, j, k);
+        s->src_w[n++] = src_amp / (2.0 * M_PI * i * dr * dr * dz);
+        s->src_field[n] = F_SPZ; s->src_cell[n] = RX(ih, j, k);
+        s->src_w[n++] = src_amp / (2.0 * M_PI * (ih + 0.5) * dr * dr * dz);
       }
     } else {
       if (axis) {
@@ -573,7 +605,7 @@ void or_ref_stress_update(ref_sim *s) {
 }
 
 void or_ref_inject_source(ref_sim *s, int n) {
-  const int force = s->src_kind == 1;
+  const int force = s->src_kind == 1 || s->src_kind == 2;
   const double f = or_ricker((force ? n : n + 0.5) * s->dt, s->f0);
   for (int q = 0; q < s->src_n; q++) {
     const double add = s->dt * s->src_w[q] * f;
@@ -605,7 +637,7 @@ void or_ref_sample(ref_sim *s, int n) {
 int or_ref_step(ref_sim *s, int n) {
   if (!s || n < 0) return OR_EINVAL;
   for (int q = 0; q < n; q++) {
-    const int m = s->steps_done, force = s->src_kind == 1;
+    const int m = s->steps_done, force = s->src_kind == 1 || s->src_kind == 2;
     or_ref_velocity_update(s);
     if (force) or_ref_inject_source(s, m);
     or_ref_stress_update(s);

@@ -17,8 +17,7 @@
 // is exact across the interface.  Fields on half-integer azimuth nodes
 // (v_phi, s_rphi, s_phiz) use the interpolant evaluated half a fine step
 // off the coarse nodes.  Materials of a ghost row below: fine node j takes
-// the coarse cell floor(j / 2).  FP32 storage; volumetric source and the
-// transverse point force.
+// the coarse cell floor(j / 2).  FP32 storage; the four source kinds.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -125,12 +124,14 @@ constexpr int REFINED_VEL_CODE = 2285, REFINED_STR_CODE = 2294;
 
 cudaError_t enqueue_refined_step(simr_t *h) {
   cudaError_t e = cudaSuccess;
+  const bool force = h->src_kind == 1 || h->src_kind == 2;
   for (size_t m = 0; m < h->kps.size() && e == cudaSuccess; m++)
     e = launch_hoist(0, REFINED_VEL_CODE, h->kps[m], h->stream, nullptr, 1);
-  if (e == cudaSuccess && h->src_kind == 1) e = launch_inject(0, h->ip, h->stream);
+  if (e == cudaSuccess && force) e = launch_inject(0, h->ip, h->stream);
   if (e == cudaSuccess) e = launch_xfer(h->xv, h->stream);
   for (size_t m = 0; m < h->kps.size() && e == cudaSuccess; m++)
     e = launch_hoist(0, REFINED_STR_CODE, h->kps[m], h->stream, nullptr, 2);
+  if (e == cudaSuccess && h->src_kind == 3) e = launch_inject(0, h->ip, h->stream);
   if (e == cudaSuccess) e = launch_xfer(h->xs, h->stream);
   if (e == cudaSuccess) e = launch_batch_receivers(0, h->d_rp, (int)h->kps.size(), h->stream);
   return e;
@@ -151,8 +152,6 @@ extern "C" int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, co
   if (opts->storage != 0) return rfail(nullptr, SIM_EUNSUPPORTED, "refined grid: FP32 storage only");
   if (opts->kernel != SIM_KERNEL_AUTO && opts->kernel != SIM_KERNEL_SPLIT)
     return rfail(nullptr, SIM_EUNSUPPORTED, "refined grid: the split kernels only");
-  if (source->kind != 0 && source->kind != 1)
-    return rfail(nullptr, SIM_EUNSUPPORTED, "refined grid: volumetric source or transverse force only");
   if (M < 1 || M > 5 || (M > 1 && !zones->row0)) return rfail(nullptr, SIM_EINVAL, "zones: 1 to 5 zones");
   const int nth0 = g.nth >> (M - 1);
   if (nth0 < 4 || (nth0 << (M - 1)) != g.nth || (nth0 & 1))
@@ -181,10 +180,10 @@ extern "C" int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, co
   };
   auto fine = [&](int j, int i, int k) { return cid[((size_t)j * NR + i) * NZ + k]; };  // finest-grid cell ID
   auto zone_id = [&](int m, int j, int i, int k) { return fine(j << (M - 1 - m), i, k); };  // zone m's cell j
-  if (source->kind == 1 && source->r >= g.dr) {
+  if ((source->kind == 1 || source->kind == 3) && source->r >= g.dr) {
     const int i = (int)lround(source->r / g.dr);
     if (i >= 1 && i < NR && zone_of(i - 1) != zone_of(i))
-      return rfail(nullptr, SIM_EUNSUPPORTED, "source: the force's v_r node is the first row of a zone");
+      return rfail(nullptr, SIM_EUNSUPPORTED, "source: the force's v_r node or the torsion ring's s_rphi row is the first row of a zone");
   }
 
   simr_t *h = new simr_t();
@@ -302,9 +301,10 @@ extern "C" int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, co
   int n_pulse = (int)std::min<double>(ceil(8.0 / (source->f0 * dt)) + 1.0, 1e8);
   h->n_wav = std::max(n_pulse, 1);
   std::vector<float> wav(h->n_wav);
-  for (int n = 0; n < h->n_wav; n++)
+  for (int n = 0; n < h->n_wav; n++)  // volumetric: the stress increment; forces f(t_n); torsion f(t_{n+1/2})
     wav[n] = source->kind == 0 ? (float)(dt * source->amplitude * ricker((n + 0.5) * dt, source->f0) / vol)
-                               : (float)ricker(n * dt, source->f0);
+             : source->kind == 3 ? (float)ricker((n + 0.5) * dt, source->f0)
+                                 : (float)ricker(n * dt, source->f0);
   ALLOC(h->wav, wav.size() * 4);
   UP(h->wav, wav.data(), wav.size() * 4);
 
@@ -447,18 +447,51 @@ extern "C" int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, co
     UP(h->d_rp, rp.data(), M * sizeof(RParams));
   }
 
-  // --- transverse point force (R12) on the zone's own nodes
-  if (source->kind == 1) {
+  // --- point forces (R12) and the torsion ring (R13) on the zone's own nodes
+  if (source->kind != 0) {
     std::vector<int> ifld;
     std::vector<long long> ioff;
     std::vector<float> iw;
-    const int mz = axis ? 0 : zone_of((int)lround(source->r / g.dr));
+    const int mz = axis ? 0 : zone_of(source->kind == 2 ? (int)floor(source->r / g.dr) : (int)lround(source->r / g.dr));
     const RZone &Z = h->z[mz];
     const int n = Z.nth, base = Z.row - Z.g_lo;
     const double dth = 2.0 * M_PI / n, dr = g.dr, dz = g.dz, A = source->amplitude;
     auto rho2 = [&](int a, int b) { return 0.5 * (medium->rho[a] + medium->rho[b]); };
     auto dc = [&](int j, int l) { return ((long long)j * Z.NR + l) * NZp + ks; };
-    if (axis) {
+    auto mu = [&](int a) { return medium->rho[a] * medium->vs[a] * medium->vs[a]; };
+    if (source->kind == 2) {  // longitudinal force: v_z nodes, the cells above and below in one row
+      if (ks + 1 >= NZ) return bail(rfail(h, SIM_EINVAL, "source: the force node falls outside the grid"));
+      if (axis) {
+        for (int j = 0; j < n; j++) {
+          ifld.push_back(F_VZ);
+          ioff.push_back(dc(j, 0));
+          iw.push_back((float)(dt * A / (rho2(zone_id(0, j, 0, ks), zone_id(0, j, 0, ks + 1)) * M_PI * dr * dr * dz)));
+        }
+      } else {
+        const int i = (int)floor(source->r / dr);
+        const int js = (int)(((lround(source->theta / dth) % n) + n) % n);
+        ifld.push_back(F_VZ);
+        ioff.push_back(dc(js, i - base));
+        iw.push_back((float)(dt * A / (rho2(zone_id(mz, js, i, ks), zone_id(mz, js, i, ks + 1)) * (i + 0.5) * dr * dr * dth * dz)));
+      }
+    } else if (source->kind == 3) {  // torsion ring on every node of its zone
+      const int i = (int)lround(source->r / dr), ih = (int)floor(source->r / dr);
+      if (i < 1 || i >= NR || ks + 1 >= NZ)
+        return bail(rfail(h, SIM_EINVAL, "source: the torsion ring falls outside the grid"));
+      for (int j = 0; j < n; j++) {
+        const int jp = (j + 1) % n;
+        if (!(mu(zone_id(mz, j, i - 1, ks)) > 0 && mu(zone_id(mz, j, i, ks)) > 0 && mu(zone_id(mz, jp, i - 1, ks)) > 0 &&
+              mu(zone_id(mz, jp, i, ks)) > 0 && mu(zone_id(mz, j, ih, ks)) > 0 && mu(zone_id(mz, jp, ih, ks)) > 0 &&
+              mu(zone_id(mz, j, ih, ks + 1)) > 0 && mu(zone_id(mz, jp, ih, ks + 1)) > 0))
+          return bail(rfail(h, SIM_EUNSUPPORTED, "source: the torsion ring needs a solid at both shear nodes"));
+        ifld.push_back(F_SRP);
+        ioff.push_back(dc(j, i - base));
+        iw.push_back((float)(dt * A / (2.0 * M_PI * i * dr * dr * dz)));
+        ifld.push_back(F_SPZ);
+        ioff.push_back(dc(j, ih - base));
+        iw.push_back((float)(dt * A / (2.0 * M_PI * (ih + 0.5) * dr * dr * dz)));
+      }
+    } else if (axis) {  // transverse force on the axis: the ring-1 v_r nodes
       for (int j = 0; j < n; j++) {
         ifld.push_back(F_VR);
         ioff.push_back(dc(j, 1));

@@ -101,7 +101,7 @@ def _refined(nth=16, nr=16):
     ([1, 8], {}, B.SIM_EINVAL),                           # one-row zone
     ([4, 15], {}, B.SIM_EINVAL),                          # interface inside the radial PML
     ([2, 4, 8], {}, B.SIM_EINVAL),                        # 16 / 2^3 = 2 nodes in zone 0
-    ([4, 8], dict(source_kind=2), B.SIM_EUNSUPPORTED),    # longitudinal force not on this grid
+    ([4, 8], dict(source_kind=3, source_r=0.02), B.SIM_EUNSUPPORTED),  # torsion ring on a zone's first row
     ([4, 8], dict(nth=24), B.SIM_EINVAL),                 # nth not a power of two
     ([4, 8], dict(source_kind=1, source_r=0.02), B.SIM_EUNSUPPORTED),  # force node on a zone's first row
 ])

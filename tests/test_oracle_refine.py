@@ -219,3 +219,41 @@ def test_zoning_rule_halves_the_step_each_time_the_radius_doubles():
     size = [(edges[m + 1] * g.dr) * 2 * np.pi / nths[m] for m in range(len(nths))]
     assert max(size) / min(size) < 2.2
     assert W.refinement_rows(W.Grid(nr=20, nth=8, nz=8, pml_r=4, pml_z=2, dr=0.003, dz=0.003)) == [12]
+
+
+@pytest.mark.parametrize("kind,r0", [(2, 0.0), (2, 0.0305), (3, 0.046)])
+def test_axisymmetric_force_and_torsion_reproduced_on_every_zone(kind, r0):
+    """The longitudinal force on the axis and the torsion ring (R12, R13) in an
+    axisymmetric well excite axisymmetric fields, so every zone must carry
+    the uniform grid's values at its nodes; the off-axis force is checked
+    for running on its zone's nodes (finite, non-zero)."""
+    g = W.Grid(nr=24, nth=16, nz=40, pml_r=4, pml_z=4, dr=0.004, dz=0.004)
+    med = W.cased_well(g, z_top=0.08, casing_in=0.04, casing_t=0.012, cement_out=0.06)
+    src = W.Source(r=r0, theta=0.7, z=0.08, f0=60e3, kind=kind)
+    rec = W.Receivers(r=np.array([0.0, 0.021, 0.061]), theta=np.array([0.0, 0.4, 2.0]),
+                      z=np.array([0.05, 0.1, 0.12]))
+    sc = W.Scenario("refine-src", med, src, rec, steps=200)
+    dt = oracle.Oracle(sc).dt
+    u = oracle.Oracle(sc, dt=dt)
+    r = oracle.RefinedOracle(sc, rows=[4, 8], dt=dt)
+    u.step(200)
+    r.step(200)
+    if r0 > 0 and kind == 2:  # a point off the axis is not axisymmetric
+        assert np.all(np.isfinite(r.field("vz", 1))) and np.abs(r.field("vz", 1)).max() > 0
+        return
+    vscale = max(np.abs(u.field(n)).max() for n in ("vr", "vp", "vz"))
+    sscale = max(np.abs(u.field(n)).max() for n in ("srr", "spp", "szz", "srp", "spz", "srz"))
+    assert vscale > 0 and sscale > 0
+    for n in FIELDS:
+        scale = vscale if n[0] == "v" else sscale
+        for z, (row, rows, nth, _) in enumerate(r.zones):
+            want = u.field(n)[:: g.nth // nth, row:row + rows, :]
+            assert np.abs(r.field(n, z) - want).max() <= 1e-11 * scale, (kind, n, z)
+
+
+def test_torsion_ring_on_a_zone_first_row_is_refused():
+    g = W.Grid(nr=24, nth=16, nz=40, pml_r=4, pml_z=4, dr=0.004, dz=0.004)
+    med = W.cased_well(g, z_top=0.08, casing_in=0.04, casing_t=0.012, cement_out=0.06)
+    sc = W.Scenario("t", med, W.Source(r=0.046, z=0.08, f0=60e3, kind=3), W.on_axis_receivers([0.1]), steps=10)
+    with pytest.raises(oracle.OracleError):
+        oracle.RefinedOracle(sc, rows=[6, 12])  # s_rphi row 12 starts zone 2
