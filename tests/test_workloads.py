@@ -146,6 +146,21 @@ def test_small_cement_case_draws_and_geometry():
         assert np.all(sc.medium.vs[sc.medium.cell_id[:, 0, :]] == 0)
 
 
+def _paper_well():
+    import json
+    import os
+    return json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_realistic_well.json")))
+
+
+def test_realistic_well_defaults_are_the_printed_dimensions():
+    import inspect
+    P = _paper_well()
+    d = {k: v.default for k, v in inspect.signature(W.realistic_well).parameters.items()}
+    for key in ("H_target", "ID_prev", "H_toc", "H_spacer", "L_joint", "L_collar", "OD_target", "OD_collar"):
+        assert d[key] == P[key + "_m"], key
+    assert W.PAPER_STEEL[2] == P["torsion_wave_speed_m_s"]
+
+
 def test_realistic_well_matches_the_printed_dimensions():
     """The paper's realistic well (Sec. 6) at the printed dimensions: interior
     casing OD 0.1778 m to 202 m, collars OD 0.1945 m, 0.184 m long at every
