@@ -257,3 +257,64 @@ def test_torsion_ring_on_a_zone_first_row_is_refused():
     sc = W.Scenario("t", med, W.Source(r=0.046, z=0.08, f0=60e3, kind=3), W.on_axis_receivers([0.1]), steps=10)
     with pytest.raises(oracle.OracleError):
         oracle.RefinedOracle(sc, rows=[6, 12])  # s_rphi row 12 starts zone 2
+
+
+def test_refined_cfl_step_is_inside_the_discrete_stability_limit():
+    """The refined grid's dt (R7 with each row's own azimuthal step) must lie
+    inside the leapfrog stability limit 2 / sqrt(lambda_max) of the coupled
+    zones, interfaces included.  Power iteration on the refined oracle's own
+    half-steps (dt = 1, PML off) on the 20 m well's full radius and azimuth,
+    zoned by the paper's rule, on a 40-cell z-crop: dt <= 0.6 of the limit
+    (the uniform grid's pin; measured 0.49)."""
+    import math
+    full = W.config2()
+    g = full.medium.grid
+    rows = W.refinement_rows(g)
+    ks = int(round(full.source.z / g.dz))
+    crop = W.crop_z(full.medium, ks - 20, 40)
+    sc = W.Scenario("crop", crop, W.Source(z=0.05, f0=8e3), W.on_axis_receivers([0.05]), cfl=0.5, steps=0)
+    dt = oracle.RefinedOracle(sc, rows, max_steps=0).dt
+    assert dt > 3 * oracle.Oracle(sc, max_steps=0).dt
+    o = oracle.RefinedOracle(sc, rows, max_steps=0, dt=1.0, pml_on=False)
+    rng = np.random.default_rng(1)
+    V, S = ("vr", "vp", "vz"), ("srr", "spp", "szz", "srp", "spz", "srz")
+    x = {(n, z): rng.standard_normal(o.field(n, z).shape) for n in V for z in range(o.M)}
+    for z in range(o.M):
+        x[("vz", z)][:, :, -1] = 0.0
+    x[("vr", 0)][:, 0, :] = 0.0
+    lam = 0.0
+    for it in range(150):
+        nrm = math.sqrt(sum(np.sum(a * a) for a in x.values()))
+        for k in x:
+            x[k] /= nrm
+        for z in range(o.M):
+            for n in S:
+                o.field(n, z)[...] = 0.0
+        for (n, z), a in x.items():
+            o.field(n, z)[...] = a
+        o.stress_update()  # stress from v = x
+        for (n, z) in x:
+            o.field(n, z)[...] = 0.0
+        o.velocity_update()  # the velocity that stress drives from v = 0
+        y = {(n, z): -o.field(n, z).copy() for (n, z) in x}
+        lam = sum(np.sum(y[k] * x[k]) for k in x)
+        x = y
+    assert lam > 0
+    assert dt <= 0.6 * 2.0 / math.sqrt(lam), (dt, 2.0 / math.sqrt(lam))
+
+
+def test_refined_pml_long_run_does_not_grow():
+    """20000 steps of a cased well on a refined grid with the PML on: nothing
+    grows (the interfaces add no instability to the PML's)."""
+    g = W.Grid(nr=24, nth=16, nz=48, pml_r=10, pml_z=10, dr=0.005, dz=0.005)
+    med = W.cased_well(g, z_top=0.12, casing_in=0.05, casing_t=0.01, cement_out=0.08)
+    sc = W.Scenario("long", med, W.Source(r=0.03, theta=1.0, z=0.1, f0=20e3, kind=1), W.on_axis_receivers([0.15]),
+                    steps=20000)
+    o = oracle.RefinedOracle(sc, rows=[4, 8])
+    peaks = []
+    for blk in range(20):
+        o.step(1000)
+        peaks.append(max(np.abs(o.field(n, z)).max() for n in FIELDS for z in range(o.M)))
+    peaks = np.array(peaks)
+    assert np.all(np.isfinite(peaks))
+    assert peaks[10:].max() <= peaks[:10].max(), peaks
