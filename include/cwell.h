@@ -288,6 +288,14 @@ typedef struct {
 } simr_zones_t;
 typedef struct simr_s simr_t;
 
+/* The interface maps in FP64 (host only, no device call): coarse -> fine
+ * (fine_to_coarse = 0) the [2n][n] trigonometric interpolation matrix of n
+ * coarse azimuthal nodes, for the integer (half = 0) or half-integer (half = 1)
+ * nodes; fine -> coarse (fine_to_coarse = 1) its adjoint [n][2n] = P^T / 2.
+ * out holds 2 n^2 doubles, row-major.  The refined grid applies them in FP32.
+ * SIM_EINVAL for n < 4, odd n or a null out. */
+int simr_interface_matrix(int n_coarse, int half, int fine_to_coarse, double *out);
+
 int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, const sim_medium_t *medium,
                 const sim_source_t *source, const sim_receivers_t *receivers, const sim_opts_t *opts, simr_t **out);
 /* Enqueue nsteps leapfrog steps (CUDA-graph chunks of opts.graph_chunk steps). */

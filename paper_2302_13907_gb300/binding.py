@@ -140,6 +140,8 @@ def lib(path: str | None = None):
         L.simr_destroy.restype = None
         L.simr_last_error.argtypes = [p]
         L.simr_last_error.restype = ctypes.c_char_p
+        L.simr_interface_matrix.argtypes = [i, i, i, ctypes.POINTER(ctypes.c_double)]
+        L.simr_interface_matrix.restype = i
         _lib = L
     return _lib
 
@@ -348,6 +350,17 @@ class BatchSimulation:
         n, w, g = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
         self._chk(self.L.simb_config(self.h, ctypes.byref(n), ctypes.byref(w), ctypes.byref(g)))
         return n.value, w.value, g.value
+
+
+def interface_matrix(n_coarse: int, half: bool, fine_to_coarse: bool) -> np.ndarray:
+    """The refined grid's interface map (simr_interface_matrix), FP64."""
+    L = lib()
+    shape = (n_coarse, 2 * n_coarse) if fine_to_coarse else (2 * n_coarse, n_coarse)
+    out = np.zeros(shape)
+    rc = L.simr_interface_matrix(int(n_coarse), int(bool(half)), int(bool(fine_to_coarse)), _dp(out))
+    if rc != SIM_OK:
+        raise SimError(rc, "simr_interface_matrix")
+    return out
 
 
 class RefinedSimulation:

@@ -139,6 +139,19 @@ cudaError_t enqueue_refined_step(simr_t *h) {
 
 }  // namespace
 
+extern "C" int simr_interface_matrix(int n_coarse, int half, int fine_to_coarse, double *out) {
+  if (!out || n_coarse < 4 || (n_coarse & 1)) return SIM_EINVAL;
+  const int na = n_coarse, nb = 2 * na;
+  const double hb = 2.0 * M_PI / nb;
+  for (int jb = 0; jb < nb; jb++)
+    for (int ja = 0; ja < na; ja++) {
+      const double d = dirichlet(na, (jb - 2 * ja - (half ? 0.5 : 0.0)) * hb);
+      if (fine_to_coarse) out[(size_t)ja * nb + jb] = 0.5 * d;  // (dtheta_fine / dtheta_coarse) P^T
+      else out[(size_t)jb * na + ja] = d;
+    }
+  return SIM_OK;
+}
+
 extern "C" int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, const sim_medium_t *medium,
                            const sim_source_t *source, const sim_receivers_t *receivers, const sim_opts_t *opts,
                            simr_t **out) {
@@ -531,17 +544,12 @@ extern "C" int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, co
     std::vector<float> mats;
     std::vector<size_t> at(4 * M, 0);  // per interface: P_int, P_half, R_int, R_half offsets
     for (int m = 1; m < M; m++) {
-      const int na = h->z[m - 1].nth, nb = h->z[m].nth;
-      const double hb = 2.0 * M_PI / nb, w = (double)na / nb;
-      for (int half = 0; half < 2; half++) {
-        at[4 * m + half] = mats.size();
-        for (int jb = 0; jb < nb; jb++)
-          for (int ja = 0; ja < na; ja++) mats.push_back((float)dirichlet(na, (jb - 2 * ja - 0.5 * half) * hb));
-      }
-      for (int half = 0; half < 2; half++) {
-        at[4 * m + 2 + half] = mats.size();
-        for (int ja = 0; ja < na; ja++)
-          for (int jb = 0; jb < nb; jb++) mats.push_back((float)(w * dirichlet(na, (jb - 2 * ja - 0.5 * half) * hb)));
+      const int na = h->z[m - 1].nth;
+      std::vector<double> mat(2 * (size_t)na * na);
+      for (int k = 0; k < 4; k++) {  // P_int, P_half, R_int, R_half
+        simr_interface_matrix(na, k & 1, k >> 1, mat.data());
+        at[4 * m + k] = mats.size();
+        for (double v : mat) mats.push_back((float)v);
       }
     }
     ALLOC(h->mats, mats.size() * 4);

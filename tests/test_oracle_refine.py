@@ -318,3 +318,4 @@ def test_refined_pml_long_run_does_not_grow():
     peaks = np.array(peaks)
     assert np.all(np.isfinite(peaks))
     assert peaks[10:].max() <= peaks[:10].max(), peaks
+
