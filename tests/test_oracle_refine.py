@@ -319,3 +319,24 @@ def test_refined_pml_long_run_does_not_grow():
     assert np.all(np.isfinite(peaks))
     assert peaks[10:].max() <= peaks[:10].max(), peaks
 
+
+
+def test_refined_dipole_converges_to_the_uniform_grid():
+    """Fewer halvings toward the axis (coarse zones of 4, then 8, then 16
+    nodes against the uniform 32) bring the transverse dipole's traces closer
+    to the uniform grid's at every off-axis receiver: the refinement's error
+    is the coarse zones' azimuthal resolution, and it vanishes with it
+    (measured 4.3 / 4.1 / 0.27 % and 0.40 / 0.20 / 0.05 %)."""
+    sc = _scenario(nr=30, nth=32, nz=60, kind=1, axis=True, steps=400)
+    u = oracle.Oracle(sc)
+    u.step(400)
+    tu = u.traces()
+    errs = []
+    for rows in ([4, 8, 16], [8, 16], [16]):
+        r = oracle.RefinedOracle(sc, rows=rows, dt=u.dt)
+        r.step(400)
+        tr = r.traces()
+        errs.append([rel_l2(tr[q], tu[q]) for q in (1, 2)])
+    errs = np.array(errs)
+    assert np.all(np.diff(errs, axis=0) < 0), errs
+    assert errs[-1].max() < 0.005
