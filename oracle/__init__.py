@@ -72,6 +72,10 @@ def lib():
             L.or_ricker.restype = d
             L.or_cfl_dt.argtypes = [i, i, i, d, d, p, dp, d]
             L.or_cfl_dt.restype = d
+            L.or_round_storage.argtypes = [d, i]
+            L.or_round_storage.restype = d
+            L.or_set_storage.argtypes = [p, i, d, d]
+            L.or_set_storage.restype = i
             L.or_pml_table.argtypes = [p, i]
             L.or_pml_table.restype = dp
             L.or_velocity_update.argtypes = [p]
@@ -132,7 +136,12 @@ class Oracle:
     """
 
     def __init__(self, scenario, *, max_steps: int | None = None, dt: float = 0.0,
-                 pml_on: bool | None = None, threads: int = 0):
+                 pml_on: bool | None = None, threads: int = 0, storage: str = "f64",
+                 scales: tuple = (1.0, 1.0)):
+        """`storage` "bf16" / "f16" rounds every field to that 16-bit format
+        where the reduced-precision variant stores it (values first rounded
+        to FP32, the variant's arithmetic precision); `scales` = (velocity,
+        stress) factors of the stored representation round(value * scale)."""
         L = lib()
         m = scenario.medium
         g = m.grid
@@ -163,6 +172,11 @@ class Oracle:
         self.cap = cap
         if threads:
             L.or_set_threads(self._h, int(threads))
+        mode = STORAGE_MODES[storage]
+        if mode:
+            rc = L.or_set_storage(self._h, mode, float(scales[0]), float(scales[1]))
+            if rc != 0:
+                raise OracleError(f"or_set_storage failed with code {rc}")
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -217,6 +231,18 @@ class Oracle:
             return np.zeros((self.n_rec, n))
         full = np.ctypeslib.as_array(self._L.or_traces(self._h), shape=(self.n_rec, self.cap))
         return full[:, :n].copy()
+
+
+STORAGE_MODES = {"f64": 0, "bf16": 1, "f16": 2}
+
+
+def round_storage(x, storage: str) -> np.ndarray:
+    """The oracle's rounding of values to a storage format (via FP32, round
+    to nearest even), element by element."""
+    L = lib()
+    mode = STORAGE_MODES[storage]
+    x = np.asarray(x, dtype=np.float64)
+    return np.vectorize(lambda v: L.or_round_storage(float(v), mode), otypes=[np.float64])(x)
 
 
 def cfl_dt(medium, cfl: float) -> float:

@@ -123,6 +123,10 @@ typedef struct {
   int cap, steps_done;
   double *traces;
   int threads;
+  /* storage rounding (precision variant): 0 none, 1 BF16, 2 FP16; stored
+     value = round(value * scale), scale st_sv (velocities), st_ss (stresses) */
+  int storage;
+  double st_sv, st_ss;
 } or_sim;
 
 /* Ricker pulse with dominant frequency f0 and delay 2/f0 (Sec. 2). */
@@ -130,6 +134,37 @@ double or_ricker(double t, double f0) {
   double a = M_PI * f0 * (t - 2.0 / f0);
   a = a * a;
   return (1.0 - 2.0 * a) * exp(-a);
+}
+
+/*
+ * Storage rounding of the precision variant (FP32 arithmetic on fields kept
+ * in a 16-bit format; the paper computes in full precision, so this is a
+ * property of the storage format, written from the IEEE 754 definitions):
+ * the value is first rounded to binary32 (the arithmetic precision of the
+ * variant), then to the format with p significant bits, minimum normal
+ * exponent emin and largest finite value maxf, both steps round to nearest,
+ * ties to even.  Below 2^emin the spacing stays 2^(emin - p + 1) (gradual
+ * underflow); a result beyond maxf is an infinity.
+ *   BF16: p = 8,  emin = -126, maxf = (2 - 2^-7) 2^127
+ *   FP16: p = 11, emin = -14,  maxf = 65504
+ */
+static double round_format(double x, int p, int emin, double maxf) {
+  if (x == 0.0 || !isfinite(x)) return x;
+  int e;
+  frexp(x, &e);              /* |x| in [2^(e-1), 2^e) */
+  int E = e - 1;
+  if (E < emin) E = emin;
+  const double ulp = ldexp(1.0, E - (p - 1));
+  const double q = nearbyint(x / ulp) * ulp; /* exact scaling, round half to even */
+  if (fabs(q) > maxf) return copysign(INFINITY, x);
+  return q;
+}
+
+double or_round_storage(double x, int mode) {
+  const double f = (double)(float)x; /* binary32 first */
+  if (mode == 1) return round_format(f, 8, -126, 0x1.fep127);
+  if (mode == 2) return round_format(f, 11, -14, 65504.0);
+  return x;
 }
 
 /* Reading R7 of the time step. */
@@ -223,6 +258,8 @@ or_sim *or_create(int nr, int nth, int nz, int pml_r, int pml_z, double dr, doub
   s->dr = dr; s->dz = dz; s->dth = 2.0 * M_PI / nth; s->f0 = f0; s->pml_on = pml_on;
   s->ncell = (size_t)nth * s->NR * s->NZ;
   s->threads = 0;
+  s->storage = 0;
+  s->st_sv = s->st_ss = 1.0;
   int NR = s->NR, NZ = s->NZ;
   s->id = (uint16_t *)malloc(s->ncell * sizeof(uint16_t));
   s->n_mat = n_mat;
@@ -543,16 +580,54 @@ void or_sample(or_sim *s, int n) {
   }
 }
 
-/* Advance n leapfrog steps: velocity, stress, source, receivers. */
+/* Storage rounding of the fields q0 .. q1-1 with scale sc: the stored
+   representation is round(value * sc), the value it stands for that over sc. */
+static void round_fields(or_sim *s, int q0, int q1, double sc) {
+  if (!s->storage) return;
+  set_threads(s);
+  for (int q = q0; q < q1; q++) {
+    double *f = s->f[q];
+    const long long n = (long long)s->ncell;
+#pragma omp parallel for schedule(static)
+    for (long long c = 0; c < n; c++) f[c] = or_round_storage(f[c] * sc, s->storage) / sc;
+  }
+}
+
+/* Select storage rounding: mode 0 none (FP64 fields), 1 BF16, 2 FP16, with
+   velocity and stress scales sv, ss (> 0). */
+int or_set_storage(or_sim *s, int mode, double sv, double ss) {
+  if (!s || mode < 0 || mode > 2 || !(sv > 0) || !(ss > 0)) return OR_EINVAL;
+  s->storage = mode;
+  s->st_sv = sv;
+  s->st_ss = ss;
+  round_fields(s, F_VR, F_SRR, sv);
+  round_fields(s, F_SRR, NFIELD, ss);
+  return OR_OK;
+}
+
+/* Advance n leapfrog steps: velocity, stress, source, receivers.  With
+   storage rounding the fields are rounded where the reduced-precision
+   variant stores them: velocities after the velocity half-step (and again
+   after a point force), stresses after the stress half-step with the
+   volumetric source (and again after the torsion ring). */
 int or_step(or_sim *s, int n) {
   if (!s || n < 0) return OR_EINVAL;
   for (int q = 0; q < n; q++) {
     int m = s->steps_done;
     const int force = s->src_kind == 1 || s->src_kind == 2;
     or_velocity_update(s);
-    if (force) or_inject_source(s, m);
+    round_fields(s, F_VR, F_SRR, s->st_sv);
+    if (force) {
+      or_inject_source(s, m);
+      round_fields(s, F_VR, F_SRR, s->st_sv);
+    }
     or_stress_update(s);
-    if (!force) or_inject_source(s, m);
+    if (s->src_kind == 0) or_inject_source(s, m);
+    round_fields(s, F_SRR, NFIELD, s->st_ss);
+    if (s->src_kind == 3) {
+      or_inject_source(s, m);
+      round_fields(s, F_SRR, NFIELD, s->st_ss);
+    }
     or_sample(s, m);
     s->steps_done++;
   }

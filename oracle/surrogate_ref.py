@@ -21,6 +21,10 @@ t = 2 s - 1 + q (positions outside [0, L_out) are dropped).
 Parameter vector order: W1, b1, W2, b2, W3, b3, then (W_l [C_l][C_{l+1}][4],
 b_l) for each transposed convolution, then Wf [C_5][8], bf.
 Loss: mean over the batch and all outputs of (y - target)^2.
+
+Optimiser: Adam (Kingma and Ba, 2015, Algorithm 1), written out in
+`adam_step`: first and second moment estimates with decay rates beta1,
+beta2, bias-corrected by 1 - beta^t, step lr * m_hat / (sqrt(v_hat) + eps).
 """
 from __future__ import annotations
 
@@ -150,3 +154,13 @@ def loss_and_grad(theta, x, target, shp, c0=64, l0=64, q=_ident):
     G["W1"] = c["x"].T @ q(dz1)
     grad = np.concatenate([G[name].ravel() for name, _ in shp])
     return loss, grad
+
+
+def adam_step(w, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update at step t >= 1 (Kingma and Ba, Algorithm 1), FP64.
+    Returns the new (w, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return w - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

@@ -84,3 +84,20 @@ def test_gradient_matches_finite_differences():
 def test_full_size_parameter_count():
     n = sum(int(np.prod(s)) for _, s in R.shapes())
     assert 2.0e6 < n < 2.6e6  # "~2M parameters"
+
+
+def test_adam_step_matches_torch_optim_adam():
+    """Three Adam steps of the reference against torch.optim.Adam (float64,
+    beta = (0.9, 0.999), eps = 1e-8) on changing gradients."""
+    rng = np.random.default_rng(5)
+    w0 = rng.standard_normal(50)
+    grads = [rng.standard_normal(50) * s for s in (1.0, 0.3, 2.0)]
+    lr = 1e-2
+    p = torch.nn.Parameter(torch.tensor(w0, dtype=torch.float64))
+    opt = torch.optim.Adam([p], lr=lr, betas=(0.9, 0.999), eps=1e-8)
+    w, m, v = w0.copy(), np.zeros(50), np.zeros(50)
+    for t, g in enumerate(grads, start=1):
+        p.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        w, m, v = R.adam_step(w, g, m, v, t, lr)
+        assert np.allclose(w, p.detach().numpy(), rtol=1e-13, atol=1e-15), t
