@@ -67,6 +67,8 @@ extern "C" {
 #define SIM_KERNEL_FUSED 2    /* one time-skewed kernel per step, one cell per thread */
 #define SIM_KERNEL_FUSED_VEC 3 /* the time-skewed kernel with four z cells per thread */
 #define SIM_KERNEL_MARCH 4     /* velocity and stress kernels marching theta over TMA-staged planes */
+#define SIM_KERNEL_SWEEP 5     /* one persistent launch per step sweeping z in chunks: both half-steps,
+                                  each chunk's velocities and stresses reused from L2 */
 
 /* Grid (Sec. 3): interior cell counts, PML widths in cells, steps in metres.
  * nth must be even and >= 4; nr >= 2; nz >= 2.  dt > 0 fixes the time step;
@@ -101,9 +103,9 @@ typedef struct {
  *  kind 3, torsion: s_rphi and s_phiz += dt * A f(t_{n+1/2}) / (2 pi r dr dz)
  *    on the whole ring at radius r (a torque about the axis); both shear
  *    nodes must lie in a solid, else SIM_EUNSUPPORTED.
- * Kinds 1-3 run on the split and marching paths (SIM_EUNSUPPORTED when the
- * fused kernels are asked for; AUTO picks among the others) and not in
- * batches. */
+ * Kinds 1-3 run on the split and marching paths, kind 3 on the sweep path
+ * too (SIM_EUNSUPPORTED when the fused kernels, or for kinds 1-2 the sweep
+ * kernel, are asked for; AUTO picks among the others) and not in batches. */
 typedef struct {
   int kind;
   double r, theta, z, f0, amplitude;
@@ -174,6 +176,13 @@ int sim_read_field_noalloc(sim_t *h, int which, float *out, size_t n);
 /* Overwrite field `which` from host FP32 [nth][NR][NZ] (initial conditions). */
 int sim_write_field(sim_t *h, int which, const float *in, size_t n);
 
+/* The time step sim_create would take for this grid and medium (reading R7
+ * of the scheme, Sec. 3: cfl * min over cells 1 / (Vp sqrt(1/dr^2 +
+ * 1/(r dtheta)^2 + 1/dz^2)), r the cell centre; grid->dt when > 0), computed
+ * on the host without any device call.  SIM_EINVAL for a malformed grid or
+ * an out-of-range material ID; the message is sim_last_error(NULL). */
+int sim_time_step(const sim_grid_t *grid, const sim_medium_t *medium, double *dt);
+
 /* Time step in seconds, steps done so far, device bytes held. */
 double sim_dt(const sim_t *h);
 int sim_steps_done(const sim_t *h);
@@ -200,11 +209,31 @@ size_t sim_device_bytes(const sim_t *h);
  * interior b = 5 plain or 4 prefetching, c = 0 to 3 the radial / end kernels'
  * cells per thread and blocks per SM;
  * v * 10000 + s (a pair code) for the velocity kernel of split code v with the
- * stress kernel of split code s.  opts.tile accepts every code listed here. */
+ * stress kernel of split code s; 3000 + 100 m + 10 e + b for the single-pass
+ * sweep kernel (kernel = SIM_KERNEL_SWEEP: four z cells per thread, b resident
+ * blocks per SM, the general body in runs of e cells, z chunks of 32 cells
+ * for m = 0, 1 and 64 for m = 2, 3, odd m with an L2 prefetch of each block's
+ * next velocity item: 3043, 3024, 3143, 3124, 3243, 3224, 3343, 3324).
+ * opts.tile accepts every code listed here. */
 int sim_config(const sim_t *h, int *kernel, int *tile_rows);
 
+/* Test hook of the failure path of the sweep kernel (SIM_KERNEL_SWEEP), the
+ * one kernel whose blocks wait on one another: the stress items of a z chunk
+ * wait, bounded, for the velocity items of that chunk and its two
+ * neighbours.  wait_cycles > 0 sets the limit of one wait in SM clock cycles
+ * (0 restores the default 2^31, about 1 s); withhold_chunk >= 0 makes the
+ * velocity items of that chunk (cells 32 c .. 32 c + 31 along z for the
+ * 32-cell chunks, 64 c .. for the 64-cell ones) never report, so that the
+ * waits on it run out: the kernel sets the status word, the warps that gave
+ * up skip their cells, every later wait gives up at once, and the next
+ * sim_sync returns SIM_ETIMEOUT (the state is then void; destroy the
+ * handle).  -1 turns the withholding off; SIM_EINVAL unless -1 <=
+ * withhold_chunk < ceil(NZ / 32).  Other paths ignore both.  The paper has no
+ * counterpart. */
+int sim_set_wait_test(sim_t *h, long long wait_cycles, int withhold_chunk);
+
 /* Kernel timings gathered with opts.timing = 1: for kernel slot q
- * (0 = fused kernel or velocity kernel of the split and marching paths,
+ * (0 = fused or sweep kernel, or the velocity kernel of the split and marching paths,
  * 1 = their stress kernel, 2 = receivers), total milliseconds and launch count so far.
  * Synchronises. */
 int sim_kernel_time(sim_t *h, int q, double *ms, long *launches);

@@ -17,7 +17,7 @@ from . import build as _build
 SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_EUNSTABLE, SIM_ETIMEOUT, SIM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 FIELDS = ("vr", "vp", "vz", "srr", "spp", "szz", "srp", "spz", "srz")
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
-KERNEL = {"auto": 0, "split": 1, "fused": 2, "fused4": 3, "march": 4}
+KERNEL = {"auto": 0, "split": 1, "fused": 2, "fused4": 3, "march": 4, "sweep": 5}
 
 
 class SimGrid(ctypes.Structure):
@@ -87,6 +87,10 @@ def lib(path: str | None = None):
         L.sim_device_bytes.restype = sz
         L.sim_config.argtypes = [p, ctypes.POINTER(i), ctypes.POINTER(i)]
         L.sim_config.restype = i
+        L.sim_set_wait_test.argtypes = [p, ctypes.c_longlong, i]
+        L.sim_set_wait_test.restype = i
+        L.sim_time_step.argtypes = [p, p, ctypes.POINTER(ctypes.c_double)]
+        L.sim_time_step.restype = i
         L.sim_kernel_time.argtypes = [p, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_long)]
         L.sim_kernel_time.restype = i
         L.sim_save.argtypes = [p, ctypes.c_char_p]
@@ -187,6 +191,17 @@ def make_structs(scenario, *, storage="f32", pml_on=None, graph_chunk=0, stream=
     return (grid, med, src, rec, opts), keep
 
 
+def time_step(scenario, dt=0.0) -> float:
+    """The time step sim_create takes for `scenario` (host only, sim_time_step)."""
+    L = lib()
+    (grid, med, _, _, _), keep = make_structs(scenario, dt=dt)
+    out = ctypes.c_double()
+    rc = L.sim_time_step(ctypes.byref(grid), ctypes.byref(med), ctypes.byref(out))
+    if rc != SIM_OK:
+        raise SimError(rc, L.sim_last_error(None).decode())
+    return out.value
+
+
 class Simulation:
     """One simulator handle (sim_create ... sim_destroy)."""
 
@@ -264,11 +279,15 @@ class Simulation:
                                                       a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
 
     def config(self):
-        """(kernel, tile code): kernel 1 = split, 2 = fused, 4 = marching; the tile code
+        """(kernel, tile code): kernel 1 = split, 2 = fused, 4 = marching, 5 = sweep; the tile code
         the autotuner chose (0 split; r or 100 + r fused; 1000 + 100 r + J marching)."""
         k, t = ctypes.c_int(), ctypes.c_int()
         _check(self.L, self.h, self.L.sim_config(self.h, ctypes.byref(k), ctypes.byref(t)))
         return k.value, t.value
+
+    def set_wait_test(self, wait_cycles: int, withhold_chunk: int):
+        """Test hook of the sweep kernel's bounded waits (sim_set_wait_test)."""
+        _check(self.L, self.h, self.L.sim_set_wait_test(self.h, int(wait_cycles), int(withhold_chunk)))
 
     def kernel_time(self, q: int):
         ms, n = ctypes.c_double(), ctypes.c_long()

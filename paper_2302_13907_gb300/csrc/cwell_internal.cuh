@@ -273,6 +273,17 @@ inline int hoist_cells_per_thread(int code) {
   return ((code / 100) % 10 == 1 || ((code / 100) % 10 == 2 && (c == 1 || c == 5))) ? 2 : 4;
 }
 cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts = 3);
+// single-pass sweep kernel (stencil_sweep.cu): tile code 3000 + 100 m + 10 e
+// + b (b resident blocks per SM, general body in runs of e cells; m: z chunks
+// of 32 (m = 0, 1) or 64 cells (m = 2, 3), odd m with an L2 prefetch of the
+// next velocity item); vdone = sweep_chunks(NZ) ints (zeroed by the launcher
+// before the kernel), status bit 1 = a bounded wait gave up; wait_limit in
+// cycles (0: 2^31); withhold_chunk >= 0 is the test hook that makes one z
+// chunk's velocity items never report
+inline bool is_sweep(int code) { return code >= 3000 && code < 3400; }
+int sweep_chunks(int NZ);
+cudaError_t launch_sweep(int storage, int code, const KParams &p, int *vdone, int *status, long long wait_limit,
+                         int withhold_chunk, cudaStream_t s);
 // BF16 GEMM on the tcgen05 tensor cores (gemm_tc.cu); status bit 0: a
 // bounded wait gave up (read and cleared by gemm_tcgen05_status)
 cudaError_t gemm_tcgen05(bool ta, bool tb, int M, int N, int K, const __nv_bfloat16 *A, int lda,

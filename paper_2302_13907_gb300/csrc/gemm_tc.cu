@@ -16,7 +16,8 @@
 //  * the epilogue reads the accumulator with tcgen05.ld (warp w reads TMEM
 //    lanes 32 w .. 32 w + 31, 16 columns per load) and writes C.
 // A wait that gives up sets bit 0 of the GEMM status word and skips the
-// epilogue; the TMEM columns are always freed.
+// epilogue; the block then waits (bounded) once more for the MMAs it
+// committed, and the TMEM columns are always freed.
 #include "cwell_internal.cuh"
 #include "tma_util.cuh"
 
@@ -173,6 +174,10 @@ __global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const __nv_b
     __syncthreads();
     if (s_fail) break;
   }
+  // after a give-up the MMAs committed last may still be writing the
+  // accumulator: wait (bounded) once more for that commit before the columns
+  // are freed, so that a later CTA allocating them finds them quiet
+  if (s_fail) (void)mbar_wait(bar, phase ^ 1u);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   if (!s_fail) {

@@ -73,6 +73,8 @@ int cwell::validate_inputs(const sim_grid_t *g, const sim_medium_t *m, const sim
   if (s->kind < 0 || s->kind > 3) return fail(nullptr, SIM_EINVAL, "source: kind must be 0 .. 3");
   if (s->kind != 0 && (o->kernel == SIM_KERNEL_FUSED || o->kernel == SIM_KERNEL_FUSED_VEC))
     return fail(nullptr, SIM_EUNSUPPORTED, "source: point forces and torsion run on the split and marching paths only");
+  if ((s->kind == 1 || s->kind == 2) && o->kernel == SIM_KERNEL_SWEEP)
+    return fail(nullptr, SIM_EUNSUPPORTED, "source: point forces act between the half-steps, which the sweep kernel fuses");
   if (!(s->f0 > 0) || !isfinite(s->amplitude)) return fail(nullptr, SIM_EINVAL, "source: need f0 > 0, finite amplitude");
   if (!(s->r >= 0) || s->r >= g->nr * g->dr) return fail(nullptr, SIM_EINVAL, "source: r outside the interior");
   long ks = lround(s->z / g->dz);
@@ -104,17 +106,51 @@ int cwell::validate_inputs(const sim_grid_t *g, const sim_medium_t *m, const sim
       return fail(nullptr, SIM_EINVAL, "receiver " + std::to_string(q) + " outside the interior");
   }
   if (o->storage < 0 || o->storage > 2) return fail(nullptr, SIM_EINVAL, "opts: storage must be 0, 1 or 2");
-  if (o->kernel < 0 || o->kernel > 4) return fail(nullptr, SIM_EINVAL, "opts: kernel must be 0 .. 4");
+  if (o->kernel < 0 || o->kernel > 5) return fail(nullptr, SIM_EINVAL, "opts: kernel must be 0 .. 5");
   if (o->tile != 0) {  // the family of the code must match the kernel asked for; the code itself is checked later
     const int t = o->tile;
     const bool ok = t > 0 && ((o->kernel == SIM_KERNEL_SPLIT && is_split_family(t)) ||
                               (o->kernel == SIM_KERNEL_FUSED && t < 100) ||
                               (o->kernel == SIM_KERNEL_FUSED_VEC && t >= 100 && t < 1000) ||
                               (o->kernel == SIM_KERNEL_MARCH && is_march(t)) ||
-                              (o->kernel == SIM_KERNEL_AUTO && (t < 3000 || is_split_pair(t))));
+                              (o->kernel == SIM_KERNEL_SWEEP && is_sweep(t)) ||
+                              (o->kernel == SIM_KERNEL_AUTO && (t < 3000 || is_split_pair(t) || is_sweep(t))));
     if (!ok) return fail(nullptr, SIM_EINVAL, "opts: tile " + std::to_string(t) + " is not a tile code of the kernel asked for");
   }
   if (o->max_steps < 0) return fail(nullptr, SIM_EINVAL, "opts: max_steps < 0");
+  return SIM_OK;
+}
+
+// Reading R7: dt = cfl * min over cells 1 / (Vp sqrt(1/dr^2 + 1/(r dth)^2 +
+// 1/dz^2)), r the cell centre; grid.dt > 0 overrides it.  Host only.
+static double grid_time_step(const sim_grid_t &g, const sim_medium_t *medium) {
+  if (g.dt > 0) return g.dt;
+  const int NR = g.nr + g.pml_r, NZ = g.nz + 2 * g.pml_z, nth = g.nth;
+  const double dth = 2.0 * M_PI / nth;
+  const uint16_t *cid = medium->cell_id;
+  double best = INFINITY;
+  for (int i = 0; i < NR; i++) {
+    double cmax = 0.0;
+    for (int j = 0; j < nth; j++) {
+      const uint16_t *row = cid + ((size_t)j * NR + i) * NZ;
+      for (int k = 0; k < NZ; k++) cmax = std::max(cmax, medium->vp[row[k]]);
+    }
+    const double rc = (i + 0.5) * g.dr;
+    const double s = sqrt(1.0 / (g.dr * g.dr) + 1.0 / ((rc * dth) * (rc * dth)) + 1.0 / (g.dz * g.dz));
+    best = std::min(best, 1.0 / (cmax * s));
+  }
+  return g.cfl * best;
+}
+
+extern "C" int sim_time_step(const sim_grid_t *grid, const sim_medium_t *medium, double *dt) {
+  if (!grid || !medium || !dt || !medium->cell_id || !medium->vp) return fail(nullptr, SIM_EINVAL, "null argument");
+  if (grid->nr < 1 || grid->nth < 1 || grid->nz < 1 || grid->pml_r < 0 || grid->pml_z < 0 || !(grid->dr > 0) ||
+      !(grid->dz > 0) || (!(grid->dt > 0) && !(grid->cfl > 0)))
+    return fail(nullptr, SIM_EINVAL, "grid: need positive sizes and steps, and dt > 0 or cfl > 0");
+  const size_t ncell = (size_t)grid->nth * (grid->nr + grid->pml_r) * (grid->nz + 2 * grid->pml_z);
+  for (size_t c = 0; c < ncell; c++)
+    if (medium->cell_id[c] >= medium->n_mat) return fail(nullptr, SIM_EINVAL, "medium: cell_id out of range");
+  *dt = grid_time_step(*grid, medium);
   return SIM_OK;
 }
 
@@ -229,8 +265,10 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
   const bool allow_split = kernel == SIM_KERNEL_AUTO || kernel == SIM_KERNEL_SPLIT;
   int dev = h->device, maxsm = 0;
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // point forces rule out the sweep kernel: they key a separate choice
+  const bool force = h->src_kind == 1 || h->src_kind == 2;
   auto key = std::make_tuple(dev, h->grid.nth, h->NR, h->NZ, h->storage * 8 + kernel,
-                             h->kp.pml_r > 0 ? 1 : 0);
+                             (h->kp.pml_r > 0 ? 1 : 0) + (force ? 2 : 0));
   if (!forced) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tune.find(key);
@@ -242,7 +280,8 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
   const int cand[] = {2,    4,    6,    8,    106,  110,  114,  1216, 1232, 1264, 1416, 1432, 1464, 1816, 1832,
                       1864, 2003, 2004, 2005, 2013, 2014, 2106, 2108, 2204, 2205, 2216, 2218, 2224, 2225,
                       2234, 2235, 2244, 2245, 2256, 2258, 2264, 2265, 2274, 2275,
-                      2284, 2285, 2294, 2295, 2304, 2305, 2314, 2315, 2324, 2325, 2334, 2335, SPLIT_CODE};
+                      2284, 2285, 2294, 2295, 2304, 2305, 2314, 2315, 2324, 2325, 2334, 2335, SPLIT_CODE,
+                      3043, 3024, 3143, 3124, 3243, 3224, 3343, 3324};
   cudaEvent_t a, b, c3;
   CK(h, cudaEventCreate(&a));
   CK(h, cudaEventCreate(&b));
@@ -261,11 +300,13 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
     if (kernel == SIM_KERNEL_FUSED_VEC && (!fused_code || rt < 100)) continue;
     if (kernel == SIM_KERNEL_MARCH && !is_march(rt)) continue;
     if (kernel == SIM_KERNEL_SPLIT && !is_split_family(rt)) continue;
+    if (kernel == SIM_KERNEL_SWEEP && !is_sweep(rt)) continue;
+    if (is_sweep(rt) && (force || !(kernel == SIM_KERNEL_AUTO || kernel == SIM_KERNEL_SWEEP))) continue;
     if (is_split_family(rt) && !allow_split) continue;
     if (!h->fused && fused_code) continue;  // no second buffer set for the fused kernels
     if (forced && rt != forced) continue;
     if (forced) {  // a tile asked for by the caller: check that it fits, time nothing
-      const size_t need = is_split_family(rt) ? 1
+      const size_t need = is_split_family(rt) || is_sweep(rt) ? 1
                           : is_march(rt)      ? march_smem_bytes(h->storage, rt)
                           : rt >= 100         ? fused4_smem_bytes(h->storage, rt - 100)
                                               : fused_smem_bytes(h->storage, rt);
@@ -295,6 +336,15 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
       if (mv < best_v) best_v = mv, pick_v = rt;
       if (ms < best_s) best_s = ms, pick_s = rt;
       continue;
+    } else if (is_sweep(rt)) {
+      KParams dry = h->kp;
+      dry.src_i = -1;
+      for (int w = 0; w < 2 && e == cudaSuccess; w++)
+        e = launch_sweep(h->storage, rt, dry, h->vdone, h->status, 0, -1, h->stream);
+      cudaEventRecord(a, h->stream);
+      for (int w = 0; w < 3 && e == cudaSuccess; w++)
+        e = launch_sweep(h->storage, rt, dry, h->vdone, h->status, 0, -1, h->stream);
+      cudaEventRecord(b, h->stream);
     } else if (is_march(rt)) {
       const size_t need = march_smem_bytes(h->storage, rt);
       if (need == 0 || need > (size_t)maxsm) continue;
@@ -381,6 +431,7 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   // or marching kernels; the split and marching paths update one buffer set in place
   h->kernel = opts->kernel == SIM_KERNEL_SPLIT   ? SIM_KERNEL_SPLIT
               : opts->kernel == SIM_KERNEL_MARCH ? SIM_KERNEL_MARCH
+              : opts->kernel == SIM_KERNEL_SWEEP ? SIM_KERNEL_SWEEP
                                                  : SIM_KERNEL_FUSED;
   h->src_kind = source->kind;
   // point forces and torsion are injected between the half-steps: in-place paths only
@@ -412,24 +463,9 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
     h->own_stream = true;
   }
 
-  // --- time step: dt = cfl * min over cells 1 / (Vp sqrt(1/dr^2 + 1/(r dth)^2 + 1/dz^2))
+  // --- time step (reading R7)
   const double dth = 2.0 * M_PI / nth;
-  if (g.dt > 0) {
-    h->dt = g.dt;
-  } else {
-    double best = INFINITY;
-    for (int i = 0; i < NR; i++) {
-      double cmax = 0.0;
-      for (int j = 0; j < nth; j++) {
-        const uint16_t *row = cid + ((size_t)j * NR + i) * NZ;
-        for (int k = 0; k < NZ; k++) cmax = std::max(cmax, medium->vp[row[k]]);
-      }
-      const double rc = (i + 0.5) * g.dr;
-      const double s = sqrt(1.0 / (g.dr * g.dr) + 1.0 / ((rc * dth) * (rc * dth)) + 1.0 / (g.dz * g.dz));
-      best = std::min(best, 1.0 / (cmax * s));
-    }
-    h->dt = g.cfl * best;
-  }
+  h->dt = grid_time_step(g, medium);
   const double dt = h->dt;
 
   // --- storage scales (FP16 needs the velocities lifted by an impedance)
@@ -597,6 +633,7 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   if ((rc = dev_alloc(h, (void **)&h->traces, (size_t)std::max(1, h->n_rec) * h->cap * 4))) return bail(rc);
   if ((rc = dev_alloc(h, (void **)&h->step, 16))) return bail(rc);
   if ((rc = dev_alloc(h, (void **)&h->status, 16))) return bail(rc);
+  if ((rc = dev_alloc(h, (void **)&h->vdone, (size_t)sweep_chunks(NZ) * sizeof(int)))) return bail(rc);
   int *d_ifld = nullptr;
   long long *d_ioff = nullptr;
   float *d_iw = nullptr, *d_iwav = nullptr;
@@ -723,6 +760,9 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
     if (is_split_family(h->tile_rt)) {  // the split kernels won: run in place on the first buffer set
       h->fused = false;
       h->kernel = SIM_KERNEL_SPLIT;
+    } else if (is_sweep(h->tile_rt)) {  // the sweep kernel won: in place as well
+      h->fused = false;
+      h->kernel = SIM_KERNEL_SWEEP;
     } else if (is_march(h->tile_rt)) {  // the marching kernels won: in place as well
       h->fused = false;
       h->kernel = SIM_KERNEL_MARCH;
@@ -735,8 +775,9 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
     if ((rc = autotune(h, h->kernel, opts->tile, &h->tile_rt))) return bail(rc);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "autotune"));
-    h->kernel = is_march(h->tile_rt) ? SIM_KERNEL_MARCH : SIM_KERNEL_SPLIT;
+    h->kernel = is_march(h->tile_rt) ? SIM_KERNEL_MARCH : is_sweep(h->tile_rt) ? SIM_KERNEL_SWEEP : SIM_KERNEL_SPLIT;
   }
+  h->sweep = h->kernel == SIM_KERNEL_SWEEP;
   if (h->kernel == SIM_KERNEL_MARCH) {
     h->march = true;
     if ((rc = build_march_maps(h, h->tile_rt))) return bail(rc);
@@ -760,6 +801,16 @@ static cudaError_t enqueue_step(sim_t *h, int parity, bool timed) {
       cudaEventRecord(h->ev[2], h->stream);
     }
     e = launch_receivers(h->storage, h->rp2[parity], h->stream);
+  } else if (h->sweep) {
+    if (timed) cudaEventRecord(h->ev[0], h->stream);
+    e = launch_sweep(h->storage, h->tile_rt, h->kp, h->vdone, h->status, h->wait_cycles, h->withhold_chunk, h->stream);
+    if (e != cudaSuccess) return e;
+    if (timed) {
+      cudaEventRecord(h->ev[1], h->stream);
+      cudaEventRecord(h->ev[2], h->stream);
+    }
+    if (h->src_kind == 3) e = launch_inject(h->storage, h->ip, h->stream);  // the torsion ring after the step
+    if (e == cudaSuccess) e = launch_receivers(h->storage, h->rp, h->stream);
   } else {
     // point forces act after the velocity kernel, the torsion ring after the stress kernel
     cudaEvent_t *ev = timed ? h->ev : nullptr;
@@ -855,8 +906,9 @@ extern "C" int sim_sync(sim_t *h) {
   CK(h, cudaStreamSynchronize(h->stream));
   int st = 0;
   CK(h, cudaMemcpy(&st, h->status, 4, cudaMemcpyDeviceToHost));
-  if (st & 1) return fail(h, SIM_EUNSTABLE, "non-finite value in the receiver traces");
+  // a wait that gave up voids the state: report it first
   if (st & 2) return fail(h, SIM_ETIMEOUT, "a bounded device wait gave up");
+  if (st & 1) return fail(h, SIM_EUNSTABLE, "non-finite value in the receiver traces");
   return SIM_OK;
 }
 
@@ -1013,6 +1065,21 @@ extern "C" int sim_config(const sim_t *h, int *kernel, int *tile_rows) {
   if (!h) return SIM_EINVAL;
   if (kernel) *kernel = h->kernel;
   if (tile_rows) *tile_rows = h->tile_rt;
+  return SIM_OK;
+}
+
+extern "C" int sim_set_wait_test(sim_t *h, long long wait_cycles, int withhold_chunk) {
+  if (!h) return SIM_EINVAL;
+  if (wait_cycles < 0 || withhold_chunk < -1 || withhold_chunk >= sweep_chunks(h->NZ))
+    return fail(h, SIM_EINVAL, "wait_cycles >= 0 and -1 <= withhold_chunk < ceil(NZ / 32) required");
+  CK(h, cudaSetDevice(h->device));
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->wait_cycles = wait_cycles;
+  h->withhold_chunk = withhold_chunk;
+  if (h->gexec) {  // the captured steps carry the old values
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
   return SIM_OK;
 }
 

@@ -45,6 +45,12 @@ struct sim_s {
   // point forces / torsion ring (source kinds 1-3): injection points
   int src_kind = 0;
   IParams ip{};
+  // single-pass sweep path (in place on the first buffer set): per-chunk
+  // counters of finished velocity items, the wait limit and the test hook
+  bool sweep = false;
+  int *vdone = nullptr;
+  long long wait_cycles = 0;
+  int withhold_chunk = -1;
   // marching split path (in place on the first buffer set): TMA descriptors
   bool march = false;
   FusedMaps mmaps;

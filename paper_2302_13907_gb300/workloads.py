@@ -472,12 +472,13 @@ def config1_long() -> Scenario:
     return config1(steps=4000)
 
 
-def config2(noise_seed: int = 20230227, nz: int = 8192) -> Scenario:
+def config2(noise_seed: int = 20230227, nz: int = 8192, nr: int = 180) -> Scenario:
     """Full-scale 20 m well, FP32: Nr=180 (dr 2.5 mm) + 16 PML, Nth=64,
     Nz=8192 (dz 2.5 mm) + 16 PML per end, 20000 steps; cement top at 10 m with
     a linear shear ramp 0 -> full over 0.3 m; 8 kHz monopole at 9.75 m; 16 axis
-    receivers at 2.0, 2.5, ..., 9.5 m; rock Vp/Vs +-5 % correlated noise."""
-    g = Grid(nr=180, nth=64, nz=nz, pml_r=16, pml_z=16, dr=0.0025, dz=0.0025)
+    receivers at 2.0, 2.5, ..., 9.5 m; rock Vp/Vs +-5 % correlated noise.
+    `nz` and `nr` shorten the well or its radius (profiling variants)."""
+    g = Grid(nr=nr, nth=64, nz=nz, pml_r=16, pml_z=16, dr=0.0025, dz=0.0025)
     L = nz * g.dz
     z_top = 10.0 * L / 20.48
     med = cased_well(g, z_top=z_top, ramp=0.3, top_frac=0.0, noise=Noise(seed=noise_seed))
@@ -527,6 +528,16 @@ def _case_draws(seed: int):
     return nz, u
 
 
+def case_features(seed: int) -> np.ndarray:
+    """The six surrogate inputs of scenario_case(seed, surrogate_inputs=True)
+    from its draws alone (no medium is built): cement-top depth, ramp
+    length, top shear fraction, casing thickness, cement Vs, rock Vs."""
+    nz, u = _case_draws(seed)
+    length = nz * 0.0025
+    return np.array([(0.3 + 0.4 * u[0]) * length, 0.5 * u[1], float(u[2]), 0.008 + 0.004 * u[3],
+                     CEMENT[2] * (0.9 + 0.2 * u[4]), ROCK[2] * (0.9 + 0.2 * u[5])], dtype=np.float64)
+
+
 def scenario_case(seed: int, surrogate_inputs: bool = False) -> Scenario:
     """One cement-hardening case: Nr=120 (dr 2.5 mm) + 16 PML, Nth=32,
     Nz in {2048, 3072, 4096, 6144} (dz 2.5 mm) + 16 PML per end; top depth
@@ -556,6 +567,31 @@ def scenario_case(seed: int, surrogate_inputs: bool = False) -> Scenario:
                   cement_vs=cement[2], rock_vs=rock[2])
     return Scenario(name=f"case{seed}", medium=med, source=Source(z=zs, f0=8e3),
                     receivers=on_axis_receivers(zr), cfl=0.5, steps=6000, params=params)
+
+
+def reach_crop(sc: Scenario, reach: float = 1.6) -> Scenario:
+    """The part of a well that can reach its receivers within its window:
+    the interior z cells within `reach` metres of the span of the source and
+    the receivers (clamped to the well; the crop's z PML are the neighbouring
+    stored cells, the well's own PML where the crop meets its end).  A wave
+    that leaves the span and comes back travels at most c T_end, so with
+    reach > c_max T_end / 2 nothing beyond the crop can arrive inside the
+    window (the cement cases: 5900 m/s x 0.486 ms / 2 = 1.43 m < 1.6 m).
+    params gain k0 (first interior cell of the crop in the well) and keep
+    the well's own entries."""
+    g = sc.grid
+    zs = np.concatenate([[sc.source.z], np.asarray(sc.receivers.z)])
+    k0 = max(0, int(np.floor((zs.min() - reach) / g.dz)))
+    k1 = min(g.nz, int(np.ceil((zs.max() + reach) / g.dz)) + 1)
+    med = crop_z(sc.medium, k0, k1 - k0)
+    z0 = k0 * g.dz
+    src = replace(sc.source, z=sc.source.z - z0)
+    rec = Receivers(r=np.asarray(sc.receivers.r).copy(), theta=np.asarray(sc.receivers.theta).copy(),
+                    z=np.asarray(sc.receivers.z) - z0, quantity=sc.receivers.quantity)
+    params = dict(sc.params)
+    params["k0"] = k0
+    return Scenario(name=sc.name + " crop", medium=med, source=src, receivers=rec, cfl=sc.cfl, steps=sc.steps,
+                    pml_on=sc.pml_on, params=params)
 
 
 def small_cement_case(seed: int, steps: int = 1200) -> Scenario:

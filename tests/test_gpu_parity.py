@@ -39,7 +39,7 @@ def _ragged_scenario(seed=0, nth=6, nr=9, pml_r=3, nz=37, pml_z=3):
     return W.Scenario("ragged", med, W.Source(r=0.014, theta=2.0, z=0.06, f0=60e3), rec, steps=200)
 
 
-@pytest.mark.parametrize("kernel", ["split", "fused", "fused4", "march"])
+@pytest.mark.parametrize("kernel", ["split", "fused", "fused4", "march", "sweep"])
 def test_config1_traces_match_oracle(kernel):
     sc = W.config1()
     o = oracle.Oracle(sc)
@@ -71,7 +71,7 @@ def test_config1_long_window_traces_match_oracle():
             assert rel_l2(got[q], ref[q]) <= 10 * TRACE_TOL, q
 
 
-@pytest.mark.parametrize("kernel", ["split", "fused", "fused4", "march"])
+@pytest.mark.parametrize("kernel", ["split", "fused", "fused4", "march", "sweep"])
 @pytest.mark.parametrize("seed,nth,nr,nz", [(0, 6, 9, 37), (1, 4, 5, 70), (2, 8, 13, 2), (3, 4, 40, 131),
                                             (4, 10, 29, 190)])
 def test_ragged_grid_fields_elementwise(kernel, seed, nth, nr, nz):
@@ -101,13 +101,22 @@ def _torsion_scenario():
     return W.Scenario("torsion", med, W.Source(kind=W.SOURCE_TORSION, r=0.024, z=0.05, f0=60e3), rec, steps=200)
 
 
-@pytest.mark.parametrize("kernel", ["split", "march"])
+@pytest.mark.parametrize("kernel", ["split", "march", "sweep"])
 @pytest.mark.parametrize("kind,r,theta", [(1, 0.0, 0.7), (1, 0.013, 1.1), (2, 0.0, 0.0), (2, 0.014, 2.0),
                                           (3, 0.024, 0.0)])
 def test_point_forces_and_torsion_fields_elementwise(kernel, kind, r, theta):
     """The transverse and longitudinal point forces (on and off the axis)
     and the torsion ring, injected between the half-steps, against the
-    oracle element by element on every field."""
+    oracle element by element on every field (the sweep kernel fuses the
+    half-steps: the torsion ring only, the forces are refused)."""
+    if kernel == "sweep" and kind != 3:
+        from paper_2302_13907_gb300.binding import SIM_EUNSUPPORTED, SimError
+        sc = _ragged_scenario(seed=7, nth=8, nr=11, nz=45)
+        sc.source = W.Source(kind=kind, r=r, theta=theta, z=0.06, f0=60e3)
+        with pytest.raises(SimError) as ei:
+            sim(sc, kernel=kernel)
+        assert ei.value.code == SIM_EUNSUPPORTED
+        return
     if kind == 3:
         sc = _torsion_scenario()
     else:
@@ -369,7 +378,8 @@ def test_fused_matches_split_and_autotuner_choice():
         ta = a.traces()
         fa = {n: a.field(n) for n in ("vr", "srr", "srz")}
     for kern, kind_want, tiles in (("fused", 2, (2, 4, 6, 8)), ("fused4", 2, (106, 110, 114)),
-                                   ("march", 4, MARCH_TILES), ("split", 1, SPLIT_TILES)):
+                                   ("march", 4, MARCH_TILES), ("split", 1, SPLIT_TILES),
+                                   ("sweep", 5, (3043, 3024, 3143, 3124, 3243, 3224, 3343, 3324))):
         with sim(sc, kernel=kern) as b:
             kind, tile = b.config()
             halves = (tile // 10000, tile % 10000) if tile >= 10000 else (tile, tile)

@@ -106,3 +106,56 @@ def test_training_reduces_loss_on_a_smooth_map():
         hist = s.train(X, Y, epochs=40, batch=16, lr=2e-3, seed=1)
         assert np.all(np.isfinite(hist))
         assert hist[-1] < 0.5 * hist[0], hist
+
+
+def test_forward_elementwise_against_bf16_rounded_reference():
+    """The GPU forward pass element by element against the FP64 reference
+    that rounds every contraction operand to BF16 where the GPU does (weights,
+    inputs, activations): what is left is FP32 accumulation and FP32 GELU,
+    plus the rare activation that FP32 and FP64 round to neighbouring BF16
+    values."""
+    from paper_2302_13907_gb300.binding import Surrogate
+    shp = R.shapes()
+    rng = np.random.default_rng(12)
+    X = rng.uniform(-1, 1, (6, 6)).astype(np.float32)
+    with Surrogate(max_batch=8, seed=4) as s:
+        th = s.params()
+        Y = s.forward(X).astype(np.float64)
+    ref = R.forward(_bf16_theta(th, shp), X.astype(np.float64), shp, q=bf16_round)
+    ref_exact = R.forward(_bf16_theta(th, shp), X.astype(np.float64), shp)
+    err = np.abs(Y - ref)
+    scale = np.abs(ref).max()
+    rel = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
+    rel_exact = np.linalg.norm(ref_exact - ref) / np.linalg.norm(ref)
+    print(f"forward: max elementwise {err.max() / scale:.3e} of max, rel-L2 {rel:.3e}; "
+          f"unrounded reference {rel_exact:.3e}")
+    assert err.max() <= 8e-3 * scale, err.max() / scale
+    assert rel <= 2e-3, rel
+    # the rounded reference is the closer one: BF16 rounding points are reproduced
+    assert rel <= 0.5 * rel_exact, (rel, rel_exact)
+
+
+def test_adam_steps_match_fp64_adam():
+    """Two training steps on one sample (so the minibatch gradient is the one
+    sur_loss_grad returns, bit for bit) against the FP64 Adam of the reference
+    (beta = (0.9, 0.999), eps = 1e-8; learning rate lr on the first step of
+    each one-epoch call of the cosine schedule): each FP32 weight within
+    1e-6 of itself plus 1e-4 lr of the FP64 update."""
+    from paper_2302_13907_gb300.binding import Surrogate
+    rng = np.random.default_rng(21)
+    X = rng.uniform(-1, 1, (1, 6)).astype(np.float32)
+    T = (rng.standard_normal((1, 8, 2048)) * 0.05).astype(np.float32)
+    lr = 1e-3
+    with Surrogate(max_batch=4, seed=9) as s:
+        w = s.params().astype(np.float64)
+        m = np.zeros_like(w)
+        v = np.zeros_like(w)
+        for t in (1, 2):
+            _, g = s.loss_grad(X, T)
+            s.train(X, T, epochs=1, batch=1, lr=lr, seed=t)
+            w_gpu = s.params().astype(np.float64)
+            w_ref, m, v = R.adam_step(w, g.astype(np.float64), m, v, t, lr)
+            bad = np.abs(w_gpu - w_ref) > 1e-6 * np.abs(w_ref) + 1e-4 * lr
+            assert not bad.any(), (t, int(bad.sum()), float(np.abs(w_gpu - w_ref).max()))
+            assert np.abs(w_gpu - w).max() > 0.5 * lr  # the step moved the weights
+            w = w_gpu
