@@ -76,8 +76,17 @@ def lib():
             L.or_round_storage.restype = d
             L.or_set_storage.argtypes = [p, i, d, d]
             L.or_set_storage.restype = i
+            L.or_round_stochastic_f16.argtypes = [d, ctypes.c_uint]
+            L.or_round_stochastic_f16.restype = d
+            L.or_splitmix64.argtypes = [ctypes.c_uint64]
+            L.or_splitmix64.restype = ctypes.c_uint64
+            L.or_sr_dither.argtypes = [i, i, i, i, i, i, i, i]
+            L.or_sr_dither.restype = ctypes.c_uint
             L.or_pml_table.argtypes = [p, i]
             L.or_pml_table.restype = dp
+            L.or_set_zrange.argtypes = [p, i, i]
+            L.or_set_zrange.restype = i
+            L.or_set_steps_done.argtypes = [p, i]
             L.or_velocity_update.argtypes = [p]
             L.or_stress_update.argtypes = [p]
             L.or_inject_source.argtypes = [p, i]
@@ -140,8 +149,9 @@ class Oracle:
                  scales: tuple = (1.0, 1.0)):
         """`storage` "bf16" / "f16" rounds every field to that 16-bit format
         where the reduced-precision variant stores it (values first rounded
-        to FP32, the variant's arithmetic precision); `scales` = (velocity,
-        stress) factors of the stored representation round(value * scale)."""
+        to FP32, the variant's arithmetic precision; "f16sr": FP16 with
+        stochastic rounding); `scales` = (velocity, stress) factors of the
+        stored representation round(value * scale)."""
         L = lib()
         m = scenario.medium
         g = m.grid
@@ -204,6 +214,22 @@ class Oracle:
     def stress_update(self):
         self._L.or_stress_update(self._h)
 
+    def inject_source(self, n: int):
+        """The source of step n (point forces after the velocity update, the
+        volumetric source and the torsion ring after the stress update)."""
+        self._L.or_inject_source(self._h, int(n))
+
+    def sample(self, n: int):
+        self._L.or_sample(self._h, int(n))
+
+    def set_zrange(self, k_lo: int, k_hi: int):
+        """Update, inject and sample only stored z cells k_lo <= k < k_hi."""
+        if self._L.or_set_zrange(self._h, int(k_lo), int(k_hi)) != 0:
+            raise OracleError("bad z range")
+
+    def set_steps_done(self, n: int):
+        self._L.or_set_steps_done(self._h, int(n))
+
     def field(self, name: str) -> np.ndarray:
         """Writable view of a field, shape [nth][NR][NZ]."""
         q = FIELDS.index(name)
@@ -233,7 +259,7 @@ class Oracle:
         return full[:, :n].copy()
 
 
-STORAGE_MODES = {"f64": 0, "bf16": 1, "f16": 2}
+STORAGE_MODES = {"f64": 0, "bf16": 1, "f16": 2, "f16sr": 3}
 
 
 def round_storage(x, storage: str) -> np.ndarray:
@@ -243,6 +269,22 @@ def round_storage(x, storage: str) -> np.ndarray:
     mode = STORAGE_MODES[storage]
     x = np.asarray(x, dtype=np.float64)
     return np.vectorize(lambda v: L.or_round_storage(float(v), mode), otypes=[np.float64])(x)
+
+
+def round_stochastic_f16(x, dither) -> np.ndarray:
+    """The oracle's stochastic rounding to FP16 with the given 13-bit dithers."""
+    L = lib()
+    x = np.asarray(x, dtype=np.float64)
+    d = np.broadcast_to(np.asarray(dither, dtype=np.uint32), x.shape)
+    return np.vectorize(lambda v, r: L.or_round_stochastic_f16(float(v), int(r)), otypes=[np.float64])(x, d)
+
+
+def splitmix64(key: int) -> int:
+    return int(lib().or_splitmix64(int(key)))
+
+
+def sr_dither(n, q, j, i, k, nth, NR, NZ) -> int:
+    return int(lib().or_sr_dither(n, q, j, i, k, nth, NR, NZ))
 
 
 def cfl_dt(medium, cfl: float) -> float:

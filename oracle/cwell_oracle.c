@@ -123,10 +123,15 @@ typedef struct {
   int cap, steps_done;
   double *traces;
   int threads;
-  /* storage rounding (precision variant): 0 none, 1 BF16, 2 FP16; stored
-     value = round(value * scale), scale st_sv (velocities), st_ss (stresses) */
+  /* storage rounding (precision variant): 0 none, 1 BF16, 2 FP16, 3 FP16
+     with stochastic rounding; stored value = round(value * scale), scale
+     st_sv (velocities), st_ss (stresses) */
   int storage;
   double st_sv, st_ss;
+  /* z range the updates, the sources and the receivers cover (a z slab of
+     a decomposed run: the cells outside are the neighbours' and arrive by
+     exchange); 0 .. NZ by default */
+  int k_lo, k_hi;
 } or_sim;
 
 /* Ricker pulse with dominant frequency f0 and delay 2/f0 (Sec. 2). */
@@ -165,6 +170,44 @@ double or_round_storage(double x, int mode) {
   if (mode == 1) return round_format(f, 8, -126, 0x1.fep127);
   if (mode == 2) return round_format(f, 11, -14, 65504.0);
   return x;
+}
+
+/*
+ * Stochastic rounding to FP16 (storage mode 3): the binary32 value x of
+ * magnitude a is rounded down to the FP16 grid, a_lo = floor(a / u) u with
+ * u = 2^(E - 10) the grid spacing (E the exponent of a, at least -14), and
+ * up to a_lo + u when frac(a / u) * 2^13 > d, d a 13-bit dither, so that the
+ * expected result is x.  Beyond 65504 (and for zero) round to nearest.
+ */
+double or_round_stochastic_f16(double x, unsigned d) {
+  const double f = (double)(float)x;
+  const double a = fabs(f);
+  if (!(a <= 65504.0) || a == 0.0) return round_format(f, 11, -14, 65504.0);
+  int e;
+  frexp(a, &e);
+  int E = e - 1;
+  if (E < -14) E = -14;
+  const double q = ldexp(a, 10 - E), fl = floor(q);
+  const double m = ldexp(fl + ((q - fl) * 8192.0 > (double)d ? 1.0 : 0.0), E - 10);
+  return copysign(m, f);
+}
+
+/* SplitMix64 (Steele, Lea and Flood, 2014): the output for counter value
+   key, i.e. the mix of state (key + 1) * 0x9E3779B97F4A7C15. */
+uint64_t or_splitmix64(uint64_t key) {
+  uint64_t z = (key + 1u) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+/* The 13-bit dither of field q of cell (j, i, k) in the update of step n:
+   one SplitMix64 output per group of four cells along z, 16 bits per cell. */
+unsigned or_sr_dither(int n, int q, int j, int i, int k, int nth, int NR, int NZ) {
+  const uint64_t ngrp = (uint64_t)((NZ + 3) / 4);
+  const uint64_t key = ((((uint64_t)n * 9u + (uint64_t)q) * (uint64_t)nth + (uint64_t)j) * (uint64_t)NR +
+                        (uint64_t)i) * ngrp + (uint64_t)(k / 4);
+  return (unsigned)((or_splitmix64(key) >> (16 * (k % 4))) & 0x1fffu);
 }
 
 /* Reading R7 of the time step. */
@@ -260,6 +303,8 @@ or_sim *or_create(int nr, int nth, int nz, int pml_r, int pml_z, double dr, doub
   s->threads = 0;
   s->storage = 0;
   s->st_sv = s->st_ss = 1.0;
+  s->k_lo = 0;
+  s->k_hi = nz + 2 * pml_z;
   int NR = s->NR, NZ = s->NZ;
   s->id = (uint16_t *)malloc(s->ncell * sizeof(uint16_t));
   s->n_mat = n_mat;
@@ -437,7 +482,7 @@ void or_velocity_update(or_sim *s) {
     for (int i = 0; i < NR; i++) {
       const int jm = (j + nth - 1) % nth, jp = (j + 1) % nth;
       const double ri = i * dr, rh = (i + 0.5) * dr;
-      for (int k = 0; k < NZ; k++) {
+      for (int k = s->k_lo; k < s->k_hi; k++) {
         const size_t c = IX(j, i, k);
         /* v_r at (r_i, theta_j, z_k); r = 0 is not an unknown (R4).
            ds_rr/dr + [(s_rr - s_phiphi) + ds_rphi/dphi] / r + ds_rz/dz */
@@ -492,7 +537,7 @@ void or_stress_update(or_sim *s) {
     for (int i = 0; i < NR; i++) {
       const int jm = (j + nth - 1) % nth, jp = (j + 1) % nth;
       const double ri = i * dr, rh = (i + 0.5) * dr;
-      for (int k = 0; k < NZ; k++) {
+      for (int k = s->k_lo; k < s->k_hi; k++) {
         const size_t c = IX(j, i, k);
         /* normal stresses at the cell centre (r_{i+1/2}, theta_j, z_k):
            e_rr = du_r/dr, e_phiphi = [du_phi/dphi + u_r] / r, e_zz = du_z/dz */
@@ -556,6 +601,8 @@ void or_inject_source(or_sim *s, int n) {
   for (int q = 0; q < s->src_n; q++) {
     const double add = s->dt * s->src_w[q] * f;
     const size_t c = s->src_cell[q];
+    const int kc = (int)(c % (size_t)s->NZ);
+    if (kc < s->k_lo || kc >= s->k_hi) continue; /* another slab's cell */
     if (s->src_kind == 0) {
       s->f[F_SRR][c] += add;
       s->f[F_SPP][c] += add;
@@ -570,6 +617,7 @@ void or_inject_source(or_sim *s, int n) {
 void or_sample(or_sim *s, int n) {
   const int NR = s->NR, NZ = s->NZ;
   for (int r = 0; r < s->n_rec; r++) {
+    if (s->rec_k[r] < s->k_lo || s->rec_k[r] >= s->k_hi) continue; /* another slab's receiver */
     int j0 = s->rec_j[r] < 0 ? 0 : s->rec_j[r], j1 = s->rec_j[r] < 0 ? s->nth : s->rec_j[r] + 1;
     double acc = 0.0;
     for (int j = j0; j < j1; j++) {
@@ -582,26 +630,37 @@ void or_sample(or_sim *s, int n) {
 
 /* Storage rounding of the fields q0 .. q1-1 with scale sc: the stored
    representation is round(value * sc), the value it stands for that over sc. */
-static void round_fields(or_sim *s, int q0, int q1, double sc) {
+static void round_fields(or_sim *s, int q0, int q1, double sc, int step) {
   if (!s->storage) return;
   set_threads(s);
+  const int NR = s->NR, NZ = s->NZ, nth = s->nth;
   for (int q = q0; q < q1; q++) {
     double *f = s->f[q];
     const long long n = (long long)s->ncell;
+    if (s->storage == 3) {
 #pragma omp parallel for schedule(static)
-    for (long long c = 0; c < n; c++) f[c] = or_round_storage(f[c] * sc, s->storage) / sc;
+      for (long long c = 0; c < n; c++) {
+        const int k = (int)(c % NZ), i = (int)((c / NZ) % NR), j = (int)(c / ((long long)NZ * NR));
+        f[c] = or_round_stochastic_f16(f[c] * sc, or_sr_dither(step, q, j, i, k, nth, NR, NZ)) / sc;
+      }
+    } else {
+#pragma omp parallel for schedule(static)
+      for (long long c = 0; c < n; c++) f[c] = or_round_storage(f[c] * sc, s->storage) / sc;
+    }
   }
 }
 
-/* Select storage rounding: mode 0 none (FP64 fields), 1 BF16, 2 FP16, with
-   velocity and stress scales sv, ss (> 0). */
+/* Select storage rounding: mode 0 none (FP64 fields), 1 BF16, 2 FP16 (round
+   to nearest even), 3 FP16 with stochastic rounding, with velocity and
+   stress scales sv, ss (> 0).  The present fields are rounded to nearest. */
 int or_set_storage(or_sim *s, int mode, double sv, double ss) {
-  if (!s || mode < 0 || mode > 2 || !(sv > 0) || !(ss > 0)) return OR_EINVAL;
-  s->storage = mode;
+  if (!s || mode < 0 || mode > 3 || !(sv > 0) || !(ss > 0)) return OR_EINVAL;
+  s->storage = mode == 3 ? 2 : mode;
   s->st_sv = sv;
   s->st_ss = ss;
-  round_fields(s, F_VR, F_SRR, sv);
-  round_fields(s, F_SRR, NFIELD, ss);
+  round_fields(s, F_VR, F_SRR, sv, 0);
+  round_fields(s, F_SRR, NFIELD, ss, 0);
+  s->storage = mode;
   return OR_OK;
 }
 
@@ -616,23 +675,34 @@ int or_step(or_sim *s, int n) {
     int m = s->steps_done;
     const int force = s->src_kind == 1 || s->src_kind == 2;
     or_velocity_update(s);
-    round_fields(s, F_VR, F_SRR, s->st_sv);
+    round_fields(s, F_VR, F_SRR, s->st_sv, m);
     if (force) {
       or_inject_source(s, m);
-      round_fields(s, F_VR, F_SRR, s->st_sv);
+      round_fields(s, F_VR, F_SRR, s->st_sv, m);
     }
     or_stress_update(s);
     if (s->src_kind == 0) or_inject_source(s, m);
-    round_fields(s, F_SRR, NFIELD, s->st_ss);
+    round_fields(s, F_SRR, NFIELD, s->st_ss, m);
     if (s->src_kind == 3) {
       or_inject_source(s, m);
-      round_fields(s, F_SRR, NFIELD, s->st_ss);
+      round_fields(s, F_SRR, NFIELD, s->st_ss, m);
     }
     or_sample(s, m);
     s->steps_done++;
   }
   return OR_OK;
 }
+
+/* Restrict the updates, sources and receivers to stored z cells
+   k_lo <= k < k_hi (a slab of a z decomposition). */
+int or_set_zrange(or_sim *s, int k_lo, int k_hi) {
+  if (!s || k_lo < 0 || k_hi > s->NZ || k_lo >= k_hi) return OR_EINVAL;
+  s->k_lo = k_lo;
+  s->k_hi = k_hi;
+  return OR_OK;
+}
+
+void or_set_steps_done(or_sim *s, int n) { s->steps_done = n; }
 
 double or_dt(const or_sim *s) { return s->dt; }
 int or_steps_done(const or_sim *s) { return s->steps_done; }

@@ -1,13 +1,24 @@
 """Training / test data of the trace surrogate, generated by the simulator.
 
 Each sample is one cement-hardening case (136 x 32 x Nz cylindrical grid,
-uneven Nz, FP32, 6000 steps) run in batches of up to 64 wells per launch;
-the target is the last 2048 steps (the reflected window) of the 8 axis
-receivers, the input the six case parameters (cement-top depth, ramp
+uneven Nz, FP32, 6000 steps of the uniform grid's time step); the target is
+the last 2048 samples (the reflected window, steps 3952 .. 5999) of the 8
+axis receivers, the input the six case parameters (cement-top depth, ramp
 length, top shear fraction, casing thickness, cement Vs, rock Vs).
 
+Two generators:
+  * "uniform": the case as defined, on the uniform grid, in batches of up to
+    64 wells per launch (the plain solver);
+  * "refined" (default): the case's reach crop (the z cells within 1.6 m of
+    the source and receivers; nothing farther can reach them within the
+    window) on the azimuthally refined grid of the paper (Sec. 3), whose
+    larger time step covers the same physical window in fewer steps; the
+    receiver traces are sampled at the uniform grid's times (m + 1) dt by
+    linear interpolation in time (the refined step is under 1/800 of the
+    8 kHz period: interpolation error below 1e-4 of the amplitude).
+
     python -m paper_2302_13907_gb300.surrogate_data --out data.npz \
-        --seeds 1000:1320 [--batch 64]
+        --seeds 1000:1320 [--mode refined|uniform] [--batch 64]
 """
 from __future__ import annotations
 
@@ -30,6 +41,45 @@ def parse_seeds(spec: str):
         else:
             out.append(int(part))
     return out
+
+
+def window_times(sc):
+    """Uniform-grid time step of a case and the times of its reflected window."""
+    from .binding import time_step
+    dt = time_step(sc)
+    m = np.arange(sc.steps - WINDOW, sc.steps)
+    return dt, (m + 1) * dt
+
+
+def refined_window(sc, stream=None, reach=1.6):
+    """Reflected-window traces [8][2048] of one case by the refined-grid
+    simulator on its reach crop, at the uniform grid's sample times."""
+    from .binding import RefinedSimulation
+    dt_u, t = window_times(sc)
+    crop = W.reach_crop(sc, reach)
+    rows = W.refinement_rows(crop.grid)
+    # the refined step is the larger one, so sc.steps samples cover the window
+    with RefinedSimulation(crop, rows, graph_chunk=256, stream=stream, max_steps=sc.steps) as R:
+        dt_r = R.dt
+        n = int(np.ceil(t[-1] / dt_r)) + 1
+        if n > sc.steps:
+            raise ValueError("refined time step below the uniform one")
+        R.step(n)
+        tr = R.traces().astype(np.float64)
+    tr_t = (np.arange(n) + 1) * dt_r  # sample m is the value after step m
+    return np.stack([np.interp(t, tr_t, tr[q]) for q in range(tr.shape[0])]).astype(np.float32)
+
+
+def generate_refined(seeds, stream=None, log=print, every=256):
+    X, Y = [], []
+    t0 = time.time()
+    for q, s in enumerate(seeds):
+        sc = W.scenario_case(s, surrogate_inputs=True)
+        Y.append(refined_window(sc, stream))
+        X.append(W.surrogate_features(sc))
+        if (q + 1) % every == 0 or q + 1 == len(seeds):
+            log(f"{q + 1}/{len(seeds)} cases, {time.time() - t0:.0f} s")
+    return np.asarray(X, np.float64), np.asarray(Y, np.float32), time.time() - t0
 
 
 def generate(seeds, batch=64, stream=None, log=print):
@@ -57,10 +107,14 @@ def main():
     ap.add_argument("--out", required=True)
     ap.add_argument("--seeds", required=True)
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--mode", default="refined", choices=["refined", "uniform"])
     a = ap.parse_args()
     seeds = parse_seeds(a.seeds)
-    X, Y, secs = generate(seeds, a.batch)
-    np.savez_compressed(a.out, X=X, Y=Y, seeds=np.asarray(seeds), sim_seconds=secs)
+    if a.mode == "refined":
+        X, Y, secs = generate_refined(seeds)
+    else:
+        X, Y, secs = generate(seeds, a.batch)
+    np.savez_compressed(a.out, X=X, Y=Y, seeds=np.asarray(seeds), sim_seconds=secs, mode=a.mode)
     print("wrote", a.out, X.shape, Y.shape)
 
 

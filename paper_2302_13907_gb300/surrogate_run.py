@@ -8,6 +8,16 @@ train/test .npz come from `surrogate_data` (X [n][6] case parameters,
 Y [n][8][2048] reflected-window traces, seeds, sim_seconds).  Every step of
 training and inference runs in the library's kernels; the simulator runs the
 cases the gate rejects.
+
+    python -m paper_2302_13907_gb300.surrogate_run --pipeline --out-dir DIR \
+        [--train-seeds 1000:5096] [--test-seeds 9000:9512] [--epochs 400]
+
+runs the whole job in one process: generates both sets with the refined
+generator of `surrogate_data`, times the plain solver on a sample of the test
+cases, trains, chooses the gate's margin on the validation cases alone
+(leave-one-out), gates and falls back on the test cases, and writes
+DIR/params.npz (weights as BF16 bit patterns, biases, normalisation, the
+gate's validation data and margin) and DIR/report.json.
 """
 from __future__ import annotations
 
@@ -47,22 +57,189 @@ def simulate(seeds, stream=None):
     return np.asarray(out, np.float32), time.perf_counter() - t0
 
 
+def surrogate_shapes(arch):
+    """Parameter layout of the network (the order sur_get_params uses):
+    W1, b1, W2, b2, W3, b3, (T_l, t_l) per transposed convolution, Wf, bf."""
+    ch = list(arch["chans"])
+    s = [("W1", (arch["in_dim"], arch["h1"])), ("b1", (arch["h1"],)), ("W2", (arch["h1"], arch["h2"])),
+         ("b2", (arch["h2"],)), ("W3", (arch["h2"], arch["l0"] * ch[0])), ("b3", (arch["l0"] * ch[0],))]
+    for i in range(len(ch) - 1):
+        s += [(f"T{i}", (ch[i], ch[i + 1], 4)), (f"t{i}", (ch[i + 1],))]
+    s += [("Wf", (ch[-1], arch["out_ch"])), ("bf", (arch["out_ch"],))]
+    return s
+
+
+def pack_params(theta, arch):
+    """Weights as BF16 bit patterns (round to nearest even; the GEMMs read
+    BF16), biases FP32."""
+    w, b, o = [], [], 0
+    for _, sh in surrogate_shapes(arch):
+        n = int(np.prod(sh))
+        (w if len(sh) > 1 else b).append(theta[o:o + n])
+        o += n
+    wv = np.concatenate(w).astype(np.float32).view(np.uint32).astype(np.uint64)
+    bits = ((wv + 0x7FFF + ((wv >> 16) & 1)) >> 16).astype(np.uint16)
+    return bits, np.concatenate(b).astype(np.float32)
+
+
+def unpack_params(bits, biases, arch):
+    w = (bits.astype(np.uint32) << 16).view(np.float32)
+    out, wo, bo = [], 0, 0
+    for _, sh in surrogate_shapes(arch):
+        n = int(np.prod(sh))
+        if len(sh) > 1:
+            out.append(w[wo:wo + n])
+            wo += n
+        else:
+            out.append(biases[bo:bo + n])
+            bo += n
+    return np.concatenate(out).astype(np.float32)
+
+
+def knn_worst(Xn_query, Xn_ref, err_ref, k, exclude_self=False):
+    """Largest error among the k nearest reference inputs of each query
+    (Euclidean distance in normalised input space), as the gate computes."""
+    d = ((Xn_query[:, None, :] - Xn_ref[None, :, :]) ** 2).sum(-1)
+    if exclude_self:
+        np.fill_diagonal(d, np.inf)
+    nn = np.argsort(d, axis=1)[:, :k]
+    return err_ref[nn].max(axis=1)
+
+
+def choose_margin(Xn_val, e_val, k, tol=TOL):
+    """The largest margin m (in steps of 0.05) for which the gate, run leave
+    one out on the validation cases, accepts no validation case above tol."""
+    worst = knn_worst(Xn_val, Xn_val, e_val, k, exclude_self=True)
+    best = 0.0
+    for m in np.arange(0.05, 1.0001, 0.05):
+        acc = worst <= m * tol
+        if np.all(e_val[acc] <= tol):
+            best = float(m)
+    return best
+
+
+def pipeline(a):
+    """The whole surrogate job in one process (see the module docstring)."""
+    import os
+    from . import surrogate_data as D
+    from .binding import SURROGATE_DEFAULT, Simulation
+
+    os.makedirs(a.out_dir, exist_ok=True)
+    log = lambda m: print(m, flush=True)
+    tr_seeds = D.parse_seeds(a.train_seeds)
+    te_seeds = D.parse_seeds(a.test_seeds)
+    X, Y, t_gen_tr = D.generate_refined(tr_seeds, log=log)
+    Xt, Yt, t_gen_te = D.generate_refined(te_seeds, log=log)
+    log(f"generated {len(X)} + {len(Xt)} cases in {t_gen_tr + t_gen_te:.0f} s")
+    # the plain solver (uniform grid, the whole well, 6000 steps) on a sample of the test cases
+    plain_t, plain_err = [], []
+    for sd, y_ref in zip(te_seeds[:a.plain_sample], Yt[:a.plain_sample]):
+        sc = W.scenario_case(sd, surrogate_inputs=True)
+        t0 = time.perf_counter()
+        with Simulation(sc, graph_chunk=200, max_steps=sc.steps) as s:
+            s.step(sc.steps)
+            tr = s.traces()[:, sc.steps - D.WINDOW:]
+        plain_t.append(time.perf_counter() - t0)
+        plain_err.append(float(np.linalg.norm(y_ref - tr) / np.linalg.norm(tr)))
+    X, Y, Xt, Yt = X.astype(np.float32), Y.astype(np.float32), Xt.astype(np.float32), Yt.astype(np.float32)
+    rng = np.random.default_rng(a.seed)
+    perm = rng.permutation(len(X))
+    nv = max(1, int(round(a.val_frac * len(X))))
+    iv, it = perm[:nv], perm[nv:]
+    x_mean = X[it].mean(axis=0)
+    x_scale = np.maximum(X[it].std(axis=0), 1e-12)
+    y_scale = float(np.sqrt(np.mean(Y[it].astype(np.float64) ** 2)))
+    S = Surrogate(max_batch=64, seed=a.seed + 1)
+    S.set_normalization(x_mean, x_scale, y_scale)
+    t0 = time.perf_counter()
+    hist = S.train(X[it], Y[it], epochs=a.epochs, batch=a.batch, lr=a.lr, seed=a.seed)
+    t_train = time.perf_counter() - t0
+    log(f"trained {len(it)} cases x {a.epochs} epochs in {t_train:.0f} s, loss {hist[0]:.3g} -> {hist[-1]:.3g}")
+    # the deployed weights are the BF16 ones: evaluate with exactly those
+    bits, biases = pack_params(S.params(), SURROGATE_DEFAULT)
+    S.set_params(unpack_params(bits, biases, SURROGATE_DEFAULT))
+    e_val = rel_err(S.forward(X[iv]), Y[iv])
+    Xn = lambda x: (x - x_mean) / x_scale
+    margin = choose_margin(Xn(X[iv]), e_val, a.k)
+    S.gate_fit(X[iv], e_val)
+    S.forward(Xt[:4])
+    t0 = time.perf_counter()
+    P = S.forward(Xt)
+    acc = S.gate(Xt, k=a.k, tol=TOL * margin)
+    t_inf = time.perf_counter() - t0
+    e_test = rel_err(P, Yt)
+    rejected = np.flatnonzero(~acc)
+    t0 = time.perf_counter()
+    for q in rejected:
+        P[q] = D.refined_window(W.scenario_case(te_seeds[q], surrogate_inputs=True))
+    t_fb = time.perf_counter() - t0
+    final = rel_err(P, Yt)
+    n = len(Xt)
+    per_sim = t_gen_te / n
+    per_plain = float(np.mean(plain_t)) if plain_t else None
+    rep = {
+        "train_cases": int(len(it)), "val_cases": int(nv), "test_cases": n, "params": int(S.n_params),
+        "epochs": a.epochs, "batch": a.batch, "lr": a.lr, "train_seconds": t_train,
+        "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
+        "generator": "refined grid (Sec. 3 zoning) on each case's 1.6 m reach crop, traces at the uniform grid's times",
+        "generate_seconds": t_gen_tr + t_gen_te, "judge_seconds_per_case": per_sim,
+        "plain_seconds_per_case": per_plain, "plain_sample": len(plain_t),
+        "plain_vs_judge_rel_l2": plain_err,
+        "val_rel_l2_median": float(np.median(e_val)), "val_rel_l2_max": float(e_val.max()),
+        "test_rel_l2_median": float(np.median(e_test)), "test_rel_l2_p90": float(np.quantile(e_test, 0.9)),
+        "test_rel_l2_max": float(e_test.max()), "test_frac_within_5pct": float(np.mean(e_test <= TOL)),
+        "gate_k": a.k, "gate_margin": margin, "gate_tol": TOL * margin,
+        "accepted": int(acc.sum()), "accepted_frac": float(acc.mean()),
+        "max_accepted_rel_l2": float(e_test[acc].max()) if acc.any() else None,
+        "false_accepts": int(np.sum(acc & (e_test > TOL))),
+        "fallback_cases": int(len(rejected)), "fallback_seconds": t_fb,
+        "final_max_rel_l2": float(final.max()), "final_frac_within_5pct": float(np.mean(final <= TOL + 1e-7)),
+        "inference_and_gate_seconds": t_inf,
+        "cases_per_s": n / (t_inf + t_fb),
+        "judge_cases_per_s": 1.0 / per_sim,
+        "speedup_vs_judge": per_sim * n / (t_inf + t_fb),
+        "speedup_vs_plain": (per_plain * n / (t_inf + t_fb)) if per_plain else None,
+        "test_rel_l2": [float(x) for x in e_test], "test_accepted": [bool(x) for x in acc],
+        "epoch_loss": [float(x) for x in hist[:: max(1, len(hist) // 50)]],
+    }
+    json.dump(rep, open(os.path.join(a.out_dir, "report.json"), "w"), indent=1)
+    np.savez_compressed(os.path.join(a.out_dir, "params.npz"), w_bf16=bits, biases=biases, x_mean=x_mean,
+                        x_scale=x_scale, y_scale=np.float64(y_scale), gate_x=X[iv], gate_err=e_val.astype(np.float32),
+                        gate_k=np.int64(a.k), gate_margin=np.float64(margin),
+                        train_seeds=np.asarray(tr_seeds), test_seeds=np.asarray(te_seeds),
+                        val_index=np.asarray(iv), seed=np.int64(a.seed))
+    log(json.dumps({k: v for k, v in rep.items() if k not in ("epoch_loss", "test_rel_l2", "test_accepted")},
+                   indent=1))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train", required=True)
-    ap.add_argument("--test", required=True)
-    ap.add_argument("--out", required=True)
+    ap.add_argument("--pipeline", action="store_true", help="generate, train, gate and report in one process")
+    ap.add_argument("--out-dir", default=None)
+    ap.add_argument("--train-seeds", default="1000:5096")
+    ap.add_argument("--test-seeds", default="9000:9512")
+    ap.add_argument("--plain-sample", type=int, default=4)
+    ap.add_argument("--train", default=None)
+    ap.add_argument("--test", default=None)
+    ap.add_argument("--out", default=None)
     ap.add_argument("--params", default=None)
     ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--val-frac", type=float, default=0.15)
     ap.add_argument("--k", type=int, default=3)
-    ap.add_argument("--gate-margin", type=float, default=1.0,
+    ap.add_argument("--gate-margin", type=float, default=0.5,
                     help="accept a case only where its nearest validation cases are within margin * 5 %%")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fallback", action="store_true", help="run the simulator on the rejected test cases")
     a = ap.parse_args()
+    if a.pipeline:
+        if not a.out_dir:
+            ap.error("--pipeline needs --out-dir")
+        pipeline(a)
+        return
+    if not (a.train and a.test and a.out):
+        ap.error("--train, --test and --out are required without --pipeline")
 
     tr = np.load(a.train)
     te = np.load(a.test)
@@ -110,6 +287,7 @@ def main():
         "test_frac_within_5pct": float(np.mean(e_test <= TOL)),
         "gate_k": a.k, "gate_tol": TOL * a.gate_margin, "gate_accept_frac": float(acc.mean()),
         "gate_accepted_within_5pct": float(np.mean(e_test[acc] <= TOL)) if acc.any() else None,
+        "false_accepts": int(np.sum(acc & (e_test > TOL))),
         "final_frac_within_5pct": float(np.mean(final_err <= TOL + 1e-7)),
         "inference_seconds": t_inf, "surrogate_cases_per_s": n / t_inf,
         "plain_solver_seconds": t_sim_plain, "plain_cases_per_s": (n / t_sim_plain) if t_sim_plain else None,

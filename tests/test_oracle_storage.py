@@ -130,3 +130,55 @@ def test_rounded_run_differs_from_fp64_by_the_storage_resolution():
                         - ref) / np.linalg.norm(ref)
     assert 0 < eh < eb, (eh, eb)
     assert eb > 2.0 ** -12 and eh > 2.0 ** -16, (eh, eb)
+
+
+# ---------------------------------------------------------------- stochastic rounding (FP16)
+def test_splitmix64_published_outputs():
+    """SplitMix64 from seed 0 (Steele, Lea and Flood): the first outputs of
+    the reference generator, and the same as the input generators' own copy."""
+    assert oracle.splitmix64(0) == 0xE220A8397B1DCDAF
+    assert oracle.splitmix64(1) == 0x6E789E6AA1B965F4
+    assert oracle.splitmix64(2) == 0x06C45D188009454F
+    ks = np.array([0, 1, 7, 123456789, 2 ** 40 + 3], dtype=np.uint64)
+    assert [oracle.splitmix64(int(k)) for k in ks] == [int(x) for x in W.splitmix64(0, ks)]
+
+
+def test_dither_takes_16_bits_per_cell_of_one_hash_per_four_cells():
+    nth, NR, NZ = 8, 26, 71
+    for n, q, j, i, k in [(0, 0, 0, 0, 0), (5, 3, 2, 7, 13), (999, 8, 7, 25, 70)]:
+        key = (((n * 9 + q) * nth + j) * NR + i) * ((NZ + 3) // 4) + k // 4
+        z = oracle.splitmix64(key)
+        assert oracle.sr_dither(n, q, j, i, k, nth, NR, NZ) == (z >> (16 * (k % 4))) & 0x1FFF
+
+
+def test_stochastic_rounding_is_unbiased_and_stays_between_neighbours():
+    """For FP32 values in FP16's range, over all 8192 dithers the rounded
+    values are the two FP16 neighbours of x and average to x: exactly in the
+    normal range (an FP32 value has 13 bits below the FP16 spacing there, as
+    many as the dither), within 2^-13 of the spacing 2^-24 below it; values
+    of the format are kept for every dither."""
+    rng = np.random.default_rng(4)
+    xs = np.concatenate([rng.uniform(-2, 2, 40), rng.uniform(-1e-5, 1e-5, 20), 2.0 ** -rng.integers(15, 24, 10)])
+    xs = xs.astype(np.float32).astype(np.float64)
+    d = np.arange(8192)
+    for x in xs:
+        r = oracle.round_stochastic_f16(np.full(8192, x), d)
+        lo = np.float16(x)
+        nb = {float(lo), float(np.nextafter(lo, np.float16(np.inf))), float(np.nextafter(lo, np.float16(-np.inf)))}
+        assert set(np.unique(r)) <= nb, x
+        tol = 0.0 if abs(x) >= 2.0 ** -14 else 2.0 ** -24 / 8192
+        assert abs(r.mean() - x) <= tol + 1e-15 * abs(x), (x, r.mean())
+    for h in np.float16([0.5, -1.25, 6.0e-5, 3.0e-8, 1024.0]):
+        assert np.all(oracle.round_stochastic_f16(np.full(64, float(h)), np.arange(0, 8192, 128)) == float(h))
+
+
+def test_stochastic_rounding_run_keeps_fields_in_fp16():
+    sc = _small_case(r=0.02)
+    scales = fp16_scales(sc)
+    o = oracle.Oracle(sc, storage="f16sr", scales=scales, max_steps=300)
+    o.step(300)
+    for q, name in enumerate(oracle.FIELDS):
+        s = scales[0] if q < 3 else scales[1]
+        stored = o.field(name) * s
+        assert np.abs(stored).max() > 0, name
+        assert np.allclose(oracle.round_storage(stored, "f16"), stored, rtol=1e-14, atol=0), name
