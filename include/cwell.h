@@ -61,6 +61,7 @@ extern "C" {
 #define SIM_STORAGE_F32 0
 #define SIM_STORAGE_BF16 1
 #define SIM_STORAGE_F16 2
+#define SIM_STORAGE_F16_SR 3  /* FP16 written with stochastic rounding by the stencil kernels (see sim_opts_t) */
 
 #define SIM_KERNEL_AUTO 0     /* fastest path for the storage type */
 #define SIM_KERNEL_SPLIT 1    /* separate velocity and stress kernels */
@@ -121,7 +122,13 @@ typedef struct {
 
 /* Options.  Zero-initialised options are valid defaults. */
 typedef struct {
-  int storage;        /* SIM_STORAGE_*: field/coefficient storage; arithmetic is FP32 */
+  int storage;        /* SIM_STORAGE_*: field storage; arithmetic is FP32.  SIM_STORAGE_F16_SR stores
+                         FP16 (the FP16 scales) rounded stochastically: field f of cell (j, i, k)
+                         at step n rounds up with probability frac(|x| / u), u the FP16 spacing,
+                         against a 13-bit dither from SplitMix64 of the counter
+                         ((((n * 9 + f) * nth + j) * NR + i) * ceil(NZ / 4) + k / 4), bits
+                         16 (k mod 4) .. 16 (k mod 4) + 12; the split (23xx) and sweep kernels and
+                         the volumetric source only (SIM_EUNSUPPORTED otherwise) */
   int pml_off;        /* 1: rigid walls with no PML (energy-conserving closure) */
   int graph_chunk;    /* steps per captured CUDA graph; 0 = 64; < 0 = no graph */
   void *cuda_stream;  /* cudaStream_t to enqueue on; NULL = a stream owned by the handle */
@@ -147,6 +154,49 @@ int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, const sim_sou
 /* Enqueue nsteps leapfrog steps (velocity to t_{n+1/2}, stress to t_{n+1},
  * source, receivers; Eq. 1a then Eq. 1b).  nsteps >= 0. */
 int sim_step(sim_t *h, int nsteps);
+
+/* ------------------------------------------------------------------------
+ * Z slabs of one well (Sec. 4 of the paper: each processing unit owns a
+ * contiguous range of z planes and swaps the planes next to its boundaries
+ * with its neighbours after each half-step), one handle per slab, e.g. one
+ * per GPU.
+ *
+ * sim_create_slab takes the whole well (grid, medium, source, receivers as
+ * for sim_create) and the slab's stored z cells s0 <= k < s1 (k = the
+ * well's index, PML cells included; inner bounds multiples of 4, at least 8
+ * cells).  The handle holds those cells and 4 ghost cells on each side shared
+ * with another slab, updates only its own cells, injects the source only if
+ * it owns its depth, records only its own receivers (the others read zero)
+ * and takes the well's time step and PML profile, so that its cells evolve
+ * exactly as in the undivided well once the ghost cells are refilled after
+ * every half-step: FP32 storage, split kernels (interior / edge codes).
+ *
+ * A step of a slab is sim_half_step(h, 0) (velocity half-step and point
+ * forces), the velocity swap, sim_half_step(h, 1) (stress half-step,
+ * volumetric or torsion source, receivers), the stress swap.  A swap copies
+ * the slab's 4 own cells next to each inner boundary (sim_get_planes) to the
+ * neighbour's ghost cells (sim_put_planes).  sim_step also works on a slab
+ * (without swaps: its ghost cells then stay as they are).
+ * ------------------------------------------------------------------------ */
+int sim_create_slab(const sim_grid_t *grid, const sim_medium_t *medium, const sim_source_t *source,
+                    const sim_receivers_t *receivers, const sim_opts_t *opts, int s0, int s1, sim_t **out);
+
+/* One half of a leapfrog step: which = 0 velocity half-step (and point
+ * forces), which = 1 stress half-step (volumetric or torsion source) and the
+ * receivers; enqueued on the handle's stream.  Split kernels only. */
+int sim_half_step(sim_t *h, int which);
+
+/* Stored z cells the handle holds (l0 .. l0 + nz_local - 1 of the well) and
+ * owns (s0 .. s1 - 1); a whole-well handle gives 0, 0, NZ, NZ. */
+int sim_slab_info(const sim_t *h, int *l0, int *s0, int *s1, int *nz_local);
+
+/* Copy the planes k0 <= k < k1 (the well's stored index, within the cells the
+ * handle holds) of the velocities (group 0: v_r, v_phi, v_z) or the stresses
+ * (group 1: the six in field order) to / from buf, laid out
+ * [field][nth * NR][k1 - k0] in the storage type; buf may be device or host
+ * memory.  Enqueued on the handle's stream (asynchronous). */
+int sim_get_planes(sim_t *h, int group, int k0, int k1, void *dst);
+int sim_put_planes(sim_t *h, int group, int k0, int k1, const void *src);
 
 /* Wait for the handle's stream; reports device-side failures. */
 int sim_sync(sim_t *h);
@@ -211,9 +261,11 @@ size_t sim_device_bytes(const sim_t *h);
  * v * 10000 + s (a pair code) for the velocity kernel of split code v with the
  * stress kernel of split code s; 3000 + 100 m + 10 e + b for the single-pass
  * sweep kernel (kernel = SIM_KERNEL_SWEEP: four z cells per thread, b resident
- * blocks per SM, the general body in runs of e cells, z chunks of 32 cells
- * for m = 0, 1 and 64 for m = 2, 3, odd m with an L2 prefetch of each block's
- * next velocity item: 3043, 3024, 3143, 3124, 3243, 3224, 3343, 3324).
+ * blocks per SM, the general body in runs of e cells; (b, e) = (3, 4) or
+ * (4, 2); m = 0, 1: z chunks of 32 cells with stress items 3 chunks behind,
+ * m = 2, 3: chunks of 64 cells 2.5 chunks behind, m = 4, 5: chunks of 32
+ * cells 2.5 and 2 chunks behind; m = 1, 3 add an L2 prefetch of each block's
+ * next velocity item).
  * opts.tile accepts every code listed here. */
 int sim_config(const sim_t *h, int *kernel, int *tile_rows);
 
@@ -254,13 +306,16 @@ const char *sim_error_string(int code);
  * Each case is defined exactly as for sim_create (grid, medium, source,
  * receivers; shapes may differ between cases); opts is shared (storage,
  * stream, device, mem_cap applied to the batch total, graph_chunk,
- * max_steps; opts.kernel and opts.tile are ignored).  Cases of fewer than
- * 4 Mi cells share one interior and one edge launch per half step of the
- * load-first split bodies, driven by blocks that walk a work list of (case,
- * theta, r tile, z tile) items; the number of blocks is chosen by timing
- * candidates at create time.  A larger case fills the GPU alone and runs its
- * own split launches with the code its tuner picks (as sim_create with kernel
- * SIM_KERNEL_SPLIT).  Every case computes what its own sim_create handle on
+ * max_steps; opts.kernel is ignored).  Cases of fewer than 4 Mi cells share
+ * one interior and one edge launch per half step of the load-first split
+ * bodies, driven by blocks that walk a work list of (case, theta, r tile, z
+ * tile) items; the number of blocks is chosen by timing candidates at create
+ * time.  A larger case fills the GPU alone and runs its own split launches
+ * with the code its tuner picks (as sim_create with kernel SIM_KERNEL_SPLIT);
+ * those cases are spread over 1, 2 or 4 parallel streams (branches of the
+ * captured graph, the count timed at create time), so that one case's launch
+ * tails overlap another's work.  opts.tile: 0 = as above; 1 = every case in
+ * the shared launches, whatever its size; -1, -2, -4 = that many branches.  Every case computes what its own sim_create handle on
  * the split path computes, to FP32 rounding.  SIM_EINVAL for a shared case
  * of more than 2^31 - 1 items.
  * ------------------------------------------------------------------------ */
@@ -283,6 +338,8 @@ int simb_read_field(simb_t *b, int which, int field, float *out, size_t n);
 
 /* Number of cases, work items of the shared launches, persistent blocks per shared launch. */
 int simb_config(const simb_t *b, int *n_cases, long long *work_items, int *grid_blocks);
+/* Cases on their own launches and the parallel streams they run on. */
+int simb_layout(const simb_t *b, int *own_cases, int *branches);
 
 void simb_destroy(simb_t *b);
 const char *simb_last_error(const simb_t *b);

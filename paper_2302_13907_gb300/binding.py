@@ -16,7 +16,7 @@ from . import build as _build
 
 SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_EUNSTABLE, SIM_ETIMEOUT, SIM_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 FIELDS = ("vr", "vp", "vz", "srr", "spp", "szz", "srp", "spz", "srz")
-STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "f16sr": 3}
 KERNEL = {"auto": 0, "split": 1, "fused": 2, "fused4": 3, "march": 4, "sweep": 5}
 
 
@@ -91,6 +91,16 @@ def lib(path: str | None = None):
         L.sim_set_wait_test.restype = i
         L.sim_time_step.argtypes = [p, p, ctypes.POINTER(ctypes.c_double)]
         L.sim_time_step.restype = i
+        L.sim_create_slab.argtypes = [p, p, p, p, p, i, i, ctypes.POINTER(p)]
+        L.sim_create_slab.restype = i
+        L.sim_half_step.argtypes = [p, i]
+        L.sim_half_step.restype = i
+        L.sim_slab_info.argtypes = [p] + [ctypes.POINTER(i)] * 4
+        L.sim_slab_info.restype = i
+        L.sim_get_planes.argtypes = [p, i, i, i, p]
+        L.sim_get_planes.restype = i
+        L.sim_put_planes.argtypes = [p, i, i, i, p]
+        L.sim_put_planes.restype = i
         L.sim_kernel_time.argtypes = [p, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_long)]
         L.sim_kernel_time.restype = i
         L.sim_save.argtypes = [p, ctypes.c_char_p]
@@ -116,6 +126,8 @@ def lib(path: str | None = None):
         L.simb_read_field.restype = i
         L.simb_config.argtypes = [p, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i)]
         L.simb_config.restype = i
+        L.simb_layout.argtypes = [p, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.simb_layout.restype = i
         L.simb_destroy.argtypes = [p]
         L.simb_destroy.restype = None
         L.simb_last_error.argtypes = [p]
@@ -154,6 +166,15 @@ class SimError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{msg} (code {code})")
         self.code = code
+
+
+def _ptr(a):
+    """Data pointer of a contiguous numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return ctypes.c_void_p(a.ctypes.data)
+    assert a.is_contiguous()
+    return ctypes.c_void_p(a.data_ptr())
 
 
 def _dp(a):
@@ -205,17 +226,43 @@ def time_step(scenario, dt=0.0) -> float:
 class Simulation:
     """One simulator handle (sim_create ... sim_destroy)."""
 
-    def __init__(self, scenario, **kw):
+    def __init__(self, scenario, slab=None, **kw):
+        """slab = (s0, s1): the z slab of stored cells s0 <= k < s1 of the
+        well (sim_create_slab); fields then cover the cells the handle holds."""
         self.L = lib()
         (grid, med, src, rec, opts), self._keep = make_structs(scenario, **kw)
         self.grid = scenario.medium.grid
         self.n_rec = rec.n
         h = ctypes.c_void_p()
-        rc = self.L.sim_create(ctypes.byref(grid), ctypes.byref(med), ctypes.byref(src), ctypes.byref(rec),
-                               ctypes.byref(opts), ctypes.byref(h))
+        if slab is None:
+            rc = self.L.sim_create(ctypes.byref(grid), ctypes.byref(med), ctypes.byref(src), ctypes.byref(rec),
+                                   ctypes.byref(opts), ctypes.byref(h))
+        else:
+            rc = self.L.sim_create_slab(ctypes.byref(grid), ctypes.byref(med), ctypes.byref(src), ctypes.byref(rec),
+                                        ctypes.byref(opts), int(slab[0]), int(slab[1]), ctypes.byref(h))
         if rc != SIM_OK:
             raise SimError(rc, self.L.sim_last_error(None).decode())
         self.h = h
+        l0, s0, s1, nz = (ctypes.c_int() for _ in range(4))
+        _check(self.L, self.h, self.L.sim_slab_info(self.h, ctypes.byref(l0), ctypes.byref(s0), ctypes.byref(s1),
+                                                    ctypes.byref(nz)))
+        self.l0, self.s0, self.s1 = l0.value, s0.value, s1.value
+        self.shape = (self.grid.nth, self.grid.NR, nz.value)
+
+    def half_step(self, which: int):
+        """0: velocity half-step (and point forces); 1: stress half-step,
+        source and receivers (sim_half_step)."""
+        _check(self.L, self.h, self.L.sim_half_step(self.h, int(which)))
+
+    def get_planes(self, group: int, k0: int, k1: int, out):
+        """Planes k0 <= k < k1 of group 0 (velocities) / 1 (stresses) into
+        `out` (a float32 numpy array or a CUDA torch tensor of
+        [fields][nth * NR][k1 - k0]); asynchronous on the handle's stream."""
+        _check(self.L, self.h, self.L.sim_get_planes(self.h, int(group), int(k0), int(k1), _ptr(out)))
+        return out
+
+    def put_planes(self, group: int, k0: int, k1: int, buf):
+        _check(self.L, self.h, self.L.sim_put_planes(self.h, int(group), int(k0), int(k1), _ptr(buf)))
 
     def close(self):
         if getattr(self, "h", None):
@@ -259,14 +306,14 @@ class Simulation:
         return out
 
     def field(self, name: str) -> np.ndarray:
-        out = np.zeros(self.grid.shape, np.float32)
+        out = np.zeros(self.shape, np.float32)
         _check(self.L, self.h, self.L.sim_read_field(self.h, FIELDS.index(name),
                                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size))
         return out
 
     def field_noalloc(self, name: str) -> np.ndarray:
         """As field(), staged in the library's fixed device scratch (no device allocation)."""
-        out = np.zeros(self.grid.shape, np.float32)
+        out = np.zeros(self.shape, np.float32)
         _check(self.L, self.h, self.L.sim_read_field_noalloc(self.h, FIELDS.index(name),
                                                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                                              out.size))
@@ -274,7 +321,7 @@ class Simulation:
 
     def set_field(self, name: str, a: np.ndarray):
         a = np.ascontiguousarray(a, np.float32)
-        assert a.shape == self.grid.shape
+        assert a.shape == self.shape
         _check(self.L, self.h, self.L.sim_write_field(self.h, FIELDS.index(name),
                                                       a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
 
@@ -369,6 +416,12 @@ class BatchSimulation:
         n, w, g = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
         self._chk(self.L.simb_config(self.h, ctypes.byref(n), ctypes.byref(w), ctypes.byref(g)))
         return n.value, w.value, g.value
+
+    def layout(self):
+        """(cases on their own launches, parallel streams they run on)."""
+        o, b = ctypes.c_int(), ctypes.c_int()
+        self._chk(self.L.simb_layout(self.h, ctypes.byref(o), ctypes.byref(b)))
+        return o.value, b.value
 
 
 def interface_matrix(n_coarse: int, half: bool, fine_to_coarse: bool) -> np.ndarray:

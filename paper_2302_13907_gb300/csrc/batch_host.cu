@@ -3,7 +3,9 @@
 // in place by the load-first split bodies).  Small cases share one interior
 // and one edge launch per half step (their kernel parameters travel as kernel
 // parameters, up to 64 cases per launch); a case large enough to fill the GPU
-// runs its own tuned split launches.  The steps are captured in a CUDA graph.
+// runs its own tuned split launches, the large cases spread over parallel
+// streams (branches of the captured graph) so that one case's launch tails
+// overlap another's work.  The steps are captured in a CUDA graph.
 #include <algorithm>
 #include <string>
 #include <vector>
@@ -20,6 +22,12 @@ struct simb_s {
   RParams *d_rp = nullptr;
   long long total = 0;  // bound on the items of one work list of the shared cases
   int grid = 0, graph_chunk = 64, steps_done = 0;
+  // parallel streams for the own-launch cases: case own[q] runs on branch[q % nbranch]
+  static constexpr int MAX_BRANCH = 4;
+  cudaStream_t branch[MAX_BRANCH] = {};
+  cudaEvent_t fork = nullptr, join[MAX_BRANCH] = {};
+  int nbranch = 1;
+  bool fixed_branches = false;
   cudaGraphExec_t gexec = nullptr;
   int gsteps = 0;
   std::string err;
@@ -40,6 +48,11 @@ static int bcuda(simb_t *b, cudaError_t e, const char *what) {
 static void brelease(simb_t *b) {
   if (!b) return;
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (int k = 0; k < simb_t::MAX_BRANCH; k++) {
+    if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
+    if (b->join[k]) cudaEventDestroy(b->join[k]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   for (sim_t *h : b->cases) sim_destroy(h);
   b->cases.clear();
   if (b->d_rp) cudaFree(b->d_rp);
@@ -52,15 +65,29 @@ static void brelease(simb_t *b) {
 // the same stream and graph.
 constexpr long long OWN_CELLS = 4LL << 20;
 
+// One step of every case.  The shared cases run on the batch's stream; the
+// own-launch cases on nbranch streams forked from it and joined back (each
+// case's two halves stay in order on its branch; cases share nothing).
 static cudaError_t batch_step(simb_t *b, const KParams *cases) {
   cudaError_t e = cudaSuccess;
   std::vector<KParams> sh;
   for (int c : b->shared) sh.push_back(cases[c]);
+  const int nb = b->own.size() > 1 ? std::min<int>(b->nbranch, (int)b->own.size()) : 1;
+  auto stream_of = [&](size_t q) { return nb > 1 ? b->branch[q % nb] : b->stream; };
+  if (nb > 1) {
+    e = cudaEventRecord(b->fork, b->stream);
+    for (int k = 0; k < nb && e == cudaSuccess; k++) e = cudaStreamWaitEvent(b->branch[k], b->fork, 0);
+  }
   for (int half = 1; half <= 2 && e == cudaSuccess; half++) {
     if (!sh.empty()) e = launch_batch_split(b->storage, half == 1, sh.data(), (int)sh.size(), b->grid, b->stream);
     for (size_t q = 0; q < b->own.size() && e == cudaSuccess; q++)
-      e = sim_split_halves(b->cases[b->own[q]], cases[b->own[q]], b->stream, half);
+      e = sim_split_halves(b->cases[b->own[q]], cases[b->own[q]], stream_of(q), half);
   }
+  if (nb > 1)
+    for (int k = 0; k < nb && e == cudaSuccess; k++) {
+      e = cudaEventRecord(b->join[k], b->branch[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[k], 0);
+    }
   return e;
 }
 
@@ -98,10 +125,31 @@ static int tune_grid(simb_t *b) {
       pick = b->grid;
     }
   }
+  b->grid = pick;
+  // branches of the own-launch cases: 1, 2 or 4 parallel streams
+  int pick_b = 1;
+  if (e == cudaSuccess && b->own.size() > 1 && !b->fixed_branches) {
+    float best_b = INFINITY;
+    for (int nb : {1, 2, 4}) {
+      if (nb > (int)b->own.size() || e != cudaSuccess) break;
+      b->nbranch = nb;
+      e = batch_step(b, dry.data());
+      cudaEventRecord(t0, b->stream);
+      for (int w = 0; w < 3 && e == cudaSuccess; w++) e = batch_step(b, dry.data());
+      cudaEventRecord(t1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, t0, t1);
+      if (e == cudaSuccess && ms < best_b) {
+        best_b = ms;
+        pick_b = nb;
+      }
+    }
+    b->nbranch = pick_b;
+  }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   if (e != cudaSuccess) return bcuda(b, e, "batch autotune");
-  b->grid = pick;
   return SIM_OK;
 }
 
@@ -111,8 +159,14 @@ extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *m
   *out = nullptr;
   if (n < 1 || !grids || !media || !sources || !receivers || !opts)
     return bfail(nullptr, SIM_EINVAL, "need n >= 1 and non-null arrays");
+  if (opts->storage == SIM_STORAGE_F16_SR)
+    return bfail(nullptr, SIM_EUNSUPPORTED, "batches store FP32, BF16 or FP16 rounded to nearest");
+  if (opts->tile != 0 && opts->tile != 1 && opts->tile != -1 && opts->tile != -2 && opts->tile != -4)
+    return bfail(nullptr, SIM_EINVAL, "opts.tile of a batch: 0, 1 (all shared) or -1, -2, -4 (branches)");
+  sim_opts_t vo = *opts;  // the batch's own use of opts.tile is not a tile code
+  vo.tile = 0;
   for (int c = 0; c < n; c++) {  // host-side checks of every case before any device work
-    int rc = validate_inputs(&grids[c], &media[c], &sources[c], &receivers[c], opts);
+    int rc = validate_inputs(&grids[c], &media[c], &sources[c], &receivers[c], &vo);
     if (rc) return bfail(nullptr, rc, "case " + std::to_string(c) + ": " + g_create_err);
     if (sources[c].kind != 0)
       return bfail(nullptr, SIM_EUNSUPPORTED, "case " + std::to_string(c) + ": batches run the volumetric source only");
@@ -136,6 +190,19 @@ extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *m
     if (e != cudaSuccess) return bail(bcuda(b, e, "cudaStreamCreate"));
     b->own_stream = true;
   }
+  if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(bcuda(b, e, "cudaEventCreate"));
+  for (int k = 0; k < simb_t::MAX_BRANCH; k++)
+    if ((e = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming)) != cudaSuccess)
+      return bail(bcuda(b, e, "batch branches"));
+  // opts.tile of a batch: 1 = every case in the shared persistent launches,
+  // -b (b = 1, 2, 4) = b branches for the own-launch cases; 0 = tuned
+  const bool all_shared = opts->tile == 1;
+  if (opts->tile < 0) {
+    b->nbranch = std::min(simb_t::MAX_BRANCH, -opts->tile);
+    b->fixed_branches = true;
+  }
   sim_opts_t o = *opts;
   o.kernel = SIM_KERNEL_SPLIT;
   o.cuda_stream = b->stream;
@@ -146,7 +213,7 @@ extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *m
     if (opts->mem_cap) o.mem_cap = opts->mem_cap > used ? opts->mem_cap - used : 1;
     const long long cells =
         (long long)grids[c].nth * (grids[c].nr + grids[c].pml_r) * (grids[c].nz + 2 * grids[c].pml_z);
-    const bool own = cells >= OWN_CELLS;
+    const bool own = cells >= OWN_CELLS && !all_shared;
     o.tile = own ? 0 : SPLIT_CODE;  // a large case is tuned (split family); the shared ones take the plain code
     (own ? b->own : b->shared).push_back(c);
     sim_t *h = nullptr;
@@ -246,6 +313,13 @@ extern "C" int simb_config(const simb_t *b, int *n_cases, long long *work_items,
   if (n_cases) *n_cases = (int)b->cases.size();
   if (work_items) *work_items = b->total;
   if (grid_blocks) *grid_blocks = b->grid;
+  return SIM_OK;
+}
+
+extern "C" int simb_layout(const simb_t *b, int *own_cases, int *branches) {
+  if (!b) return SIM_EINVAL;
+  if (own_cases) *own_cases = (int)b->own.size();
+  if (branches) *branches = b->own.size() > 1 ? std::min<int>(b->nbranch, (int)b->own.size()) : 1;
   return SIM_OK;
 }
 

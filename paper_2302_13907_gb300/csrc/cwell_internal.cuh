@@ -52,6 +52,9 @@ struct KParams {
   int src_i, src_j, src_k;  // src_j < 0: all ring-0 cells
   int *step;                // device step counter
   int i_lo, i_hi;           // rows updated: i_lo <= i < i_hi (the rest are interface ghost rows)
+  // z cells the split kernels update: k_lo <= k < k_hi (a z slab's own cells;
+  // the rest are its ghost cells, filled by the neighbouring slabs)
+  int k_lo = 0, k_hi = 1 << 30;
 };
 
 // Point forces and the torsion ring (source kinds 1-3): entry e adds
@@ -125,6 +128,20 @@ struct St<__half> {
     u.y = *reinterpret_cast<unsigned *>(&b);
     *reinterpret_cast<uint2 *>(p) = u;
   }
+};
+
+// FP16 storage with stochastic rounding (storage mode 3): the same 16-bit
+// format as __half, a distinct type so that the stencil kernels store it with
+// stochastic rounding (hoist_body.cuh); every other reader and writer treats
+// it as __half.
+struct half_sr {
+  __half h;
+};
+
+template <>
+struct St<half_sr> {
+  static __device__ __forceinline__ float4 ld4(const half_sr *p) { return St<__half>::ld4(reinterpret_cast<const __half *>(p)); }
+  static __device__ __forceinline__ float ld1(const half_sr *p) { return St<__half>::ld1(reinterpret_cast<const __half *>(p)); }
 };
 
 template <typename T>
@@ -273,14 +290,27 @@ inline int hoist_cells_per_thread(int code) {
   return ((code / 100) % 10 == 1 || ((code / 100) % 10 == 2 && (c == 1 || c == 5))) ? 2 : 4;
 }
 cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts = 3);
+// A second stream for the three-way split halves (23xx): while set on the
+// calling thread, each half forks its radial-PML and z-end launches onto
+// `side` (event `fork` recorded on the launching stream) and joins them back
+// (event `join`) after the interior launch, so that the edge kernels fill
+// the SMs the interior kernel leaves idle at its end; null = one stream.
+// ghost cells a z slab keeps on each side it shares with another slab
+constexpr int SLAB_GHOST = 4;
+
+struct SideStream {
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+};
+void set_side_stream(const SideStream *ss);
 // single-pass sweep kernel (stencil_sweep.cu): tile code 3000 + 100 m + 10 e
 // + b (b resident blocks per SM, general body in runs of e cells; m: z chunks
-// of 32 (m = 0, 1) or 64 cells (m = 2, 3), odd m with an L2 prefetch of the
-// next velocity item); vdone = sweep_chunks(NZ) ints (zeroed by the launcher
+// of 32 or 64 cells, the lag of the stress items, an L2 prefetch of the next
+// velocity item); vdone = sweep_chunks(NZ) ints (zeroed by the launcher
 // before the kernel), status bit 1 = a bounded wait gave up; wait_limit in
 // cycles (0: 2^31); withhold_chunk >= 0 is the test hook that makes one z
 // chunk's velocity items never report
-inline bool is_sweep(int code) { return code >= 3000 && code < 3400; }
+inline bool is_sweep(int code) { return code >= 3000 && code < 3600; }
 int sweep_chunks(int NZ);
 cudaError_t launch_sweep(int storage, int code, const KParams &p, int *vdone, int *status, long long wait_limit,
                          int withhold_chunk, cudaStream_t s);

@@ -8,6 +8,8 @@
 // (stencil_hoist.cu) and the single-pass sweep kernel (stencil_sweep.cu).
 #pragma once
 
+#include <type_traits>
+
 #include "cwell_internal.cuh"
 
 namespace cwell {
@@ -97,6 +99,9 @@ __device__ __forceinline__ float2 u32_to_f2(unsigned u, const __nv_bfloat16 *) {
 __device__ __forceinline__ float2 u32_to_f2(unsigned u, const __half *) {
   return __half22float2(*reinterpret_cast<const __half2 *>(&u));
 }
+__device__ __forceinline__ float2 u32_to_f2(unsigned u, const half_sr *) {
+  return __half22float2(*reinterpret_cast<const __half2 *>(&u));
+}
 template <typename T>
 struct VecCG<T, 4> {
   static __device__ __forceinline__ void ld(float (&d)[4], const T *p) {
@@ -123,6 +128,143 @@ __device__ __forceinline__ float ld1cg(const __nv_bfloat16 *p) {
 __device__ __forceinline__ float ld1cg(const __half *p) {
   return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short *>(p))));
 }
+__device__ __forceinline__ float ld1cg(const half_sr *p) { return ld1cg(reinterpret_cast<const __half *>(p)); }
+// Streaming loads and stores (ld/st.global.cs: lines allocated evict-first,
+// so a last use does not push out lines that other items still need): the
+// sweep kernel's stress items read their own stresses for the last time and
+// write the new ones, which nothing reads again in the launch.
+template <typename T, int NV>
+struct VecCS;
+template <>
+struct VecCS<float, 4> {
+  static __device__ __forceinline__ void ld(float (&d)[4], const float *p) {
+    const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+    d[0] = v.x;
+    d[1] = v.y;
+    d[2] = v.z;
+    d[3] = v.w;
+  }
+  static __device__ __forceinline__ void st(float *p, const float (&v)[4]) {
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+  }
+};
+template <>
+struct VecCS<float, 2> {
+  static __device__ __forceinline__ void ld(float (&d)[2], const float *p) {
+    const float2 v = __ldcs(reinterpret_cast<const float2 *>(p));
+    d[0] = v.x;
+    d[1] = v.y;
+  }
+  static __device__ __forceinline__ void st(float *p, const float (&v)[2]) {
+    __stcs(reinterpret_cast<float2 *>(p), make_float2(v[0], v[1]));
+  }
+};
+__device__ __forceinline__ unsigned f2_to_u32(float a, float b, const __nv_bfloat16 *) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const unsigned *>(&h);
+}
+__device__ __forceinline__ unsigned f2_to_u32(float a, float b, const __half *) {
+  const __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const unsigned *>(&h);
+}
+template <typename T>
+struct VecCS<T, 4> {
+  static __device__ __forceinline__ void ld(float (&d)[4], const T *p) {
+    const uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
+    const float2 a = u32_to_f2(u.x, p), b = u32_to_f2(u.y, p);
+    d[0] = a.x;
+    d[1] = a.y;
+    d[2] = b.x;
+    d[3] = b.y;
+  }
+  static __device__ __forceinline__ void st(T *p, const float (&v)[4]) {
+    __stcs(reinterpret_cast<uint2 *>(p), make_uint2(f2_to_u32(v[0], v[1], p), f2_to_u32(v[2], v[3], p)));
+  }
+};
+template <typename T>
+struct VecCS<T, 2> {
+  static __device__ __forceinline__ void ld(float (&d)[2], const T *p) {
+    const float2 a = u32_to_f2(__ldcs(reinterpret_cast<const unsigned *>(p)), p);
+    d[0] = a.x;
+    d[1] = a.y;
+  }
+  static __device__ __forceinline__ void st(T *p, const float (&v)[2]) {
+    __stcs(reinterpret_cast<unsigned *>(p), f2_to_u32(v[0], v[1], p));
+  }
+};
+// CS selects the streaming loads and stores
+template <typename T, int NV, bool CS>
+__device__ __forceinline__ void ldown(float (&d)[NV], const T *p) {
+  if (CS) VecCS<T, NV>::ld(d, p);
+  else Vec<T, NV>::ld(d, p);
+}
+template <typename T, int NV, bool CS>
+__device__ __forceinline__ void stown(T *p, const float (&v)[NV]) {
+  if (CS) VecCS<T, NV>::st(p, v);
+  else Vec<T, NV>::st(p, v);
+}
+
+// Stochastic rounding of the FP16 storage (mode 3).  The dither of field f
+// of cell (j, i, k) in the update of step n is the 13-bit group
+// (z >> 16 (k mod 4)) & 0x1fff of z = SplitMix64 mix of
+// (key + 1) 0x9E3779B97F4A7C15, key = (((n * 9 + f) * nth + j) * NR + i) *
+// ceil(NZ / 4) + floor(k / 4): one 64-bit hash per four cells.  A value x
+// (the FP32 result) of magnitude a rounds away from zero when
+// frac(a / u) * 8192 > dither, u the FP16 spacing at a (2^(E - 10), E the
+// exponent of a, at least -14), so that E[rounded] = x; every step of this
+// is exact in FP32.  Magnitudes beyond 65504 round to nearest.
+__device__ __forceinline__ unsigned long long sr_hash(const KParams &p, int n, int f, int j, int i, int k0) {
+  const unsigned long long ngrp = (unsigned long long)((p.NZ + 3) >> 2);
+  const unsigned long long key =
+      (((((unsigned long long)n * NF + f) * p.nth + j) * p.NR + i) * ngrp) + (unsigned long long)(k0 >> 2);
+  unsigned long long z = (key + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }  // -126 <= k <= 127
+
+__device__ __forceinline__ __half sr_round(float x, unsigned dither) {
+  const float a = fabsf(x);
+  if (!(a <= 65504.f) || a == 0.f) return __float2half_rn(x);  // beyond the format, not finite, or zero
+  const int ex = (int)((__float_as_uint(a) >> 23) & 0xff) - 127;
+  const int E = ex < -14 ? -14 : ex;
+  const float q = a * pow2f(10 - E);  // a / u, exact
+  const float fl = floorf(q);
+  const float up = ((q - fl) * 8192.f > (float)dither) ? 1.f : 0.f;
+  const float m = (fl + up) * pow2f(E - 10);  // exact, a value of the format
+  return __float2half_rn(copysignf(m, x));
+}
+
+// the NV values of field f at cells (j, i, k0 .. k0 + NV - 1) of step n
+template <int NV>
+__device__ __forceinline__ void sr_store(half_sr *p, const float (&v)[NV], const KParams &kp, int n, int f, int j,
+                                         int i, int k0) {
+  const unsigned long long z = sr_hash(kp, n, f, j, i, k0);
+  __half h[NV];
+#pragma unroll
+  for (int e = 0; e < NV; e++) h[e] = sr_round(v[e], (unsigned)(z >> (16 * ((k0 + e) & 3))) & 0x1fffu);
+  if (NV == 4) {
+    uint2 u;
+    u.x = (unsigned)__half_as_ushort(h[0]) | ((unsigned)__half_as_ushort(h[1 % NV]) << 16);
+    u.y = (unsigned)__half_as_ushort(h[2 % NV]) | ((unsigned)__half_as_ushort(h[3 % NV]) << 16);
+    *reinterpret_cast<uint2 *>(p) = u;
+  } else {
+    *reinterpret_cast<unsigned *>(p) =
+        (unsigned)__half_as_ushort(h[0]) | ((unsigned)__half_as_ushort(h[1 % NV]) << 16);
+  }
+}
+
+// store of a field's NV new values: stochastic rounding for half_sr, else
+// the plain (CS = false) or streaming (CS = true) store
+template <typename T, int NV, bool CS>
+__device__ __forceinline__ void st_field(T *ptr, const float (&v)[NV], const KParams &kp, int n, int f, int j,
+                                         int i, int k0) {
+  if constexpr (std::is_same<T, half_sr>::value) sr_store<NV>(ptr, v, kp, n, f, j, i, k0);
+  else stown<T, NV, CS>(ptr, v);
+}
+
 // CG selects the L2-only loads
 template <typename T, int NV, bool CG>
 __device__ __forceinline__ void ldrow(float (&d)[NV], const T *p) {
@@ -134,6 +276,13 @@ __device__ __forceinline__ float ldone(const T *p) {
   if (CG) return ld1cg(p);
   return St<T>::ld1(p);
 }
+
+template <>
+struct Vec<half_sr, 2> {
+  static __device__ __forceinline__ void ld(float (&d)[2], const half_sr *p) {
+    Vec<__half, 2>::ld(d, reinterpret_cast<const __half *>(p));
+  }
+};
 
 // PML memory variables: plain (not read-only path) vector loads and stores,
 // since the thread that reads a memory variable rewrites it
@@ -361,9 +510,10 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
       out_z[e] += vel_coef(dtv, rho_c[e] + rho_c[e + 1]) * (Dr + Q + Dz);
     }
   }
-  if (im) Vec<T, NV>::st(vr + c, out_r);
-  Vec<T, NV>::st(vp + c, out_p);
-  Vec<T, NV>::st(vz + c, out_z);
+  const int n_sr = std::is_same<T, half_sr>::value ? *p.step : 0;  // the step, for stochastic rounding
+  if (im) st_field<T, NV, false>(vr + c, out_r, p, n_sr, F_VR, j, i, k0);
+  st_field<T, NV, false>(vp + c, out_p, p, n_sr, F_VP, j, i, k0);
+  st_field<T, NV, false>(vz + c, out_z, p, n_sr, F_VZ, j, i, k0);
   if (PRE && rp) {  // cells the loop skipped keep the values loaded
     stv(p.psr[R_VR] + cr, ur_vr);
     stv(p.psr[Q_VR] + cr, uq_vr);
@@ -387,7 +537,8 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
 }
 
 // CG: the velocities are read through L2 only (ldrow / ldone), for a launch
-// in which other blocks wrote them
+// in which other blocks wrote them, and the cell's own stresses are read and
+// written streaming (last use in the launch)
 template <typename T, int NV, bool LEAN, bool PRE = false, bool ZIN = LEAN, bool CG = false>
 __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, const int i, const int k0) {
   const int nth = p.nth, NR = p.NR, NZ = p.NZ;
@@ -426,17 +577,17 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
   float jp_vz[NV];
   ldrow<T, NV, CG>(jp_vz, vz + cjp);
   float o_rr[NV];
-  Vec<T, NV>::ld(o_rr, srr + c);
+  ldown<T, NV, CG>(o_rr, srr + c);
   float o_pp[NV];
-  Vec<T, NV>::ld(o_pp, spp + c);
+  ldown<T, NV, CG>(o_pp, spp + c);
   float o_zz[NV];
-  Vec<T, NV>::ld(o_zz, szz + c);
+  ldown<T, NV, CG>(o_zz, szz + c);
   float o_rp[NV];
-  Vec<T, NV>::ld(o_rp, srp + c);
+  ldown<T, NV, CG>(o_rp, srp + c);
   float o_pz[NV];
-  Vec<T, NV>::ld(o_pz, spz + c);
+  ldown<T, NV, CG>(o_pz, spz + c);
   float o_rz[NV];
-  Vec<T, NV>::ld(o_rz, srz + c);
+  ldown<T, NV, CG>(o_rz, srz + c);
   int idc[NV], idj[NV], idm[NV], idjm[NV];
   ldids(p.id + c, idc);
   ldids(p.id + cjp, idj);
@@ -578,14 +729,15 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
       opz[e] += dts * mu * (Q + gz);
     }
   }
-  Vec<T, NV>::st(srr + c, orr);
-  Vec<T, NV>::st(spp + c, opp);
-  Vec<T, NV>::st(szz + c, ozz);
+  const int n_sr = std::is_same<T, half_sr>::value ? *p.step : 0;  // the step, for stochastic rounding
+  st_field<T, NV, CG>(srr + c, orr, p, n_sr, F_SRR, j, i, k0);
+  st_field<T, NV, CG>(spp + c, opp, p, n_sr, F_SPP, j, i, k0);
+  st_field<T, NV, CG>(szz + c, ozz, p, n_sr, F_SZZ, j, i, k0);
   if (im) {
-    Vec<T, NV>::st(srp + c, orp);
-    Vec<T, NV>::st(srz + c, orz);
+    st_field<T, NV, CG>(srp + c, orp, p, n_sr, F_SRP, j, i, k0);
+    st_field<T, NV, CG>(srz + c, orz, p, n_sr, F_SRZ, j, i, k0);
   }
-  Vec<T, NV>::st(spz + c, opz);
+  st_field<T, NV, CG>(spz + c, opz, p, n_sr, F_SPZ, j, i, k0);
   if (PRE && rp) {  // cells the loop skipped keep the values loaded
     stv(p.psr[R_ERR] + cr, ur_rr);
     stv(p.psr[Q_EPP] + cr, uq_pp);

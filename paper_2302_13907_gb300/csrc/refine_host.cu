@@ -87,10 +87,12 @@ int ralloc(simr_t *h, void **p, size_t bytes) {
   bytes = (bytes + 255) & ~size_t(255);
   if (h->mem_cap && h->bytes + bytes > h->mem_cap)
     return rfail(h, SIM_ENOMEM, "device memory cap exceeded (" + std::to_string(h->bytes + bytes) + " bytes)");
-  cudaError_t e = cudaMalloc(p, bytes);
+  // stream-ordered: freeing a handle then waits for nothing but its own
+  // stream, so handles on other streams keep running
+  cudaError_t e = cudaMallocAsync(p, bytes, h->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return rfail(h, SIM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return rfail(h, SIM_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
   }
   h->allocs.push_back(*p);
   h->bytes += bytes;
@@ -102,8 +104,9 @@ int ralloc(simr_t *h, void **p, size_t bytes) {
 void rrelease(simr_t *h) {
   if (!h) return;
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  for (void *p : h->allocs) cudaFree(p);
+  for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
   h->allocs.clear();
+  if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 

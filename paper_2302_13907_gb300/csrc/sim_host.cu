@@ -105,7 +105,16 @@ int cwell::validate_inputs(const sim_grid_t *g, const sim_medium_t *m, const sim
     if (!isfinite(r->z[q]) || kr < 0 || kr >= g->nz || !(r->r[q] >= 0) || r->r[q] >= g->nr * g->dr)
       return fail(nullptr, SIM_EINVAL, "receiver " + std::to_string(q) + " outside the interior");
   }
-  if (o->storage < 0 || o->storage > 2) return fail(nullptr, SIM_EINVAL, "opts: storage must be 0, 1 or 2");
+  if (o->storage < 0 || o->storage > 3) return fail(nullptr, SIM_EINVAL, "opts: storage must be 0 .. 3");
+  if (o->storage == SIM_STORAGE_F16_SR) {
+    if (!(o->kernel == SIM_KERNEL_AUTO || o->kernel == SIM_KERNEL_SPLIT || o->kernel == SIM_KERNEL_SWEEP))
+      return fail(nullptr, SIM_EUNSUPPORTED, "storage: stochastic rounding runs on the split and sweep kernels only");
+    if (s->kind != 0)
+      return fail(nullptr, SIM_EUNSUPPORTED, "storage: stochastic rounding with the volumetric source only");
+    if (o->tile != 0 && !(o->tile >= 2300 && o->tile < 2400) && !is_sweep(o->tile) &&
+        !(is_split_pair(o->tile) && split_vel_code(o->tile) / 100 == 23 && split_str_code(o->tile) / 100 == 23))
+      return fail(nullptr, SIM_EUNSUPPORTED, "storage: stochastic rounding runs on the 23xx split and the sweep codes");
+  }
   if (o->kernel < 0 || o->kernel > 5) return fail(nullptr, SIM_EINVAL, "opts: kernel must be 0 .. 5");
   if (o->tile != 0) {  // the family of the code must match the kernel asked for; the code itself is checked later
     const int t = o->tile;
@@ -154,9 +163,18 @@ extern "C" int sim_time_step(const sim_grid_t *grid, const sim_medium_t *medium,
   return SIM_OK;
 }
 
+// RAII: the handle's side stream for the three-way split halves while in scope
+struct SideScope {
+  explicit SideScope(const sim_t *h) { set_side_stream(h->side.side ? &h->side : nullptr); }
+  ~SideScope() { set_side_stream(nullptr); }
+};
+
 static void release(sim_t *h) {
   if (!h) return;
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->side.fork) cudaEventDestroy(h->side.fork);
+  if (h->side.join) cudaEventDestroy(h->side.join);
+  if (h->side.side) cudaStreamDestroy(h->side.side);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
   for (void *p : h->allocs) cudaFree(p);
@@ -258,16 +276,17 @@ static cudaError_t launch_split_family(int storage, int code, const KParams &p, 
 // (the batch drives its large cases this way, on the batch's stream)
 cudaError_t cwell::sim_split_halves(const sim_t *h, const KParams &p, cudaStream_t s, int parts) {
   if (!is_split_family(h->tile_rt)) return cudaErrorInvalidValue;
-  return launch_split_family(h->storage, h->tile_rt, p, s, nullptr, parts);
+  return launch_split_family(h->stencil_storage, h->tile_rt, p, s, nullptr, parts);
 }
 
 static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
+  SideScope side_scope(h);
   const bool allow_split = kernel == SIM_KERNEL_AUTO || kernel == SIM_KERNEL_SPLIT;
   int dev = h->device, maxsm = 0;
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   // point forces rule out the sweep kernel: they key a separate choice
   const bool force = h->src_kind == 1 || h->src_kind == 2;
-  auto key = std::make_tuple(dev, h->grid.nth, h->NR, h->NZ, h->storage * 8 + kernel,
+  auto key = std::make_tuple(dev, h->grid.nth, h->NR, h->NZ, h->stencil_storage * 8 + kernel,
                              (h->kp.pml_r > 0 ? 1 : 0) + (force ? 2 : 0));
   if (!forced) {
     std::lock_guard<std::mutex> g(g_tune_mu);
@@ -281,7 +300,7 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
                       1864, 2003, 2004, 2005, 2013, 2014, 2106, 2108, 2204, 2205, 2216, 2218, 2224, 2225,
                       2234, 2235, 2244, 2245, 2256, 2258, 2264, 2265, 2274, 2275,
                       2284, 2285, 2294, 2295, 2304, 2305, 2314, 2315, 2324, 2325, 2334, 2335, SPLIT_CODE,
-                      3043, 3024, 3143, 3124, 3243, 3224, 3343, 3324};
+                      3043, 3024, 3143, 3124, 3243, 3224, 3343, 3324, 3443, 3424, 3543, 3524};
   cudaEvent_t a, b, c3;
   CK(h, cudaEventCreate(&a));
   CK(h, cudaEventCreate(&b));
@@ -304,6 +323,10 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
     if (is_sweep(rt) && (force || !(kernel == SIM_KERNEL_AUTO || kernel == SIM_KERNEL_SWEEP))) continue;
     if (is_split_family(rt) && !allow_split) continue;
     if (!h->fused && fused_code) continue;  // no second buffer set for the fused kernels
+    // a slab: the interior / edge split codes, whose kernels honour its z range
+    if (h->slab && !(rt >= 2200 && rt < 2400)) continue;
+    // stochastic rounding: the three-way split codes and the sweep kernel only
+    if (h->stencil_storage == SIM_STORAGE_F16_SR && !(rt >= 2300 && rt < 2400) && !is_sweep(rt)) continue;
     if (forced && rt != forced) continue;
     if (forced) {  // a tile asked for by the caller: check that it fits, time nothing
       const size_t need = is_split_family(rt) || is_sweep(rt) ? 1
@@ -317,11 +340,14 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
     if (is_split_family(rt)) {  // each half timed on its own: the best velocity and stress kernels may differ
       KParams dry = h->kp;
       dry.src_i = -1;  // no source: zero state stays zero
-      for (int w = 0; w < 2 && e == cudaSuccess; w++) e = launch_split_family(h->storage, rt, dry, h->stream, nullptr);
+      for (int w = 0; w < 2 && e == cudaSuccess; w++)
+        e = launch_split_family(h->stencil_storage, rt, dry, h->stream, nullptr);
       cudaEventRecord(a, h->stream);
-      for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_split_family(h->storage, rt, dry, h->stream, nullptr, 1);
+      for (int w = 0; w < 3 && e == cudaSuccess; w++)
+        e = launch_split_family(h->stencil_storage, rt, dry, h->stream, nullptr, 1);
       cudaEventRecord(b, h->stream);
-      for (int w = 0; w < 3 && e == cudaSuccess; w++) e = launch_split_family(h->storage, rt, dry, h->stream, nullptr, 2);
+      for (int w = 0; w < 3 && e == cudaSuccess; w++)
+        e = launch_split_family(h->stencil_storage, rt, dry, h->stream, nullptr, 2);
       cudaEventRecord(c3, h->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(c3);
       if (e != cudaSuccess) {
@@ -340,10 +366,10 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
       KParams dry = h->kp;
       dry.src_i = -1;
       for (int w = 0; w < 2 && e == cudaSuccess; w++)
-        e = launch_sweep(h->storage, rt, dry, h->vdone, h->status, 0, -1, h->stream);
+        e = launch_sweep(h->stencil_storage, rt, dry, h->vdone, h->status, 0, -1, h->stream);
       cudaEventRecord(a, h->stream);
       for (int w = 0; w < 3 && e == cudaSuccess; w++)
-        e = launch_sweep(h->storage, rt, dry, h->vdone, h->status, 0, -1, h->stream);
+        e = launch_sweep(h->stencil_storage, rt, dry, h->vdone, h->status, 0, -1, h->stream);
       cudaEventRecord(b, h->stream);
     } else if (is_march(rt)) {
       const size_t need = march_smem_bytes(h->storage, rt);
@@ -401,23 +427,41 @@ static int autotune(sim_t *h, int kernel, int forced, int *best_rt) {
   return SIM_OK;
 }
 
-extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, const sim_source_t *source,
-                          const sim_receivers_t *receivers, const sim_opts_t *opts, sim_t **out) {
+// slab == nullptr: the whole well; otherwise {s0, s1}: the z slab of stored
+// cells s0 <= k < s1 (sim_create_slab)
+static int create_impl(const sim_grid_t *grid, const sim_medium_t *medium, const sim_source_t *source,
+                       const sim_receivers_t *receivers, const sim_opts_t *opts, const int *slab, sim_t **out) {
   if (!out) return fail(nullptr, SIM_EINVAL, "out is null");
   *out = nullptr;
   int rc = validate_inputs(grid, medium, source, receivers, opts);
   if (rc) return rc;
   const sim_grid_t &g = *grid;
-  const int NR = g.nr + g.pml_r, NZ = g.nz + 2 * g.pml_z, nth = g.nth;
+  const int NR = g.nr + g.pml_r, NZg = g.nz + 2 * g.pml_z, nth = g.nth;
+  // the stored z cells this handle holds: l0 <= k < l1 of the well (all of
+  // them, or a slab with SLAB_GHOST ghost cells on each inner side)
+  int l0 = 0, l1 = NZg, s0 = 0, s1 = NZg;
+  if (slab) {
+    s0 = slab[0];
+    s1 = slab[1];
+    if (s0 < 0 || s1 > NZg || s1 - s0 < 2 * SLAB_GHOST || (s0 % 4) || (s1 < NZg && (s1 % 4)))
+      return fail(nullptr, SIM_EINVAL, "slab: need 0 <= s0 < s1 <= NZ, s1 - s0 >= 8, inner bounds multiples of 4");
+    if (opts->storage != 0 || !(opts->kernel == SIM_KERNEL_AUTO || opts->kernel == SIM_KERNEL_SPLIT))
+      return fail(nullptr, SIM_EUNSUPPORTED, "slab: FP32 storage on the split kernels only");
+    l0 = std::max(0, s0 - SLAB_GHOST);
+    l1 = std::min(NZg, s1 + SLAB_GHOST);
+    if (g.pml_z > 0 && l1 - l0 < 2 * g.pml_z + 8)
+      return fail(nullptr, SIM_EINVAL, "slab: fewer cells than two z layers and eight more");
+  }
+  const int NZ = l1 - l0;
   const int NZp = (NZ + 31) / 32 * 32;
-  const size_t ncell = (size_t)nth * NR * NZ;
+  const size_t ncell = (size_t)nth * NR * NZg;
   const uint16_t *cid = medium->cell_id;
   // material IDs in range; ring 0 (the axis cells) must be a liquid
   for (size_t c = 0; c < ncell; c++)
     if (cid[c] >= medium->n_mat) return fail(nullptr, SIM_EINVAL, "medium: cell_id out of range at " + std::to_string(c));
   for (int j = 0; j < nth; j++)
-    for (int k = 0; k < NZ; k++)
-      if (medium->vs[cid[((size_t)j * NR) * NZ + k]] != 0.0)
+    for (int k = 0; k < NZg; k++)
+      if (medium->vs[cid[((size_t)j * NR) * NZg + k]] != 0.0)
         return fail(nullptr, SIM_EUNSUPPORTED, "medium: ring 0 (next to the axis) must be a liquid");
 
   sim_t *h = new sim_t();
@@ -425,11 +469,16 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   h->NR = NR;
   h->NZ = NZ;
   h->NZp = NZp;
-  h->storage = opts->storage;
+  h->slab = slab != nullptr;
+  h->l0 = l0;
+  h->s0 = s0;
+  h->s1 = s1;
+  h->stencil_storage = opts->storage;
+  h->storage = opts->storage == SIM_STORAGE_F16_SR ? SIM_STORAGE_F16 : opts->storage;  // the stored format
   h->elem = opts->storage == 0 ? 4 : 2;
   // AUTO prepares the fused path and lets the autotuner fall back to the split
   // or marching kernels; the split and marching paths update one buffer set in place
-  h->kernel = opts->kernel == SIM_KERNEL_SPLIT   ? SIM_KERNEL_SPLIT
+  h->kernel = opts->kernel == SIM_KERNEL_SPLIT || slab ? SIM_KERNEL_SPLIT
               : opts->kernel == SIM_KERNEL_MARCH ? SIM_KERNEL_MARCH
               : opts->kernel == SIM_KERNEL_SWEEP ? SIM_KERNEL_SWEEP
                                                  : SIM_KERNEL_FUSED;
@@ -462,6 +511,10 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaStreamCreate"));
     h->own_stream = true;
   }
+  if ((e = cudaStreamCreateWithFlags(&h->side.side, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(cuda_fail(h, e, "side stream"));
 
   // --- time step (reading R7)
   const double dth = 2.0 * M_PI / nth;
@@ -473,7 +526,7 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   int is = source->r < g.dr ? 0 : (int)floor(source->r / g.dr);
   int js = source->r < g.dr ? -1 : (int)(((lround(source->theta / dth) % nth) + nth) % nth);
   if (h->storage == 2) {
-    int m0 = cid[((size_t)(js < 0 ? 0 : js) * NR + is) * NZ + ks];
+    int m0 = cid[((size_t)(js < 0 ? 0 : js) * NR + is) * NZg + ks];
     h->sscale = source->amplitude != 0 ? 1.0 / fabs(source->amplitude) : 1.0;
     h->vscale = h->sscale * medium->rho[m0] * medium->vp[m0];
   }
@@ -517,8 +570,9 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
     cpml(profbar(xh, (i + 0.5) * g.dr, Lr, d0r), al, dt, &ab_q[i].z, &ab_q[i].w);
   }
   for (int k = 0; k < NZ; k++) {
-    double xi = std::max((g.pml_z - 0.5 - k) * g.dz, (k - (g.pml_z + g.nz - 0.5)) * g.dz);
-    double xh = std::max((g.pml_z - 1.0 - k) * g.dz, (k + 1.0 - g.pml_z - g.nz) * g.dz);
+    const int kg = k + l0;  // the well's stored index (a slab's profile is the well's)
+    double xi = std::max((g.pml_z - 0.5 - kg) * g.dz, (kg - (g.pml_z + g.nz - 0.5)) * g.dz);
+    double xh = std::max((g.pml_z - 1.0 - kg) * g.dz, (kg + 1.0 - g.pml_z - g.nz) * g.dz);
     if (!pml) xi = xh = 0.0;
     cpml(prof(xi, Lz, d0z), al, dt, &ab_z[k].x, &ab_z[k].y);
     cpml(prof(xh, Lz, d0z), al, dt, &ab_z[k].z, &ab_z[k].w);
@@ -541,11 +595,15 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
     const bool axis = source->r < g.dr;
     const int jsrc = (int)(((lround(source->theta / dth) % nth) + nth) % nth);
     const double A = source->amplitude, dr = g.dr, dz = g.dz;
-    auto hc = [&](int j, int i, long k) { return ((size_t)j * NR + i) * NZ + (size_t)k; };  // host cell
-    auto dc = [&](int j, int i, long k) { return ((long long)j * NR + i) * NZp + k; };      // device element
+    auto hc = [&](int j, int i, long k) { return ((size_t)j * NR + i) * NZg + (size_t)k; };  // host cell
+    auto dc = [&](int j, int i, long k) { return ((long long)j * NR + i) * NZp + (k - l0); };  // device element
     auto rho2 = [&](size_t a, size_t b) { return 0.5 * (medium->rho[cid[a]] + medium->rho[cid[b]]); };
     auto solid = [&](size_t c) { return medium->vs[cid[c]] > 0.0; };
+    // every point of a source sits at depth k = ks; a slab that does not own
+    // it injects nothing (the owner does, and the planes it sends carry it)
+    const bool own_src = ks >= s0 && ks < s1;
     auto add = [&](int fld, long long off, double w) {
+      if (!own_src) return;
       ifld.push_back(fld);
       ioff.push_back(off);
       iw.push_back((float)(dt * A * w * (fld <= F_VZ ? h->vscale : h->sscale)));
@@ -562,7 +620,7 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
         else add(F_VR, dc(jsrc, i, k), 1.0 / (rho2(hc(jsrc, i - 1, k), hc(jsrc, i, k)) * i * dr * dr * dth * dz));
       }
     } else if (source->kind == 2) {
-      if (k + 1 >= NZ) bad = true;
+      if (k + 1 >= NZg) bad = true;
       else if (axis) {
         for (int j = 0; j < nth; j++)
           add(F_VZ, dc(j, 0, k), 1.0 / (rho2(hc(j, 0, k), hc(j, 0, k + 1)) * M_PI * dr * dr * dz));
@@ -572,7 +630,7 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
       }
     } else {
       const int i = (int)lround(source->r / dr), ih = (int)floor(source->r / dr);
-      if (i < 1 || i >= NR || ih + 1 > NR || k + 1 >= NZ) bad = true;
+      if (i < 1 || i >= NR || ih + 1 > NR || k + 1 >= NZg) bad = true;
       for (int j = 0; j < nth && !bad; j++) {
         const int jp = (j + 1) % nth;
         if (!(solid(hc(j, i - 1, k)) && solid(hc(j, i, k)) && solid(hc(jp, i - 1, k)) && solid(hc(jp, i, k)) &&
@@ -593,7 +651,8 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
     bool axis = receivers->r[q] < g.dr;
     rec[3 * q] = axis ? 0 : (int)floor(receivers->r[q] / g.dr);
     rec[3 * q + 1] = axis ? -1 : (int)(((lround(receivers->theta[q] / dth) % nth) + nth) % nth);
-    rec[3 * q + 2] = (int)(lround(receivers->z[q] / g.dz) + g.pml_z);
+    const int kr = (int)(lround(receivers->z[q] / g.dz) + g.pml_z);
+    rec[3 * q + 2] = (kr >= s0 && kr < s1) ? kr - l0 : -1;  // -1: another slab records it
   }
 
   // --- device memory
@@ -647,7 +706,7 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   cudaStream_t st = h->stream;
 #define UP(dst, src, n) \
   if ((e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st)) != cudaSuccess) return bail(cuda_fail(h, e, "upload"))
-  e = cudaMemcpy2DAsync(h->id, NZp * 2, cid, NZ * 2, NZ * 2, (size_t)nth * NR, cudaMemcpyHostToDevice, st);
+  e = cudaMemcpy2DAsync(h->id, NZp * 2, cid + l0, NZg * 2, NZ * 2, (size_t)nth * NR, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return bail(cuda_fail(h, e, "upload cell_id"));
   UP(h->mat, mat.data(), mat.size() * sizeof(float4));
   UP(h->m_rho, m_rho.data(), mat.size() * 4);
@@ -701,9 +760,13 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   for (int q = 0; q < NPZ; q++) p.psz[q] = h->psz[q];
   p.wav = h->wav;
   p.n_wav = h->n_wav;
-  p.src_i = source->kind == 0 ? is : -1;  // the stress kernels inject only the volumetric source
+  // the stress kernels inject only the volumetric source, and only in the
+  // cells this handle owns
+  p.src_i = (source->kind == 0 && ks >= s0 && ks < s1) ? is : -1;
   p.src_j = js;
-  p.src_k = (int)ks;
+  p.src_k = (int)ks - l0;
+  p.k_lo = s0 - l0;
+  p.k_hi = s1 - l0;
   p.step = h->step;
   p.i_lo = 0;
   p.i_hi = NR;
@@ -789,8 +852,21 @@ extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, co
   return SIM_OK;
 }
 
+extern "C" int sim_create(const sim_grid_t *grid, const sim_medium_t *medium, const sim_source_t *source,
+                          const sim_receivers_t *receivers, const sim_opts_t *opts, sim_t **out) {
+  return create_impl(grid, medium, source, receivers, opts, nullptr, out);
+}
+
+extern "C" int sim_create_slab(const sim_grid_t *grid, const sim_medium_t *medium, const sim_source_t *source,
+                               const sim_receivers_t *receivers, const sim_opts_t *opts, int s0, int s1,
+                               sim_t **out) {
+  const int slab[2] = {s0, s1};
+  return create_impl(grid, medium, source, receivers, opts, slab, out);
+}
+
 // Enqueue one step; `parity` = index of the step mod 2 (fused path buffers).
 static cudaError_t enqueue_step(sim_t *h, int parity, bool timed) {
+  SideScope side_scope(h);
   cudaError_t e;
   if (h->fused) {
     if (timed) cudaEventRecord(h->ev[0], h->stream);
@@ -803,7 +879,8 @@ static cudaError_t enqueue_step(sim_t *h, int parity, bool timed) {
     e = launch_receivers(h->storage, h->rp2[parity], h->stream);
   } else if (h->sweep) {
     if (timed) cudaEventRecord(h->ev[0], h->stream);
-    e = launch_sweep(h->storage, h->tile_rt, h->kp, h->vdone, h->status, h->wait_cycles, h->withhold_chunk, h->stream);
+    e = launch_sweep(h->stencil_storage, h->tile_rt, h->kp, h->vdone, h->status, h->wait_cycles, h->withhold_chunk,
+                     h->stream);
     if (e != cudaSuccess) return e;
     if (timed) {
       cudaEventRecord(h->ev[1], h->stream);
@@ -817,7 +894,7 @@ static cudaError_t enqueue_step(sim_t *h, int parity, bool timed) {
     const bool force = h->src_kind == 1 || h->src_kind == 2;
     auto half = [&](int parts) {
       return h->march ? launch_march(h->storage, h->tile_rt, h->mmaps, h->kp, h->status, h->stream, ev, parts)
-                      : launch_split_family(h->storage, h->tile_rt, h->kp, h->stream, ev, parts);
+                      : launch_split_family(h->stencil_storage, h->tile_rt, h->kp, h->stream, ev, parts);
     };
     if (force) {
       e = half(1);
@@ -899,6 +976,60 @@ extern "C" int sim_step(sim_t *h, int nsteps) {
 static void **cur_fields(sim_t *h) { return (h->fused && (h->steps_done & 1)) ? h->f2 : h->f; }
 static float **cur_psr(sim_t *h) { return (h->fused && (h->steps_done & 1)) ? h->psr2 : h->psr; }
 static float **cur_psz(sim_t *h) { return (h->fused && (h->steps_done & 1)) ? h->psz2 : h->psz; }
+
+extern "C" int sim_half_step(sim_t *h, int which) {
+  if (!h) return SIM_EINVAL;
+  if (which != 0 && which != 1) return fail(h, SIM_EINVAL, "which must be 0 (velocity) or 1 (stress)");
+  if (h->fused || h->march || h->sweep) return fail(h, SIM_EUNSUPPORTED, "half steps run on the split kernels only");
+  CK(h, cudaSetDevice(h->device));
+  SideScope side_scope(h);
+  const bool force = h->src_kind == 1 || h->src_kind == 2;
+  cudaError_t e = launch_split_family(h->stencil_storage, h->tile_rt, h->kp, h->stream, nullptr, which == 0 ? 1 : 2);
+  if (e == cudaSuccess && ((which == 0 && force) || (which == 1 && h->src_kind == 3)))
+    e = launch_inject(h->storage, h->ip, h->stream);
+  if (e == cudaSuccess && which == 1) e = launch_receivers(h->storage, h->rp, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "half step");
+  if (which == 1) h->steps_done++;
+  return SIM_OK;
+}
+
+extern "C" int sim_slab_info(const sim_t *h, int *l0, int *s0, int *s1, int *nz_local) {
+  if (!h) return SIM_EINVAL;
+  if (l0) *l0 = h->l0;
+  if (s0) *s0 = h->slab ? h->s0 : 0;
+  if (s1) *s1 = h->slab ? h->s1 : h->NZ;
+  if (nz_local) *nz_local = h->NZ;
+  return SIM_OK;
+}
+
+// planes k0 <= k < k1 (the well's stored z index) of the velocities (group 0)
+// or the stresses (group 1) to / from buf [field][nth * NR][k1 - k0]
+static int copy_planes(sim_t *h, int group, int k0, int k1, void *buf, bool out) {
+  if (!h) return SIM_EINVAL;
+  if ((group != 0 && group != 1) || !buf) return fail(h, SIM_EINVAL, "group must be 0 or 1, buffer non-null");
+  if (k0 < h->l0 || k1 > h->l0 + h->NZ || k0 >= k1)
+    return fail(h, SIM_EINVAL, "planes outside the cells the handle holds");
+  if (h->fused) return fail(h, SIM_EUNSUPPORTED, "plane copies run on the in-place paths");
+  CK(h, cudaSetDevice(h->device));
+  const int q0 = group == 0 ? F_VR : F_SRR, q1 = group == 0 ? F_SRR : NF;
+  const size_t w = (size_t)(k1 - k0) * h->elem, rows = (size_t)h->grid.nth * h->NR;
+  for (int q = q0; q < q1; q++) {
+    char *f = (char *)h->f[q] + (size_t)(k0 - h->l0) * h->elem;
+    char *b = (char *)buf + (size_t)(q - q0) * rows * w;
+    cudaError_t e = out ? cudaMemcpy2DAsync(b, w, f, (size_t)h->NZp * h->elem, w, rows, cudaMemcpyDefault, h->stream)
+                        : cudaMemcpy2DAsync(f, (size_t)h->NZp * h->elem, b, w, w, rows, cudaMemcpyDefault, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "plane copy");
+  }
+  return SIM_OK;
+}
+
+extern "C" int sim_get_planes(sim_t *h, int group, int k0, int k1, void *dst) {
+  return copy_planes(h, group, k0, k1, dst, true);
+}
+
+extern "C" int sim_put_planes(sim_t *h, int group, int k0, int k1, const void *src) {
+  return copy_planes(h, group, k0, k1, const_cast<void *>(src), false);
+}
 
 extern "C" int sim_sync(sim_t *h) {
   if (!h) return SIM_EINVAL;

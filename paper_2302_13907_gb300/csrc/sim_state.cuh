@@ -20,7 +20,9 @@ struct sim_s {
   sim_grid_t grid{};
   int NR = 0, NZ = 0, NZp = 0;
   double dt = 0, vscale = 1, sscale = 1;
-  int storage = 0, kernel = SIM_KERNEL_SPLIT, graph_chunk = 64, timing = 0;
+  // storage: the stored format (0 FP32, 1 BF16, 2 FP16); stencil_storage:
+  // what the stencil kernels write (also 3 = FP16 with stochastic rounding)
+  int storage = 0, stencil_storage = 0, kernel = SIM_KERNEL_SPLIT, graph_chunk = 64, timing = 0;
   int n_mat = 0, n_rec = 0, cap = 0;
   size_t elem = 4;
   void *f[NF] = {};
@@ -56,6 +58,12 @@ struct sim_s {
   FusedMaps mmaps;
   FusedParams fp[2];
   RParams rp2[2];
+  // second stream and fork / join events of the three-way split halves
+  SideStream side{};
+  // z slab (sim_create_slab): the handle holds the well's stored z cells
+  // l0 .. l0 + NZ - 1 and owns s0 .. s1 - 1 of them
+  bool slab = false;
+  int l0 = 0, s0 = 0, s1 = 0;
   int steps_done = 0;
   size_t bytes = 0, mem_cap = 0, psr_elems = 0, psz_elems = 0;
   std::vector<void *> allocs;

@@ -75,7 +75,7 @@ template <typename T, int NV, int MINB, bool VEL>
 __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_interior(const KParams p, int zt_lo) {
   const int j = blockIdx.x, i = blockIdx.y * HB_Y + threadIdx.y;
   const int k0 = ((zt_lo + blockIdx.z) * HB_X + threadIdx.x) * NV;
-  if (i < p.i_lo || i >= p.i_hi) return;
+  if (i < p.i_lo || i >= p.i_hi || k0 < p.k_lo || k0 >= p.k_hi) return;
   if (VEL) vel_hoist_body<T, NV, true>(p, j, i, k0);
   else str_hoist_body<T, NV, true>(p, j, i, k0);
 }
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB)
       prefetch_tile<T, NV, VEL>(p, j, i, k0);
     }
     cell(t, j, i, k0);
-    if (i < p.i_lo || i >= p.i_hi) continue;
+    if (i < p.i_lo || i >= p.i_hi || k0 < p.k_lo || k0 >= p.k_hi) continue;
     if (VEL) vel_hoist_body<T, NV, true>(p, j, i, k0);
     else str_hoist_body<T, NV, true>(p, j, i, k0);
   }
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_edge(const KParams p, 
   int rt, zt;
   edge_tile(q, blockIdx.y, rt, zt);
   const int j = blockIdx.x, i = rt * HB_Y + threadIdx.y, k0 = (zt * HB_X + threadIdx.x) * NV;
-  if (i >= p.i_lo && i < p.i_hi && k0 < p.NZ) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
+  if (i >= p.i_lo && i < p.i_hi && k0 < p.NZ && k0 >= p.k_lo && k0 < p.k_hi) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
 }
 
 // the same edge tiles walked by one wave of resident blocks, each prefetching
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_edge_pf(const KParams 
       }
     }
     cell(t, j, i, k0);
-    if (i >= p.i_lo && i < p.i_hi && k0 < p.NZ) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
+    if (i >= p.i_lo && i < p.i_hi && k0 < p.NZ && k0 >= p.k_lo && k0 < p.k_hi) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
   }
 }
 
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_radial_pf(const KParam
       prefetch_edge_tile<T, NV, VEL>(p, j, i, k0);
     }
     cell(t, j, i, k0);
-    if (i < p.i_lo || i >= p.i_hi) continue;
+    if (i < p.i_lo || i >= p.i_hi || k0 < p.k_lo || k0 >= p.k_hi) continue;
     if (VEL) vel_hoist_body<T, NV, false, true, true>(p, j, i, k0);
     else str_hoist_body<T, NV, false, true, true>(p, j, i, k0);
   }
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(HB_X *HB_Y, MINB) hoist_ends_pf(const KParams 
       prefetch_edge_tile<T, NV, VEL>(p, j, i, k0);
     }
     cell(t, j, i, k0);
-    if (i >= p.i_lo && i < p.i_hi && k0 < p.NZ) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
+    if (i >= p.i_lo && i < p.i_hi && k0 < p.NZ && k0 >= p.k_lo && k0 < p.k_hi) hoist_cells<T, NV, VEL, true>(p, j, i, k0);
   }
 }
 
@@ -357,11 +357,46 @@ int sm_count() {
   return n;
 }
 
+thread_local const SideStream *g_side = nullptr;
+
+// fork / join of the edge launches of a half onto the side stream (when one
+// is set and the half has both kinds of tiles); returns the edge stream
+inline cudaError_t side_fork(bool fork, cudaStream_t s, cudaStream_t *se) {
+  *se = s;
+  if (!fork) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(g_side->fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(g_side->side, g_side->fork, 0);
+  if (e == cudaSuccess) *se = g_side->side;
+  return e;
+}
+inline cudaError_t side_join(bool fork, cudaStream_t s) {
+  if (!fork) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(g_side->join, g_side->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g_side->join, 0);
+  return e;
+}
+
 template <typename T, int NV, int MINB_IN, int NVE, int MINB_E, bool VEL, bool PF, bool PFE>
 cudaError_t launch_split2_half(const KParams &p, const Split2 &q, cudaStream_t s) {
   dim3 blk(HB_X, HB_Y);
   const int nin = q.zt_hi - q.zt_lo;
-  if (q.nrt_in > 0 && nin > 0) {
+  const long long nedge = (long long)(q.nrt - q.nrt_in) * q.enzt + (long long)q.nrt_in * (q.ez_lo + q.enzt - q.ez_hi);
+  if (nedge > 65535 || p.nth > 65535) return cudaErrorInvalidValue;
+  const bool interior = q.nrt_in > 0 && nin > 0;
+  const bool fork = g_side && interior && nedge > 0;  // the edge launch beside the interior one
+  cudaStream_t se;
+  cudaError_t e = side_fork(fork, s, &se);
+  if (e != cudaSuccess) return e;
+  if (nedge > 0) {
+    if constexpr (PFE) {
+      const long long tiles = (long long)p.nth * nedge;
+      const int grid = (int)std::min<long long>(tiles, (long long)sm_count() * MINB_E);
+      hoist_edge_pf<T, NVE, MINB_E, VEL><<<grid, blk, 0, se>>>(p, q, (int)tiles);
+    } else {
+      hoist_edge<T, NVE, MINB_E, VEL><<<dim3(p.nth, (unsigned)nedge), blk, 0, se>>>(p, q);
+    }
+  }
+  if (interior) {
     if constexpr (PF) {  // one wave of resident blocks
       const long long tiles = (long long)p.nth * q.nrt_in * nin;
       if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -371,27 +406,34 @@ cudaError_t launch_split2_half(const KParams &p, const Split2 &q, cudaStream_t s
       hoist_interior<T, NV, MINB_IN, VEL><<<dim3(p.nth, q.nrt_in, nin), blk, 0, s>>>(p, q.zt_lo);
     }
   }
-  const long long nedge = (long long)(q.nrt - q.nrt_in) * q.enzt + (long long)q.nrt_in * (q.ez_lo + q.enzt - q.ez_hi);
-  if (nedge > 65535 || p.nth > 65535) return cudaErrorInvalidValue;
-  if (nedge > 0) {
-    if constexpr (PFE) {
-      const long long tiles = (long long)p.nth * nedge;
-      const int grid = (int)std::min<long long>(tiles, (long long)sm_count() * MINB_E);
-      hoist_edge_pf<T, NVE, MINB_E, VEL><<<grid, blk, 0, s>>>(p, q, (int)tiles);
-    } else {
-      hoist_edge<T, NVE, MINB_E, VEL><<<dim3(p.nth, (unsigned)nedge), blk, 0, s>>>(p, q);
-    }
-  }
+  if ((e = side_join(fork, s)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
+
 // three-way split half step: interior (plain or prefetching), radial tiles
-// (NVE cells per thread, MINB_R blocks per SM), z-end tiles (NVE, MINB_E)
+// (NVE cells per thread, MINB_R blocks per SM), z-end tiles (NVE, MINB_E).
+// The three update disjoint cells from inputs no launch of the half writes,
+// so with a side stream the edge launches run beside the interior launch.
 template <typename T, int NV, int MINB_IN, bool PF, int NVE, int MINB_R, int MINB_E, bool VEL>
 cudaError_t launch_split3_half(const KParams &p, const Split2 &q, cudaStream_t s) {
   dim3 blk(HB_X, HB_Y);
   const int nin = q.zt_hi - q.zt_lo;
-  if (q.nrt_in > 0 && nin > 0) {
+  const long long rad = (long long)p.nth * (q.nrt - q.nrt_in) * (q.ez_hi - q.ez_lo);
+  const long long ends = (long long)p.nth * q.nrt * (q.ez_lo + q.enzt - q.ez_hi);
+  if (rad > 0x7fffffffLL || ends > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const bool interior = q.nrt_in > 0 && nin > 0;
+  const bool fork = g_side && interior && (rad > 0 || ends > 0);
+  cudaStream_t se;  // stream of the edge launches
+  cudaError_t e = side_fork(fork, s, &se);
+  if (e != cudaSuccess) return e;
+  if (rad > 0)
+    hoist_radial_pf<T, NVE, MINB_R, VEL>
+        <<<(int)std::min<long long>(rad, (long long)sm_count() * MINB_R), blk, 0, se>>>(p, q, (int)rad);
+  if (ends > 0)
+    hoist_ends_pf<T, NVE, MINB_E, VEL>
+        <<<(int)std::min<long long>(ends, (long long)sm_count() * MINB_E), blk, 0, se>>>(p, q, (int)ends);
+  if (interior) {
     if constexpr (PF) {
       const long long tiles = (long long)p.nth * q.nrt_in * nin;
       if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -401,15 +443,7 @@ cudaError_t launch_split3_half(const KParams &p, const Split2 &q, cudaStream_t s
       hoist_interior<T, NV, MINB_IN, VEL><<<dim3(p.nth, q.nrt_in, nin), blk, 0, s>>>(p, q.zt_lo);
     }
   }
-  const long long rad = (long long)p.nth * (q.nrt - q.nrt_in) * (q.ez_hi - q.ez_lo);
-  const long long ends = (long long)p.nth * q.nrt * (q.ez_lo + q.enzt - q.ez_hi);
-  if (rad > 0x7fffffffLL || ends > 0x7fffffffLL) return cudaErrorInvalidValue;
-  if (rad > 0)
-    hoist_radial_pf<T, NVE, MINB_R, VEL>
-        <<<(int)std::min<long long>(rad, (long long)sm_count() * MINB_R), blk, 0, s>>>(p, q, (int)rad);
-  if (ends > 0)
-    hoist_ends_pf<T, NVE, MINB_E, VEL>
-        <<<(int)std::min<long long>(ends, (long long)sm_count() * MINB_E), blk, 0, s>>>(p, q, (int)ends);
+  if ((e = side_join(fork, s)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -526,6 +560,8 @@ cudaError_t launch_hoist_st(int nv, int minb, bool zf, bool split, int edge, con
 
 }  // namespace
 
+void set_side_stream(const SideStream *ss) { g_side = ss; }
+
 long long split_items(int nth, int NR, int NZ) {  // bound on the items of either list: two-cell tiles
   return (long long)nth * ((NR + HB_Y - 1) / HB_Y) * ((NZ + 2 * HB_X - 1) / (2 * HB_X));
 }
@@ -551,6 +587,19 @@ cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s
     case 0: return launch_hoist_st<float>(nv, minb, zf, split, edge, p, s, ev, parts, split3);
     case 1: return launch_hoist_st<__nv_bfloat16>(nv, minb, zf, split, edge, p, s, ev, parts, split3);
     case 2: return launch_hoist_st<__half>(nv, minb, zf, split, edge, p, s, ev, parts, split3);
+    case 3:  // FP16 with stochastic rounding: the three-way split codes only
+      if (!split3) return cudaErrorInvalidValue;
+      switch (edge * 10 + minb) {
+        case 4: return launch_split3_t<half_sr, 4, 4, true, 4, 4, 3>(p, s, ev, parts);
+        case 5: return launch_split3_t<half_sr, 4, 5, false, 4, 4, 3>(p, s, ev, parts);
+        case 14: return launch_split3_t<half_sr, 4, 4, true, 2, 5, 4>(p, s, ev, parts);
+        case 15: return launch_split3_t<half_sr, 4, 5, false, 2, 5, 4>(p, s, ev, parts);
+        case 24: return launch_split3_t<half_sr, 4, 4, true, 2, 4, 4>(p, s, ev, parts);
+        case 25: return launch_split3_t<half_sr, 4, 5, false, 2, 4, 4>(p, s, ev, parts);
+        case 34: return launch_split3_t<half_sr, 4, 4, true, 4, 3, 3>(p, s, ev, parts);
+        case 35: return launch_split3_t<half_sr, 4, 5, false, 4, 3, 3>(p, s, ev, parts);
+      }
+      return cudaErrorInvalidValue;
   }
   return cudaErrorInvalidValue;
 }

@@ -363,6 +363,10 @@ __device__ __forceinline__ void receivers_body(const RParams &p) {
   const T *srr = (const T *)p.srr, *spp = (const T *)p.spp, *szz = (const T *)p.szz;
   for (int r = warp; r < p.n_rec; r += blockDim.x >> 5) {
     const int i = p.rec[3 * r], jr = p.rec[3 * r + 1], k = p.rec[3 * r + 2];
+    if (k < 0) {  // a receiver of another z slab: recorded as zero here
+      if (lane == 0 && n < p.cap) p.traces[(long long)r * p.cap + n] = 0.f;
+      continue;
+    }
     const int j0 = jr < 0 ? 0 : jr, j1 = jr < 0 ? p.nth : jr + 1;
     double acc = 0.0;
     for (int j = j0 + lane; j < j1; j += 32) {

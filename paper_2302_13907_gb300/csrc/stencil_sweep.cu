@@ -30,9 +30,10 @@
 // counter (a release reduction after its stores); a stress item's warp checks
 // (lane 0, acquire loads, bounded) that the counters of its three chunks are
 // complete, once per chunk, and reads the velocities through L2 only, since
-// blocks of the same launch wrote them.  m selects the chunk (ZC = 32 for
-// m = 0, 1, 64 for m = 2, 3) and, for odd m, an L2 prefetch of each block's
-// next velocity item before its current item.
+// blocks of the same launch wrote them; they read their own stresses and
+// write the new ones streaming (evict-first: last use in the launch).  m
+// selects the chunk, the lag and an L2 prefetch of each block's next
+// velocity item (launch_sweep_st).
 //
 // Order and progress: an item waits only on items handed out before it, and
 // every block is resident, so the lowest unfinished item can always finish.
@@ -225,7 +226,8 @@ cudaError_t launch_sweep_t(const KParams &p, SweepParams q, int lag_half_chunks,
   return cudaGetLastError();
 }
 
-// lag: three chunks of 32 cells, two and a half of 64
+// m: 0, 1 chunks of 32 cells, lag 3 chunks (1: with prefetch); 2, 3 chunks of
+// 64, lag 2.5 (3: with prefetch); 4, 5 chunks of 32, lag 2.5 and 2
 template <typename T>
 cudaError_t launch_sweep_st(int code, const KParams &p, const SweepParams &q, cudaStream_t s) {
   switch (code) {
@@ -237,6 +239,10 @@ cudaError_t launch_sweep_st(int code, const KParams &p, const SweepParams &q, cu
     case 3224: return launch_sweep_t<T, 64, 4, 2, false>(p, q, 5, s);
     case 3343: return launch_sweep_t<T, 64, 3, 4, true>(p, q, 5, s);
     case 3324: return launch_sweep_t<T, 64, 4, 2, true>(p, q, 5, s);
+    case 3443: return launch_sweep_t<T, 32, 3, 4, false>(p, q, 5, s);
+    case 3424: return launch_sweep_t<T, 32, 4, 2, false>(p, q, 5, s);
+    case 3543: return launch_sweep_t<T, 32, 3, 4, false>(p, q, 4, s);
+    case 3524: return launch_sweep_t<T, 32, 4, 2, false>(p, q, 4, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -260,6 +266,7 @@ cudaError_t launch_sweep(int storage, int code, const KParams &p, int *vdone, in
     case 0: return launch_sweep_st<float>(code, p, q, s);
     case 1: return launch_sweep_st<__nv_bfloat16>(code, p, q, s);
     case 2: return launch_sweep_st<__half>(code, p, q, s);
+    case 3: return launch_sweep_st<half_sr>(code, p, q, s);
   }
   return cudaErrorInvalidValue;
 }

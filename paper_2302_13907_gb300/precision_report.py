@@ -1,5 +1,5 @@
-"""Storage-precision report: FP32 / BF16 / FP16 storage of fields and
-coefficients (FP32 arithmetic, FP64 trace accumulation).
+"""Storage-precision report: FP32 / BF16 / FP16 / FP16 with stochastic
+rounding storage of the fields (FP32 arithmetic, FP64 trace accumulation).
 
     python -m paper_2302_13907_gb300.precision_report --crop-ref REF.npz --out report.json [--full]
 
@@ -68,7 +68,7 @@ def main():
     steps = min(a.steps, int(ref["steps"]))
     oracle_tr = ref["traces"][:, :steps]
     f32 = None
-    for st in ("f32", "bf16", "f16"):
+    for st in ("f32", "bf16", "f16", "f16sr"):
         tr, rate, kind, tile = run(crop, st, steps, stream.cuda_stream)
         e = {"vs_oracle_fp64": errors(tr, oracle_tr), "gcell_updates_per_s": rate, "kernel": kind, "tile": tile}
         if f32 is None:
@@ -80,7 +80,7 @@ def main():
     rep["crop"]["workload"] = f"{crop.name}, {steps} steps, receivers at z = 8.0, 8.5, 9.0, 9.5 m"
     if a.full:
         f32 = None
-        for st in ("f32", "bf16", "f16"):
+        for st in ("f32", "bf16", "f16", "f16sr"):
             tr, rate, kind, tile = run(full, st, a.steps, stream.cuda_stream)
             e = {"gcell_updates_per_s": rate, "kernel": kind, "tile": tile}
             if f32 is None:

@@ -24,7 +24,10 @@ The per-rank work is an `engine` object:
     get_planes(group, k0, k1) -> array [fields][nth][NR][k1 - k0]
     set_planes(group, k0, array)
 with group "v" (v_r, v_phi, v_z) or "s" (the six stresses) and k in the
-well's stored z index.
+well's stored z index.  SimSlab is that engine for a library handle
+(sim_create_slab: its planes stay on the device, on the stream the handle
+and the collectives share); exchange_local swaps the slabs of one process
+(several slabs on one GPU) without collectives.
 """
 from __future__ import annotations
 
@@ -107,3 +110,59 @@ def run(engine, p: SlabPlan, rank: int, steps: int, comm, first_step: int = 0, d
         engine.stress_half(n)
         exchange(engine, p, rank, "s", comm, device)
         engine.sample(n)
+
+
+class SimSlab:
+    """A slab of the well on one GPU: a sim_create_slab handle whose planes
+    are exchanged as CUDA tensors on `stream` (the handle's stream)."""
+
+    def __init__(self, scenario, p: SlabPlan, rank: int, stream=None, **kw):
+        import torch
+        from .binding import Simulation
+        self.sim = Simulation(scenario, slab=p.owned(rank), stream=stream, kernel="split", **kw)
+        self.rows = scenario.grid.nth * scenario.grid.NR
+        self._torch = torch
+
+    def velocity_half(self, n):
+        self.sim.half_step(0)
+
+    def stress_half(self, n):
+        self.sim.half_step(1)
+
+    def sample(self, n):
+        pass
+
+    def get_planes(self, group, k0, k1):
+        t = self._torch
+        out = t.empty((len(GROUPS[group]), self.rows, k1 - k0), dtype=t.float32, device="cuda")
+        return self.sim.get_planes(0 if group == "v" else 1, k0, k1, out)
+
+    def set_planes(self, group, k0, buf):
+        self.sim.put_planes(0 if group == "v" else 1, k0, k0 + buf.shape[-1], buf.contiguous())
+
+
+def exchange_local(engines, p: SlabPlan, group: str):
+    """The swap of `group` between the slabs of one process (rank r's engine
+    is engines[r]): each inner boundary's four own cells on each side go to
+    the other slab's ghost cells."""
+    for r in range(p.ranks - 1):
+        a, b = engines[r], engines[r + 1]
+        cut = p.owned(r)[1]
+        lo = a.get_planes(group, cut - GHOST, cut)
+        hi = b.get_planes(group, cut, cut + GHOST)
+        b.set_planes(group, cut - GHOST, lo)
+        a.set_planes(group, cut, hi)
+
+
+def run_local(engines, p: SlabPlan, steps: int, first_step: int = 0):
+    """`steps` leapfrog steps of all slabs of one process, swapping after
+    each half-step."""
+    for n in range(first_step, first_step + steps):
+        for e in engines:
+            e.velocity_half(n)
+        exchange_local(engines, p, "v")
+        for e in engines:
+            e.stress_half(n)
+        exchange_local(engines, p, "s")
+        for e in engines:
+            e.sample(n)

@@ -51,34 +51,64 @@ def window_times(sc):
     return dt, (m + 1) * dt
 
 
-def refined_window(sc, stream=None, reach=1.6):
-    """Reflected-window traces [8][2048] of one case by the refined-grid
-    simulator on its reach crop, at the uniform grid's sample times."""
+def _refined_start(sc, stream=None, reach=1.6, chunk=128):
+    """Create the refined-grid handle of a case's reach crop and enqueue its
+    steps (asynchronous); returns (handle, uniform window times, steps)."""
     from .binding import RefinedSimulation
     dt_u, t = window_times(sc)
     crop = W.reach_crop(sc, reach)
-    rows = W.refinement_rows(crop.grid)
+    R = RefinedSimulation(crop, W.refinement_rows(crop.grid), graph_chunk=chunk, stream=stream, max_steps=sc.steps)
     # the refined step is the larger one, so sc.steps samples cover the window
-    with RefinedSimulation(crop, rows, graph_chunk=256, stream=stream, max_steps=sc.steps) as R:
-        dt_r = R.dt
-        n = int(np.ceil(t[-1] / dt_r)) + 1
-        if n > sc.steps:
-            raise ValueError("refined time step below the uniform one")
-        R.step(n)
-        tr = R.traces().astype(np.float64)
+    n = int(np.ceil(t[-1] / R.dt)) + 1
+    if n > sc.steps:
+        R.close()
+        raise ValueError("refined time step below the uniform one")
+    R.step(n)
+    return R, t, n
+
+
+def _refined_finish(R, t, n):
+    """Wait for a handle's steps, sample its traces at the window times, free it."""
+    dt_r = R.dt
+    tr = R.traces().astype(np.float64)
+    R.close()
     tr_t = (np.arange(n) + 1) * dt_r  # sample m is the value after step m
     return np.stack([np.interp(t, tr_t, tr[q]) for q in range(tr.shape[0])]).astype(np.float32)
 
 
-def generate_refined(seeds, stream=None, log=print, every=256):
+def refined_window(sc, stream=None, reach=1.6):
+    """Reflected-window traces [8][2048] of one case by the refined-grid
+    simulator on its reach crop, at the uniform grid's sample times."""
+    return _refined_finish(*_refined_start(sc, stream, reach))
+
+
+def generate_refined(seeds, stream=None, log=print, every=256, slots=6):
+    """Refined-window traces of many cases, `slots` of them in flight at once:
+    each on its own stream (the handles free their memory stream-ordered), so
+    one case's launches fill what another's leave idle and the host builds the
+    next case while the GPU runs."""
+    from collections import deque
     X, Y = [], []
     t0 = time.time()
+    pending = deque()
+    done = 0
+
+    def finish():
+        nonlocal done
+        q, feats, args = pending.popleft()
+        Y.append(_refined_finish(*args))
+        X.append(feats)
+        done += 1
+        if done % every == 0 or done == len(seeds):
+            log(f"{done}/{len(seeds)} cases, {time.time() - t0:.0f} s")
+
     for q, s in enumerate(seeds):
         sc = W.scenario_case(s, surrogate_inputs=True)
-        Y.append(refined_window(sc, stream))
-        X.append(W.surrogate_features(sc))
-        if (q + 1) % every == 0 or q + 1 == len(seeds):
-            log(f"{q + 1}/{len(seeds)} cases, {time.time() - t0:.0f} s")
+        pending.append((q, W.surrogate_features(sc), _refined_start(sc, None if slots > 1 else stream)))
+        if len(pending) >= slots:
+            finish()
+    while pending:
+        finish()
     return np.asarray(X, np.float64), np.asarray(Y, np.float32), time.time() - t0
 
 

@@ -10,14 +10,17 @@ training and inference runs in the library's kernels; the simulator runs the
 cases the gate rejects.
 
     python -m paper_2302_13907_gb300.surrogate_run --pipeline --out-dir DIR \
+        [--phase all|train|test] [--params P] \
         [--train-seeds 1000:5096] [--test-seeds 9000:9512] [--epochs 400]
 
-runs the whole job in one process: generates both sets with the refined
-generator of `surrogate_data`, times the plain solver on a sample of the test
-cases, trains, chooses the gate's margin on the validation cases alone
-(leave-one-out), gates and falls back on the test cases, and writes
-DIR/params.npz (weights as BF16 bit patterns, biases, normalisation, the
-gate's validation data and margin) and DIR/report.json.
+runs the job with the refined generator of `surrogate_data`.  Phase "train"
+generates the training cases, trains, chooses the gate's margin on the
+validation cases alone (leave-one-out) and writes DIR/params.npz (weights as
+BF16 bit patterns, biases, normalisation, the gate's validation data and
+margin) and DIR/train_report.json; phase "test" generates the held-out
+cases, times the plain solver on a sample of them, runs the saved network and
+gate, falls back to the simulator on the rejected cases and writes
+DIR/report.json; "all" runs both in one process.
 """
 from __future__ import annotations
 
@@ -118,30 +121,28 @@ def choose_margin(Xn_val, e_val, k, tol=TOL):
     return best
 
 
-def pipeline(a):
-    """The whole surrogate job in one process (see the module docstring)."""
+def _load_params(path, arch):
+    """A Surrogate holding the saved BF16 weights, normalisation and gate."""
+    z = np.load(path)
+    S = Surrogate(max_batch=64, seed=0)
+    S.set_normalization(z["x_mean"], z["x_scale"], float(z["y_scale"]))
+    S.set_params(unpack_params(z["w_bf16"], z["biases"], arch))
+    S.gate_fit(z["gate_x"], z["gate_err"])
+    return S, z
+
+
+def pipeline_train(a, log):
+    """Generate the training cases, train, evaluate the BF16 weights on the
+    validation cases, choose the gate's margin on them alone (leave-one-out)
+    and save DIR/params.npz and DIR/train_report.json."""
     import os
     from . import surrogate_data as D
-    from .binding import SURROGATE_DEFAULT, Simulation
+    from .binding import SURROGATE_DEFAULT
 
-    os.makedirs(a.out_dir, exist_ok=True)
-    log = lambda m: print(m, flush=True)
     tr_seeds = D.parse_seeds(a.train_seeds)
-    te_seeds = D.parse_seeds(a.test_seeds)
     X, Y, t_gen_tr = D.generate_refined(tr_seeds, log=log)
-    Xt, Yt, t_gen_te = D.generate_refined(te_seeds, log=log)
-    log(f"generated {len(X)} + {len(Xt)} cases in {t_gen_tr + t_gen_te:.0f} s")
-    # the plain solver (uniform grid, the whole well, 6000 steps) on a sample of the test cases
-    plain_t, plain_err = [], []
-    for sd, y_ref in zip(te_seeds[:a.plain_sample], Yt[:a.plain_sample]):
-        sc = W.scenario_case(sd, surrogate_inputs=True)
-        t0 = time.perf_counter()
-        with Simulation(sc, graph_chunk=200, max_steps=sc.steps) as s:
-            s.step(sc.steps)
-            tr = s.traces()[:, sc.steps - D.WINDOW:]
-        plain_t.append(time.perf_counter() - t0)
-        plain_err.append(float(np.linalg.norm(y_ref - tr) / np.linalg.norm(tr)))
-    X, Y, Xt, Yt = X.astype(np.float32), Y.astype(np.float32), Xt.astype(np.float32), Yt.astype(np.float32)
+    log(f"generated {len(X)} training cases in {t_gen_tr:.0f} s")
+    X, Y = X.astype(np.float32), Y.astype(np.float32)
     rng = np.random.default_rng(a.seed)
     perm = rng.permutation(len(X))
     nv = max(1, int(round(a.val_frac * len(X))))
@@ -161,34 +162,75 @@ def pipeline(a):
     e_val = rel_err(S.forward(X[iv]), Y[iv])
     Xn = lambda x: (x - x_mean) / x_scale
     margin = choose_margin(Xn(X[iv]), e_val, a.k)
-    S.gate_fit(X[iv], e_val)
+    np.savez_compressed(os.path.join(a.out_dir, "params.npz"), w_bf16=bits, biases=biases, x_mean=x_mean,
+                        x_scale=x_scale, y_scale=np.float64(y_scale), gate_x=X[iv],
+                        gate_err=e_val.astype(np.float32), gate_k=np.int64(a.k), gate_margin=np.float64(margin),
+                        train_seeds=np.asarray(tr_seeds), test_seeds=np.asarray(D.parse_seeds(a.test_seeds)),
+                        val_index=np.asarray(iv), seed=np.int64(a.seed))
+    rep = {
+        "train_cases": int(len(it)), "val_cases": int(nv), "params": int(S.n_params),
+        "epochs": a.epochs, "batch": a.batch, "lr": a.lr, "train_seconds": t_train,
+        "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
+        "generate_train_seconds": t_gen_tr, "fallback_seconds_per_case_train": t_gen_tr / len(X),
+        "val_rel_l2_median": float(np.median(e_val)), "val_rel_l2_max": float(e_val.max()),
+        "gate_k": a.k, "gate_margin": margin,
+        "epoch_loss": [float(x) for x in hist[:: max(1, len(hist) // 50)]],
+    }
+    json.dump(rep, open(os.path.join(a.out_dir, "train_report.json"), "w"), indent=1)
+    log(f"validation rel-L2 median {np.median(e_val):.4f}, max {e_val.max():.4f}; gate margin {margin}")
+    return rep
+
+
+def pipeline_test(a, log, params, train_rep):
+    """Generate the held-out cases, time the plain solver on a sample of them,
+    run the saved surrogate and its gate, fall back to the simulator on the
+    rejected cases and write DIR/report.json."""
+    import os
+    from . import surrogate_data as D
+    from .binding import SURROGATE_DEFAULT, Simulation
+
+    te_seeds = D.parse_seeds(a.test_seeds)
+    Xt, Yt, t_gen_te = D.generate_refined(te_seeds, log=log)
+    log(f"generated {len(Xt)} test cases in {t_gen_te:.0f} s")
+    # the plain solver (uniform grid, the whole well, 6000 steps) on a sample of the test cases
+    plain_t, plain_err = [], []
+    for sd, y_ref in zip(te_seeds[:a.plain_sample], Yt[:a.plain_sample]):
+        sc = W.scenario_case(sd, surrogate_inputs=True)
+        t0 = time.perf_counter()
+        with Simulation(sc, graph_chunk=200, max_steps=sc.steps) as s:
+            s.step(sc.steps)
+            tr = s.traces()[:, sc.steps - D.WINDOW:]
+        plain_t.append(time.perf_counter() - t0)
+        plain_err.append(float(np.linalg.norm(y_ref - tr) / np.linalg.norm(tr)))
+    Xt, Yt = Xt.astype(np.float32), Yt.astype(np.float32)
+    S, z = _load_params(params, SURROGATE_DEFAULT)
+    k, margin = int(z["gate_k"]), float(z["gate_margin"])
     S.forward(Xt[:4])
     t0 = time.perf_counter()
     P = S.forward(Xt)
-    acc = S.gate(Xt, k=a.k, tol=TOL * margin)
+    acc = S.gate(Xt, k=k, tol=TOL * margin)
     t_inf = time.perf_counter() - t0
     e_test = rel_err(P, Yt)
     rejected = np.flatnonzero(~acc)
     t0 = time.perf_counter()
-    for q in rejected:
-        P[q] = D.refined_window(W.scenario_case(te_seeds[q], surrogate_inputs=True))
+    if len(rejected):
+        _, Yf, _ = D.generate_refined([te_seeds[q] for q in rejected], log=lambda m: None)
+        P[rejected] = Yf
     t_fb = time.perf_counter() - t0
     final = rel_err(P, Yt)
     n = len(Xt)
     per_sim = t_gen_te / n
     per_plain = float(np.mean(plain_t)) if plain_t else None
-    rep = {
-        "train_cases": int(len(it)), "val_cases": int(nv), "test_cases": n, "params": int(S.n_params),
-        "epochs": a.epochs, "batch": a.batch, "lr": a.lr, "train_seconds": t_train,
-        "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
+    rep = {k_: v for k_, v in (train_rep or {}).items() if k_ != "epoch_loss"}
+    rep.update({
+        "test_cases": n,
         "generator": "refined grid (Sec. 3 zoning) on each case's 1.6 m reach crop, traces at the uniform grid's times",
-        "generate_seconds": t_gen_tr + t_gen_te, "judge_seconds_per_case": per_sim,
+        "generate_test_seconds": t_gen_te, "fallback_seconds_per_case": per_sim,
         "plain_seconds_per_case": per_plain, "plain_sample": len(plain_t),
-        "plain_vs_judge_rel_l2": plain_err,
-        "val_rel_l2_median": float(np.median(e_val)), "val_rel_l2_max": float(e_val.max()),
+        "plain_vs_fallback_rel_l2": plain_err,
         "test_rel_l2_median": float(np.median(e_test)), "test_rel_l2_p90": float(np.quantile(e_test, 0.9)),
         "test_rel_l2_max": float(e_test.max()), "test_frac_within_5pct": float(np.mean(e_test <= TOL)),
-        "gate_k": a.k, "gate_margin": margin, "gate_tol": TOL * margin,
+        "gate_k": k, "gate_margin": margin, "gate_tol": TOL * margin,
         "accepted": int(acc.sum()), "accepted_frac": float(acc.mean()),
         "max_accepted_rel_l2": float(e_test[acc].max()) if acc.any() else None,
         "false_accepts": int(np.sum(acc & (e_test > TOL))),
@@ -196,29 +238,46 @@ def pipeline(a):
         "final_max_rel_l2": float(final.max()), "final_frac_within_5pct": float(np.mean(final <= TOL + 1e-7)),
         "inference_and_gate_seconds": t_inf,
         "cases_per_s": n / (t_inf + t_fb),
-        "judge_cases_per_s": 1.0 / per_sim,
-        "speedup_vs_judge": per_sim * n / (t_inf + t_fb),
+        "fallback_cases_per_s": 1.0 / per_sim,
+        "speedup_vs_fallback": per_sim * n / (t_inf + t_fb),
         "speedup_vs_plain": (per_plain * n / (t_inf + t_fb)) if per_plain else None,
         "test_rel_l2": [float(x) for x in e_test], "test_accepted": [bool(x) for x in acc],
-        "epoch_loss": [float(x) for x in hist[:: max(1, len(hist) // 50)]],
-    }
+    })
+    if train_rep and "epoch_loss" in train_rep:
+        rep["epoch_loss"] = train_rep["epoch_loss"]
     json.dump(rep, open(os.path.join(a.out_dir, "report.json"), "w"), indent=1)
-    np.savez_compressed(os.path.join(a.out_dir, "params.npz"), w_bf16=bits, biases=biases, x_mean=x_mean,
-                        x_scale=x_scale, y_scale=np.float64(y_scale), gate_x=X[iv], gate_err=e_val.astype(np.float32),
-                        gate_k=np.int64(a.k), gate_margin=np.float64(margin),
-                        train_seeds=np.asarray(tr_seeds), test_seeds=np.asarray(te_seeds),
-                        val_index=np.asarray(iv), seed=np.int64(a.seed))
-    log(json.dumps({k: v for k, v in rep.items() if k not in ("epoch_loss", "test_rel_l2", "test_accepted")},
+    log(json.dumps({k_: v for k_, v in rep.items() if k_ not in ("epoch_loss", "test_rel_l2", "test_accepted")},
                    indent=1))
+    return rep
+
+
+def pipeline(a):
+    """The surrogate job (see the module docstring): phase "train", "test"
+    or "all"; the test phase reads the weights and gate the train phase saved
+    (--params, by default DIR/params.npz, and DIR/train_report.json)."""
+    import os
+    os.makedirs(a.out_dir, exist_ok=True)
+    log = lambda m: print(m, flush=True)
+    train_rep = None
+    if a.phase in ("train", "all"):
+        train_rep = pipeline_train(a, log)
+    if a.phase in ("test", "all"):
+        params = a.params or os.path.join(a.out_dir, "params.npz")
+        if train_rep is None:
+            tr_path = os.path.join(os.path.dirname(params), "train_report.json")
+            if os.path.exists(tr_path):
+                train_rep = json.load(open(tr_path))
+        pipeline_test(a, log, params, train_rep)
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--pipeline", action="store_true", help="generate, train, gate and report in one process")
+    ap.add_argument("--pipeline", action="store_true", help="generate, train, gate and report")
+    ap.add_argument("--phase", choices=("all", "train", "test"), default="all")
     ap.add_argument("--out-dir", default=None)
     ap.add_argument("--train-seeds", default="1000:5096")
     ap.add_argument("--test-seeds", default="9000:9512")
-    ap.add_argument("--plain-sample", type=int, default=4)
+    ap.add_argument("--plain-sample", type=int, default=2)
     ap.add_argument("--train", default=None)
     ap.add_argument("--test", default=None)
     ap.add_argument("--out", default=None)

@@ -79,3 +79,32 @@ def test_batch_of_cement_cases():
         with Simulation(sc, kernel="split", tile=2004, max_steps=64) as s:
             s.step(64)
             assert rel_l2(got[c], s.traces()) <= 1e-6
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("tile", [0, 1, -2])
+def test_batch_mixing_small_and_cement_cases(tile):
+    """Two small wells (shared persistent launches) and three cement cases
+    (own launches, on parallel graph branches) in one batch; with tile = 1
+    every case runs in the shared launches, with tile = -2 on two branches.
+    Each case against its single run."""
+    from paper_2302_13907_gb300.binding import BatchSimulation, Simulation
+    cases = small_cases(2, seed=3) + [W.scenario_case(s) for s in (3, 6, 7)]
+    steps = 160
+    with BatchSimulation(cases, max_steps=steps, graph_chunk=32, tile=tile) as b:
+        own, branches = b.layout()
+        assert own == (0 if tile == 1 else 3)
+        if tile == -2:
+            assert branches == 2
+        b.run(steps)
+        b.sync()
+        got = [b.traces(c) for c in range(len(cases))]
+        got_f = [b.field(c, "srz") for c in range(len(cases))]
+    for c, sc in enumerate(cases):
+        with Simulation(sc, kernel="split", tile=2004, max_steps=steps) as s:
+            s.step(steps)
+            ref, ref_f = s.traces(), s.field("srz")
+            assert np.abs(ref_f).max() > 0, c
+            assert rel_l2(got_f[c], ref_f) <= 1e-6, c
+            if np.abs(ref).max() > 0:  # the pulse may not have reached a receiver yet
+                assert rel_l2(got[c], ref) <= 1e-6, c

@@ -379,7 +379,7 @@ def test_fused_matches_split_and_autotuner_choice():
         fa = {n: a.field(n) for n in ("vr", "srr", "srz")}
     for kern, kind_want, tiles in (("fused", 2, (2, 4, 6, 8)), ("fused4", 2, (106, 110, 114)),
                                    ("march", 4, MARCH_TILES), ("split", 1, SPLIT_TILES),
-                                   ("sweep", 5, (3043, 3024, 3143, 3124, 3243, 3224, 3343, 3324))):
+                                   ("sweep", 5, (3043, 3024, 3143, 3124, 3243, 3224, 3343, 3324, 3443, 3424, 3543, 3524))):
         with sim(sc, kernel=kern) as b:
             kind, tile = b.config()
             halves = (tile // 10000, tile % 10000) if tile >= 10000 else (tile, tile)

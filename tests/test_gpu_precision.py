@@ -66,21 +66,24 @@ def test_reduced_storage_error_is_finite_and_ordered(crop):
     sc, ref = crop
     n = int(ref["steps"])
     err = {}
-    for storage in ("bf16", "f16"):
+    for storage in ("bf16", "f16", "f16sr"):
         with Simulation(sc, storage=storage, max_steps=n, graph_chunk=200) as s:
             s.step(n)
             got = s.traces()
         assert np.all(np.isfinite(got)), storage
         assert np.abs(got).max() > 0, storage
         err[storage] = rel_l2(got, ref["traces"])
+    print("rel-L2 vs FP64 oracle:", err)
     assert err["f16"] < err["bf16"], err
     assert err["f16"] <= 0.16 and err["bf16"] <= 0.8, err
+    # stochastic rounding keeps the increments a nearest rounding loses
+    assert err["f16sr"] < err["f16"], err
 
 
 def _ulp(x, storage):
     """Spacing of the storage format at |x| (normal range; FP16 subnormals
     below 2^-14 keep the spacing 2^-24)."""
-    p, emin = (8, -126) if storage == "bf16" else (11, -14)
+    p, emin = (8, -126) if storage == "bf16" else (11, -14)  # FP16 for "f16" and "f16sr"
     e = np.floor(np.log2(np.maximum(np.abs(x), 2.0 ** emin)))
     return 2.0 ** (e - (p - 1))
 
@@ -91,13 +94,15 @@ def _ulp(x, storage):
 # increment where its terms (radial, azimuthal and z differences) nearly
 # cancel (a field near rest), so the share of such values grows with the
 # format's resolution: measured 0 of 3.2 M for BF16 and 0.4 % for FP16
-# (1.8 % of the velocities, none of the stresses).  The bounds leave room
+# (1.8 % of the velocities, none of the stresses); stochastic rounding puts
+# its boundary anywhere in the spacing, so values that stagnate near a grid
+# point can flip too (3.4 % of v_r measured).  The bounds leave room
 # for a kernel with another FP32 operation order; a value more than one ulp
 # apart fails outright.
-FLIP_FRACTION = {"bf16": 1e-3, "f16": 1e-2}
+FLIP_FRACTION = {"bf16": 1e-3, "f16": 1e-2, "f16sr": 3e-2}
 
 
-@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("storage", ["bf16", "f16", "f16sr"])
 def test_reduced_storage_step_matches_the_rounded_oracle(storage):
     """One leapfrog step of the GPU's 16-bit storage path against one step of
     the oracle with the same storage rounding, both started from the GPU's
@@ -114,7 +119,7 @@ def test_reduced_storage_step_matches_the_rounded_oracle(storage):
     import oracle
     from paper_2302_13907_gb300.binding import Simulation
     sc = W.config1(steps=701)
-    scales = fp16_scales(sc) if storage == "f16" else (1.0, 1.0)
+    scales = fp16_scales(sc) if storage in ("f16", "f16sr") else (1.0, 1.0)
     n = 700
     with Simulation(sc, storage=storage, pml_on=False) as s:
         s.step(n)
@@ -127,14 +132,14 @@ def test_reduced_storage_step_matches_the_rounded_oracle(storage):
     for q, f in enumerate(oracle.FIELDS):
         sc_f = scales[0] if q < 3 else scales[1]
         # the stored representation is recovered exactly by rounding (read-back error << half an ulp)
-        stored = oracle.round_storage(before[f] * sc_f, storage)
+        stored = oracle.round_storage(before[f] * sc_f, "f16" if storage == "f16sr" else storage)
         assert np.allclose(stored, before[f] * sc_f, rtol=1e-6, atol=0), f
         o.field(f)[...] = stored / sc_f
     o.step(1)
     total = diff = 0
     for q, f in enumerate(oracle.FIELDS):
         sc_f = scales[0] if q < 3 else scales[1]
-        g = oracle.round_storage(after[f] * sc_f, storage)
+        g = oracle.round_storage(after[f] * sc_f, "f16" if storage == "f16sr" else storage)
         r = o.field(f) * sc_f
         d = np.abs(g - r)
         big = d > 1.0000001 * _ulp(np.maximum(np.abs(g), np.abs(r)), storage)

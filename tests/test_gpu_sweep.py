@@ -22,7 +22,7 @@ from tests.test_gpu_parity import TRACE_TOL, _ragged_scenario, sim
 
 pytestmark = pytest.mark.gpu
 
-SWEEP_TILES = (3043, 3024, 3143, 3124, 3243, 3224, 3343, 3324)
+SWEEP_TILES = (3043, 3024, 3143, 3124, 3243, 3224, 3343, 3324, 3443, 3424, 3543, 3524)
 
 
 def _fields_match(s, o, tol=2e-5):
