@@ -44,7 +44,7 @@ extern "C" {
 #define SIM_EINVAL (-1)      /* invalid argument, checked on the host before any device work */
 #define SIM_ENOMEM (-2)      /* device allocation failed or opts.mem_cap exceeded */
 #define SIM_ECUDA (-3)       /* a CUDA runtime call failed */
-#define SIM_EUNSTABLE (-4)   /* non-finite value detected in the receiver traces */
+#define SIM_EUNSTABLE (-4)   /* non-finite value in the receiver traces, or the watchdog tripped */
 #define SIM_ETIMEOUT (-5)    /* a bounded device-side wait gave up */
 #define SIM_EUNSUPPORTED (-6) /* e.g. a solid (mu > 0) cell in ring 0 next to the axis */
 
@@ -141,6 +141,15 @@ typedef struct {
                          (see sim_config) of the requested kernel to run,
                          SIM_EINVAL if that kernel has no such tile or it does
                          not fit in shared memory */
+  int watchdog_every; /* K > 0: a device watchdog after every K-th full step (sim_step) sums the
+                         energy proxy 1/2 sum [rho |v|^2 + (s_rr^2 + s_pp^2 + s_zz^2 + 2 (s_rp^2 +
+                         s_pz^2 + s_rz^2)) / (lambda + 2 mu)] over the owned cells (physical units,
+                         each cell's material); it trips when the proxy is not finite, or exceeds 100
+                         times its first value once the source wavelet has ended (the energy of
+                         Eq. 1 with the PML cannot grow then; the proxy stays within a factor of
+                         about 0.3 to 3 of it), and sim_sync then returns SIM_EUNSTABLE.  Two
+                         launches per step that return at once on the other steps.  0 = off;
+                         < 0 SIM_EINVAL; batches and the refined grid: SIM_EUNSUPPORTED */
 } sim_opts_t;
 
 typedef struct sim_s sim_t;
@@ -232,6 +241,25 @@ int sim_write_field(sim_t *h, int which, const float *in, size_t n);
  * on the host without any device call.  SIM_EINVAL for a malformed grid or
  * an out-of-range material ID; the message is sim_last_error(NULL). */
 int sim_time_step(const sim_grid_t *grid, const sim_medium_t *medium, double *dt);
+
+/* The device watchdog's last energy proxy, its reference (the first proxy
+ * after the source wavelet ended; 0 until then) and the step of the last
+ * check (see opts.watchdog_every).  Synchronises the handle's stream; any
+ * output pointer may be NULL.  SIM_EINVAL when the watchdog is off.
+ * sim_load restarts the reference. */
+int sim_watchdog(sim_t *h, double *energy, double *reference, int *step);
+
+/* The stochastic rounding of the FP16-SR storage (SIM_STORAGE_F16_SR) applied
+ * to n FP32 values, for checking it value by value: out[q] = the FP16 bit
+ * pattern of x[q] rounded up in magnitude when the 13 bits that FP16 drops
+ * below its spacing u, read as frac(|x| / u) * 8192, exceed dither[q] & 0x1fff
+ * (u = 2^-24 below 2^-14, the same rule on the exact frac there); zero,
+ * non-finite values and magnitudes beyond 65504 round to nearest.  x, dither
+ * and out are DEVICE pointers of n elements, owned by the caller;
+ * cuda_stream: the stream to run on (NULL = the default stream), synchronised
+ * before return.  SIM_EINVAL for n < 0 or a null pointer with n > 0,
+ * SIM_ECUDA for a launch failure. */
+int sim_round_f16_sr(const float *x, const unsigned *dither, unsigned short *out, long long n, void *cuda_stream);
 
 /* Time step in seconds, steps done so far, device bytes held. */
 double sim_dt(const sim_t *h);

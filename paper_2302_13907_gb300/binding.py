@@ -45,7 +45,8 @@ class SimReceivers(ctypes.Structure):
 class SimOpts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("pml_off", ctypes.c_int), ("graph_chunk", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("mem_cap", ctypes.c_size_t), ("max_steps", ctypes.c_int),
-                ("kernel", ctypes.c_int), ("timing", ctypes.c_int), ("device", ctypes.c_int), ("tile", ctypes.c_int)]
+                ("kernel", ctypes.c_int), ("timing", ctypes.c_int), ("device", ctypes.c_int), ("tile", ctypes.c_int),
+                ("watchdog_every", ctypes.c_int)]
 
 
 class SimZones(ctypes.Structure):
@@ -91,6 +92,10 @@ def lib(path: str | None = None):
         L.sim_set_wait_test.restype = i
         L.sim_time_step.argtypes = [p, p, ctypes.POINTER(ctypes.c_double)]
         L.sim_time_step.restype = i
+        L.sim_watchdog.argtypes = [p, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(i)]
+        L.sim_watchdog.restype = i
+        L.sim_round_f16_sr.argtypes = [p, p, p, ctypes.c_longlong, p]
+        L.sim_round_f16_sr.restype = i
         L.sim_create_slab.argtypes = [p, p, p, p, p, i, i, ctypes.POINTER(p)]
         L.sim_create_slab.restype = i
         L.sim_half_step.argtypes = [p, i]
@@ -188,7 +193,7 @@ def _check(L, h, rc):
 
 
 def make_structs(scenario, *, storage="f32", pml_on=None, graph_chunk=0, stream=None, mem_cap=0, max_steps=None,
-                 kernel="auto", timing=False, device=0, dt=0.0, tile=0):
+                 kernel="auto", timing=False, device=0, dt=0.0, tile=0, watchdog_every=0):
     """C structs for a workload Scenario; returns (structs, keepalive)."""
     m = scenario.medium
     g = m.grid
@@ -208,7 +213,7 @@ def make_structs(scenario, *, storage="f32", pml_on=None, graph_chunk=0, stream=
     opts = SimOpts(STORAGE[storage] if isinstance(storage, str) else int(storage), 0 if on else 1, int(graph_chunk),
                    ctypes.c_void_p(stream) if stream else None, int(mem_cap), int(cap),
                    KERNEL[kernel] if isinstance(kernel, str) else int(kernel), int(bool(timing)), int(device),
-                   int(tile))
+                   int(tile), int(watchdog_every))
     return (grid, med, src, rec, opts), keep
 
 
@@ -221,6 +226,19 @@ def time_step(scenario, dt=0.0) -> float:
     if rc != SIM_OK:
         raise SimError(rc, L.sim_last_error(None).decode())
     return out.value
+
+
+def round_f16_sr(x, dither, out, stream=None):
+    """sim_round_f16_sr on CUDA tensors: x float32, dither int32 (13 bits
+    used), out int16 (FP16 bit patterns), all contiguous and of one length."""
+    L = lib()
+    n = x.numel()
+    if dither.numel() != n or out.numel() != n:
+        raise ValueError("x, dither and out need the same length")
+    rc = L.sim_round_f16_sr(_ptr(x), _ptr(dither), _ptr(out), n, stream)
+    if rc != SIM_OK:
+        raise SimError(rc, L.sim_last_error(None).decode())
+    return out
 
 
 class Simulation:
@@ -331,6 +349,13 @@ class Simulation:
         k, t = ctypes.c_int(), ctypes.c_int()
         _check(self.L, self.h, self.L.sim_config(self.h, ctypes.byref(k), ctypes.byref(t)))
         return k.value, t.value
+
+    def watchdog(self):
+        """(energy proxy of the last check, reference, step of that check)
+        of the device watchdog (opts.watchdog_every > 0; sim_watchdog)."""
+        e, r, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        _check(self.L, self.h, self.L.sim_watchdog(self.h, ctypes.byref(e), ctypes.byref(r), ctypes.byref(n)))
+        return e.value, r.value, n.value
 
     def set_wait_test(self, wait_cycles: int, withhold_chunk: int):
         """Test hook of the sweep kernel's bounded waits (sim_set_wait_test)."""

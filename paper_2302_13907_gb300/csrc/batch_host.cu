@@ -161,6 +161,8 @@ extern "C" int simb_create(int n, const sim_grid_t *grids, const sim_medium_t *m
     return bfail(nullptr, SIM_EINVAL, "need n >= 1 and non-null arrays");
   if (opts->storage == SIM_STORAGE_F16_SR)
     return bfail(nullptr, SIM_EUNSUPPORTED, "batches store FP32, BF16 or FP16 rounded to nearest");
+  if (opts->watchdog_every != 0)
+    return bfail(nullptr, SIM_EUNSUPPORTED, "batches: no device watchdog (single handles only)");
   if (opts->tile != 0 && opts->tile != 1 && opts->tile != -1 && opts->tile != -2 && opts->tile != -4)
     return bfail(nullptr, SIM_EINVAL, "opts.tile of a batch: 0, 1 (all shared) or -1, -2, -4 (branches)");
   sim_opts_t vo = *opts;  // the batch's own use of opts.tile is not a tile code

@@ -72,6 +72,23 @@ struct IParams {
   void *f[NF];
 };
 
+// Device watchdog (watchdog.cu): energy proxy of the owned cells every
+// `every` steps; status bit 3 when it is not finite or exceeds WATCH_GROWTH
+// times its first value after step n_quiet.  acc: [0] running sum,
+// [1] last proxy, [2] reference, [3] step of the last check.
+constexpr double WATCH_GROWTH = 100.0;
+struct WParams {
+  int nth, NR, NZp, k_lo, k_hi;
+  int every, n_quiet;
+  const void *f[NF];
+  const uint16_t *id;
+  const float *m_rho;
+  const float2 *m_lam;
+  double iv2, is2;  // 1 / (storage scale)^2 of the velocities and the stresses
+  int *step, *status;
+  double *acc;
+};
+
 struct RParams {
   int nth, NR, NZp, n_rec, cap;
   long long plane;
@@ -289,6 +306,10 @@ inline int hoist_cells_per_thread(int code) {
   const int c = (code / 10) % 10;
   return ((code / 100) % 10 == 1 || ((code / 100) % 10 == 2 && (c == 1 || c == 5))) ? 2 : 4;
 }
+// FP16 stochastic rounding of n device values with the given 13-bit dithers
+// (the rule of the FP16-SR stores), FP16 bit patterns out
+cudaError_t launch_watchdog(int storage, const WParams &p, int blocks, cudaStream_t s);
+cudaError_t launch_sr_round(const float *x, const unsigned *dither, unsigned short *out, long long n, cudaStream_t s);
 cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts = 3);
 // A second stream for the three-way split halves (23xx): while set on the
 // calling thread, each half forks its radial-PML and z-end launches onto

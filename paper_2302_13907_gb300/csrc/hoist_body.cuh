@@ -214,9 +214,13 @@ __device__ __forceinline__ void stown(T *p, const float (&v)[NV]) {
 // exponent of a, at least -14), so that E[rounded] = x; every step of this
 // is exact in FP32.  Magnitudes beyond 65504 round to nearest.
 __device__ __forceinline__ unsigned long long sr_hash(const KParams &p, int n, int f, int j, int i, int k0) {
+  // the key expanded: (n NF + f) S + (j NR + i) ngrp + floor(k0 / 4), S = nth NR ngrp
+  // (equal modulo 2^64); everything but f S is common to the nine fields of a cell
   const unsigned long long ngrp = (unsigned long long)((p.NZ + 3) >> 2);
-  const unsigned long long key =
-      (((((unsigned long long)n * NF + f) * p.nth + j) * p.NR + i) * ngrp) + (unsigned long long)(k0 >> 2);
+  const unsigned long long S = (unsigned long long)p.nth * (unsigned long long)p.NR * ngrp;
+  const unsigned long long base = (unsigned long long)n * NF * S +
+                                  ((unsigned long long)j * p.NR + i) * ngrp + (unsigned long long)(k0 >> 2);
+  const unsigned long long key = base + (unsigned long long)f * S;
   unsigned long long z = (key + 1ull) * 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
@@ -226,14 +230,22 @@ __device__ __forceinline__ unsigned long long sr_hash(const KParams &p, int n, i
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }  // -126 <= k <= 127
 
 __device__ __forceinline__ __half sr_round(float x, unsigned dither) {
+  const unsigned b = __float_as_uint(x) & 0x7fffffffu;  // |x|
+  if (b >= 0x38800000u && b <= 0x477fe000u) {
+    // 2^-14 <= |x| <= 65504, the normal FP16 range: u = 2^(E - 10) and FP16 keeps
+    // the top 10 of the 23 FP32 fraction bits, so the 13 below them are
+    // frac(|x| / u) * 8192; rounding up adds one FP16 spacing (a carry into the
+    // exponent included), and the result is exact in FP16
+    const unsigned t = (b & ~0x1fffu) + ((b & 0x1fffu) > dither ? 0x2000u : 0u);
+    return __float2half_rn(__uint_as_float(t | (__float_as_uint(x) & 0x80000000u)));
+  }
   const float a = fabsf(x);
   if (!(a <= 65504.f) || a == 0.f) return __float2half_rn(x);  // beyond the format, not finite, or zero
-  const int ex = (int)((__float_as_uint(a) >> 23) & 0xff) - 127;
-  const int E = ex < -14 ? -14 : ex;
-  const float q = a * pow2f(10 - E);  // a / u, exact
+  // below 2^-14: the subnormal spacing 2^-24
+  const float q = a * pow2f(24);  // a / u, exact
   const float fl = floorf(q);
   const float up = ((q - fl) * 8192.f > (float)dither) ? 1.f : 0.f;
-  const float m = (fl + up) * pow2f(E - 10);  // exact, a value of the format
+  const float m = (fl + up) * pow2f(-24);  // exact, a value of the format
   return __float2half_rn(copysignf(m, x));
 }
 

@@ -166,6 +166,8 @@ extern "C" int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, co
   const sim_grid_t &g = *grid;
   const int M = zones->n_zones, NR = g.nr + g.pml_r, NZ = g.nz + 2 * g.pml_z, NZp = (NZ + 31) / 32 * 32;
   if (opts->storage != 0) return rfail(nullptr, SIM_EUNSUPPORTED, "refined grid: FP32 storage only");
+  if (opts->watchdog_every != 0)
+    return rfail(nullptr, SIM_EUNSUPPORTED, "refined grid: no device watchdog (uniform-grid handles only)");
   if (opts->kernel != SIM_KERNEL_AUTO && opts->kernel != SIM_KERNEL_SPLIT)
     return rfail(nullptr, SIM_EUNSUPPORTED, "refined grid: the split kernels only");
   if (M < 1 || M > 5 || (M > 1 && !zones->row0)) return rfail(nullptr, SIM_EINVAL, "zones: 1 to 5 zones");

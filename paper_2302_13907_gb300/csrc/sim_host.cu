@@ -106,6 +106,7 @@ int cwell::validate_inputs(const sim_grid_t *g, const sim_medium_t *m, const sim
       return fail(nullptr, SIM_EINVAL, "receiver " + std::to_string(q) + " outside the interior");
   }
   if (o->storage < 0 || o->storage > 3) return fail(nullptr, SIM_EINVAL, "opts: storage must be 0 .. 3");
+  if (o->watchdog_every < 0) return fail(nullptr, SIM_EINVAL, "opts: watchdog_every < 0");
   if (o->storage == SIM_STORAGE_F16_SR) {
     if (!(o->kernel == SIM_KERNEL_AUTO || o->kernel == SIM_KERNEL_SPLIT || o->kernel == SIM_KERNEL_SWEEP))
       return fail(nullptr, SIM_EUNSUPPORTED, "storage: stochastic rounding runs on the split and sweep kernels only");
@@ -160,6 +161,16 @@ extern "C" int sim_time_step(const sim_grid_t *grid, const sim_medium_t *medium,
   for (size_t c = 0; c < ncell; c++)
     if (medium->cell_id[c] >= medium->n_mat) return fail(nullptr, SIM_EINVAL, "medium: cell_id out of range");
   *dt = grid_time_step(*grid, medium);
+  return SIM_OK;
+}
+
+extern "C" int sim_round_f16_sr(const float *x, const unsigned *dither, unsigned short *out, long long n,
+                                void *cuda_stream) {
+  if (n < 0 || (n > 0 && (!x || !dither || !out))) return fail(nullptr, SIM_EINVAL, "null pointer or n < 0");
+  const cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaError_t e = launch_sr_round(x, dither, out, n, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(nullptr, SIM_ECUDA, std::string("sim_round_f16_sr: ") + cudaGetErrorString(e));
   return SIM_OK;
 }
 
@@ -793,6 +804,37 @@ static int create_impl(const sim_grid_t *grid, const sim_medium_t *medium, const
   r.traces = h->traces;
   r.step = h->step;
   r.status = h->status;
+  if (opts->watchdog_every > 0) {
+    h->watch_every = opts->watchdog_every;
+    if ((rc = dev_alloc(h, (void **)&h->watch_acc, 4 * sizeof(double)))) return bail(rc);
+    if ((e = cudaMemsetAsync(h->watch_acc, 0, 4 * sizeof(double), st)) != cudaSuccess)
+      return bail(cuda_fail(h, e, "watchdog"));
+    int dev_sms = 0;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->watch_blocks = std::max(1, std::min(nth * NR, 4 * std::max(dev_sms, 1)));
+    for (int par = 0; par < 2; par++) {
+      WParams &w = h->wp[par];
+      w.nth = nth;
+      w.NR = NR;
+      w.NZp = NZp;
+      w.k_lo = std::max(0, s0 - l0);
+      w.k_hi = std::min(NZ, s1 - l0);
+      w.every = h->watch_every;
+      // the last step of the source's wavelet tables: no injection after it
+      w.n_quiet = std::max(h->n_wav, h->ip.n_wav);
+      // the state after a step of parity par (the fused path writes the other set)
+      void **cur = (h->fused && par == 0) ? h->f2 : h->f;
+      for (int q = 0; q < NF; q++) w.f[q] = cur[q];
+      w.id = h->id;
+      w.m_rho = h->m_rho;
+      w.m_lam = h->m_lam;
+      w.iv2 = 1.0 / (h->vscale * h->vscale);
+      w.is2 = 1.0 / (h->sscale * h->sscale);
+      w.step = h->step;
+      w.status = h->status;
+      w.acc = h->watch_acc;
+    }
+  }
   if (h->fused) {
     for (int par = 0; par < 2; par++) {
       FusedParams &f = h->fp[par];
@@ -908,6 +950,10 @@ static cudaError_t enqueue_step(sim_t *h, int parity, bool timed) {
     e = launch_receivers(h->storage, h->rp, h->stream);
   }
   if (e != cudaSuccess) return e;
+  if (h->watch_every > 0) {
+    e = launch_watchdog(h->storage, h->wp[parity], h->watch_blocks, h->stream);
+    if (e != cudaSuccess) return e;
+  }
   if (timed) {
     cudaEventRecord(h->ev[3], h->stream);
     e = cudaEventSynchronize(h->ev[3]);
@@ -1040,6 +1086,22 @@ extern "C" int sim_sync(sim_t *h) {
   // a wait that gave up voids the state: report it first
   if (st & 2) return fail(h, SIM_ETIMEOUT, "a bounded device wait gave up");
   if (st & 1) return fail(h, SIM_EUNSTABLE, "non-finite value in the receiver traces");
+  if (st & 8)
+    return fail(h, SIM_EUNSTABLE, "watchdog: the energy proxy is not finite or grew past " +
+                                      std::to_string((int)WATCH_GROWTH) + " times its value after the source");
+  return SIM_OK;
+}
+
+extern "C" int sim_watchdog(sim_t *h, double *energy, double *reference, int *step) {
+  if (!h) return SIM_EINVAL;
+  if (h->watch_every <= 0) return fail(h, SIM_EINVAL, "the watchdog is off (opts.watchdog_every = 0)");
+  CK(h, cudaSetDevice(h->device));
+  CK(h, cudaStreamSynchronize(h->stream));
+  double a[4];
+  CK(h, cudaMemcpy(a, h->watch_acc, sizeof(a), cudaMemcpyDeviceToHost));
+  if (energy) *energy = a[1];
+  if (reference) *reference = a[2];
+  if (step) *step = (int)a[3];
   return SIM_OK;
 }
 
@@ -1287,6 +1349,8 @@ extern "C" int sim_load(sim_t *h, const char *path) {
   load(h->traces, (size_t)h->n_rec * h->cap * 4);
   load(h->step, 4);
   fclose(fp);
+  // the watchdog takes its reference again from the restored run
+  if (ok && h->watch_acc) ok = cudaMemset(h->watch_acc, 0, 4 * sizeof(double)) == cudaSuccess;
   if (!ok) {
     h->steps_done = prev_steps;
     return fail(h, SIM_EINVAL, "checkpoint read failed");

@@ -60,6 +60,11 @@ struct sim_s {
   RParams rp2[2];
   // second stream and fork / join events of the three-way split halves
   SideStream side{};
+  // device watchdog (opts.watchdog_every > 0): parameters per step parity
+  // (the fused path's state alternates between the buffer sets)
+  int watch_every = 0, watch_blocks = 0;
+  double *watch_acc = nullptr;
+  WParams wp[2]{};
   // z slab (sim_create_slab): the handle holds the well's stored z cells
   // l0 .. l0 + NZ - 1 and owns s0 .. s1 - 1 of them
   bool slab = false;

@@ -579,6 +579,22 @@ cudaError_t launch_batch_split(int storage, bool vel, const KParams *cases, int 
   return cudaErrorInvalidValue;
 }
 
+namespace {
+// the stochastic rounding of the FP16-SR stores, element by element
+__global__ void __launch_bounds__(256) sr_round_kernel(const float *x, const unsigned *dither, unsigned short *out,
+                                                       long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    out[q] = __half_as_ushort(sr_round(x[q], dither[q] & 0x1fffu));
+}
+}  // namespace
+
+cudaError_t launch_sr_round(const float *x, const unsigned *dither, unsigned short *out, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
+  sr_round_kernel<<<grid, 256, 0, s>>>(x, dither, out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_hoist(int storage, int code, const KParams &p, cudaStream_t s, cudaEvent_t *ev, int parts) {
   const int minb = hoist_blocks(code), nv = hoist_cells_per_thread(code);
   const bool zf = hoist_zfast(code), split = hoist_split(code), split3 = (code / 100) % 10 == 3;

@@ -254,7 +254,8 @@ def pipeline_test(a, log, params, train_rep):
 def pipeline(a):
     """The surrogate job (see the module docstring): phase "train", "test"
     or "all"; the test phase reads the weights and gate the train phase saved
-    (--params, by default DIR/params.npz, and DIR/train_report.json)."""
+    (--params, by default DIR/params.npz) and the training figures
+    (DIR/train_report.json, else the one beside the params)."""
     import os
     os.makedirs(a.out_dir, exist_ok=True)
     log = lambda m: print(m, flush=True)
@@ -264,9 +265,11 @@ def pipeline(a):
     if a.phase in ("test", "all"):
         params = a.params or os.path.join(a.out_dir, "params.npz")
         if train_rep is None:
-            tr_path = os.path.join(os.path.dirname(params), "train_report.json")
-            if os.path.exists(tr_path):
-                train_rep = json.load(open(tr_path))
+            for tr_path in (os.path.join(a.out_dir, "train_report.json"),
+                            os.path.join(os.path.dirname(params), "train_report.json")):
+                if os.path.exists(tr_path):
+                    train_rep = json.load(open(tr_path))
+                    break
         pipeline_test(a, log, params, train_rep)
 
 

@@ -70,7 +70,7 @@ def test_host_validation_rejects_bad_input(mutate, code):
 
 
 @pytest.mark.parametrize("kw", [dict(kernel="split", tile=1416), dict(kernel="march", tile=-3), dict(kernel=7),
-                                dict(kernel="fused", source_kind=2)])
+                                dict(kernel="fused", source_kind=2), dict(watchdog_every=-1)])
 def test_host_validation_rejects_bad_kernel_options(kw):
     """Kernel / tile options are checked on the host before any device call
     (point forces cannot run on the fused kernels)."""
@@ -104,6 +104,7 @@ def _refined(nth=16, nr=16):
     ([4, 8], dict(source_kind=3, source_r=0.02), B.SIM_EUNSUPPORTED),  # torsion ring on a zone's first row
     ([4, 8], dict(nth=24), B.SIM_EINVAL),                 # nth not a power of two
     ([4, 8], dict(source_kind=1, source_r=0.02), B.SIM_EUNSUPPORTED),  # force node on a zone's first row
+    ([4, 8], dict(watchdog_every=10), B.SIM_EUNSUPPORTED),  # no watchdog on the refined grid
 ])
 def test_refined_grid_host_validation(rows, kw, code):
     """simr_create checks its zones, storage, kernel and source on the host

@@ -94,9 +94,10 @@ def _ulp(x, storage):
 # increment where its terms (radial, azimuthal and z differences) nearly
 # cancel (a field near rest), so the share of such values grows with the
 # format's resolution: measured 0 of 3.2 M for BF16 and 0.4 % for FP16
-# (1.8 % of the velocities, none of the stresses); stochastic rounding puts
-# its boundary anywhere in the spacing, so values that stagnate near a grid
-# point can flip too (3.4 % of v_r measured).  The bounds leave room
+# (1.8 % of the velocities, none of the stresses).  Stochastic rounding puts
+# a value's boundary anywhere in the spacing, so every value flips with
+# probability |FP32 - FP64 pre-rounding difference| / spacing, not only those
+# near a midpoint (3.4 % of v_r measured).  The bounds leave room
 # for a kernel with another FP32 operation order; a value more than one ulp
 # apart fails outright.
 FLIP_FRACTION = {"bf16": 1e-3, "f16": 1e-2, "f16sr": 3e-2}
@@ -160,3 +161,49 @@ def test_reduced_storage_step_matches_the_rounded_oracle(storage):
     ref = o.traces()[:, n]
     u = 2.0 ** -8 if storage == "bf16" else 2.0 ** -11
     assert np.allclose(tr[:, n], ref, rtol=u, atol=1e-6 * np.abs(ref).max()), (tr[:, n], ref)
+
+
+def _sr_inputs(n=60000, seed=11):
+    """FP32 values spread over the FP16 range and beyond (log-uniform
+    magnitudes 2^-30 .. 2^17, both signs), the specials, and values whose
+    dropped 13 bits equal their dither (the tie of the rule)."""
+    rng = np.random.default_rng(seed)
+    mag = np.exp2(rng.uniform(-30, 17, n)).astype(np.float32)
+    x = np.where(rng.random(n) < 0.5, -mag, mag).astype(np.float32)
+    d = rng.integers(0, 8192, n, dtype=np.uint32)
+    special = np.array([0.0, -0.0, 1.0, -1.0, 65504.0, -65504.0, 65505.0, 65519.0, 65520.0, 7e4,
+                        2.0 ** -14, -(2.0 ** -14), 2.0 ** -24, 2.0 ** -25, 3 * 2.0 ** -26, 1e-40, -1e-45,
+                        np.inf, -np.inf, np.nan], np.float32)
+    for delta in (-1, 1):  # one FP32 ulp either side of the normal / subnormal boundary
+        special = np.append(special, np.nextafter(np.float32(2.0 ** -14), np.float32(delta * np.inf)))
+    x = np.concatenate([x, special, np.repeat(special, 2)])
+    d = np.concatenate([d, rng.integers(0, 8192, special.size, dtype=np.uint32),
+                        np.tile(np.array([0, 8191], np.uint32), special.size)])
+    ties = (np.abs(x[:2000]).view(np.uint32) & 0x1FFF).astype(np.uint32)
+    x = np.concatenate([x, x[:2000]])
+    d = np.concatenate([d, ties])
+    return x.astype(np.float32), d.astype(np.uint32)
+
+
+def test_stochastic_rounding_equals_the_oracle_value_by_value():
+    """The FP16-SR stores' rounding (sim_round_f16_sr, the device function the
+    stencil kernels call) against the oracle's rule, bit for bit, over the
+    whole FP16 range, its subnormals, the overflow edge, the specials and the
+    ties (dropped bits equal to the dither: no rounding up)."""
+    import torch
+    import oracle
+    from paper_2302_13907_gb300.binding import round_f16_sr
+    x, d = _sr_inputs()
+    xt = torch.from_numpy(x).cuda()
+    dt = torch.from_numpy(d.view(np.int32)).cuda()
+    out = torch.empty(x.size, dtype=torch.int16, device="cuda")
+    got = round_f16_sr(xt, dt, out).cpu().numpy().view(np.float16).astype(np.float64)
+    ref = oracle.round_stochastic_f16(x, d)
+    both_nan = np.isnan(got) & np.isnan(ref)
+    bad = ~both_nan & (got != ref)
+    assert not bad.any(), (x[bad][:5], d[bad][:5], got[bad][:5], ref[bad][:5])
+    # signs of zeros and infinities as well
+    same_sign = np.signbit(got) == np.signbit(ref)
+    assert np.all(same_sign | both_nan)
+    empty = torch.empty(0, device="cuda")
+    round_f16_sr(empty, empty.int(), empty.short())
