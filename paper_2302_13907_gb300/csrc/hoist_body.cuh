@@ -213,15 +213,21 @@ __device__ __forceinline__ void stown(T *p, const float (&v)[NV]) {
 // frac(a / u) * 8192 > dither, u the FP16 spacing at a (2^(E - 10), E the
 // exponent of a, at least -14), so that E[rounded] = x; every step of this
 // is exact in FP32.  Magnitudes beyond 65504 round to nearest.
-__device__ __forceinline__ unsigned long long sr_hash(const KParams &p, int n, int f, int j, int i, int k0) {
-  // the key expanded: (n NF + f) S + (j NR + i) ngrp + floor(k0 / 4), S = nth NR ngrp
-  // (equal modulo 2^64); everything but f S is common to the nine fields of a cell
+// the key expanded: (n NF + f) S + (j NR + i) ngrp + floor(k0 / 4), S = nth NR
+// ngrp (equal modulo 2^64); everything but f S is common to the nine fields
+// of a cell, so a body takes it once, before its stores
+struct SrKey {
+  unsigned long long base, S;
+  int k0;
+};
+__device__ __forceinline__ SrKey sr_key(const KParams &p, int n, int j, int i, int k0) {
   const unsigned long long ngrp = (unsigned long long)((p.NZ + 3) >> 2);
   const unsigned long long S = (unsigned long long)p.nth * (unsigned long long)p.NR * ngrp;
-  const unsigned long long base = (unsigned long long)n * NF * S +
-                                  ((unsigned long long)j * p.NR + i) * ngrp + (unsigned long long)(k0 >> 2);
-  const unsigned long long key = base + (unsigned long long)f * S;
-  unsigned long long z = (key + 1ull) * 0x9E3779B97F4A7C15ull;
+  return {(unsigned long long)n * NF * S + ((unsigned long long)j * p.NR + i) * ngrp + (unsigned long long)(k0 >> 2), S,
+          k0};
+}
+__device__ __forceinline__ unsigned long long sr_hash(const SrKey &sk, int f) {
+  unsigned long long z = (sk.base + (unsigned long long)f * sk.S + 1ull) * 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
@@ -230,33 +236,24 @@ __device__ __forceinline__ unsigned long long sr_hash(const KParams &p, int n, i
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }  // -126 <= k <= 127
 
 __device__ __forceinline__ __half sr_round(float x, unsigned dither) {
-  const unsigned b = __float_as_uint(x) & 0x7fffffffu;  // |x|
-  if (b >= 0x38800000u && b <= 0x477fe000u) {
-    // 2^-14 <= |x| <= 65504, the normal FP16 range: u = 2^(E - 10) and FP16 keeps
-    // the top 10 of the 23 FP32 fraction bits, so the 13 below them are
-    // frac(|x| / u) * 8192; rounding up adds one FP16 spacing (a carry into the
-    // exponent included), and the result is exact in FP16
-    const unsigned t = (b & ~0x1fffu) + ((b & 0x1fffu) > dither ? 0x2000u : 0u);
-    return __float2half_rn(__uint_as_float(t | (__float_as_uint(x) & 0x80000000u)));
-  }
   const float a = fabsf(x);
-  if (!(a <= 65504.f) || a == 0.f) return __float2half_rn(x);  // beyond the format, not finite, or zero
-  // below 2^-14: the subnormal spacing 2^-24
-  const float q = a * pow2f(24);  // a / u, exact
+  // zero (whole warps of it ahead of the wavefront), beyond the format, not finite
+  if (!(a <= 65504.f) || a == 0.f) return __float2half_rn(x);
+  const int ex = (int)((__float_as_uint(a) >> 23) & 0xff) - 127;
+  const int E = ex < -14 ? -14 : ex;
+  const float q = a * pow2f(10 - E);  // a / u, exact
   const float fl = floorf(q);
   const float up = ((q - fl) * 8192.f > (float)dither) ? 1.f : 0.f;
-  const float m = (fl + up) * pow2f(-24);  // exact, a value of the format
-  return __float2half_rn(copysignf(m, x));
+  return __float2half_rn(copysignf((fl + up) * pow2f(E - 10), x));  // exact, a value of the format
 }
 
-// the NV values of field f at cells (j, i, k0 .. k0 + NV - 1) of step n
+// the NV values of field f at cells (j, i, k0 .. k0 + NV - 1) of step n (sk)
 template <int NV>
-__device__ __forceinline__ void sr_store(half_sr *p, const float (&v)[NV], const KParams &kp, int n, int f, int j,
-                                         int i, int k0) {
-  const unsigned long long z = sr_hash(kp, n, f, j, i, k0);
+__device__ __forceinline__ void sr_store(half_sr *p, const float (&v)[NV], const SrKey &sk, int f) {
+  const unsigned long long z = sr_hash(sk, f);
   __half h[NV];
 #pragma unroll
-  for (int e = 0; e < NV; e++) h[e] = sr_round(v[e], (unsigned)(z >> (16 * ((k0 + e) & 3))) & 0x1fffu);
+  for (int e = 0; e < NV; e++) h[e] = sr_round(v[e], (unsigned)(z >> (16 * ((sk.k0 + e) & 3))) & 0x1fffu);
   if (NV == 4) {
     uint2 u;
     u.x = (unsigned)__half_as_ushort(h[0]) | ((unsigned)__half_as_ushort(h[1 % NV]) << 16);
@@ -268,12 +265,18 @@ __device__ __forceinline__ void sr_store(half_sr *p, const float (&v)[NV], const
   }
 }
 
+// the key of a body's stores: the step and the cell group (stochastic rounding only)
+template <typename T>
+__device__ __forceinline__ SrKey body_key(const KParams &p, int j, int i, int k0) {
+  if constexpr (std::is_same<T, half_sr>::value) return sr_key(p, *p.step, j, i, k0);
+  else return SrKey{0ull, 0ull, 0};
+}
+
 // store of a field's NV new values: stochastic rounding for half_sr, else
 // the plain (CS = false) or streaming (CS = true) store
 template <typename T, int NV, bool CS>
-__device__ __forceinline__ void st_field(T *ptr, const float (&v)[NV], const KParams &kp, int n, int f, int j,
-                                         int i, int k0) {
-  if constexpr (std::is_same<T, half_sr>::value) sr_store<NV>(ptr, v, kp, n, f, j, i, k0);
+__device__ __forceinline__ void st_field(T *ptr, const float (&v)[NV], const SrKey &sk, int f) {
+  if constexpr (std::is_same<T, half_sr>::value) sr_store<NV>(ptr, v, sk, f);
   else stown<T, NV, CS>(ptr, v);
 }
 
@@ -522,10 +525,10 @@ __device__ __forceinline__ void vel_hoist_body(const KParams &p, const int j, co
       out_z[e] += vel_coef(dtv, rho_c[e] + rho_c[e + 1]) * (Dr + Q + Dz);
     }
   }
-  const int n_sr = std::is_same<T, half_sr>::value ? *p.step : 0;  // the step, for stochastic rounding
-  if (im) st_field<T, NV, false>(vr + c, out_r, p, n_sr, F_VR, j, i, k0);
-  st_field<T, NV, false>(vp + c, out_p, p, n_sr, F_VP, j, i, k0);
-  st_field<T, NV, false>(vz + c, out_z, p, n_sr, F_VZ, j, i, k0);
+  const SrKey sk = body_key<T>(p, j, i, k0);
+  if (im) st_field<T, NV, false>(vr + c, out_r, sk, F_VR);
+  st_field<T, NV, false>(vp + c, out_p, sk, F_VP);
+  st_field<T, NV, false>(vz + c, out_z, sk, F_VZ);
   if (PRE && rp) {  // cells the loop skipped keep the values loaded
     stv(p.psr[R_VR] + cr, ur_vr);
     stv(p.psr[Q_VR] + cr, uq_vr);
@@ -741,15 +744,15 @@ __device__ __forceinline__ void str_hoist_body(const KParams &p, const int j, co
       opz[e] += dts * mu * (Q + gz);
     }
   }
-  const int n_sr = std::is_same<T, half_sr>::value ? *p.step : 0;  // the step, for stochastic rounding
-  st_field<T, NV, CG>(srr + c, orr, p, n_sr, F_SRR, j, i, k0);
-  st_field<T, NV, CG>(spp + c, opp, p, n_sr, F_SPP, j, i, k0);
-  st_field<T, NV, CG>(szz + c, ozz, p, n_sr, F_SZZ, j, i, k0);
+  const SrKey sk = body_key<T>(p, j, i, k0);
+  st_field<T, NV, CG>(srr + c, orr, sk, F_SRR);
+  st_field<T, NV, CG>(spp + c, opp, sk, F_SPP);
+  st_field<T, NV, CG>(szz + c, ozz, sk, F_SZZ);
   if (im) {
-    st_field<T, NV, CG>(srp + c, orp, p, n_sr, F_SRP, j, i, k0);
-    st_field<T, NV, CG>(srz + c, orz, p, n_sr, F_SRZ, j, i, k0);
+    st_field<T, NV, CG>(srp + c, orp, sk, F_SRP);
+    st_field<T, NV, CG>(srz + c, orz, sk, F_SRZ);
   }
-  st_field<T, NV, CG>(spz + c, opz, p, n_sr, F_SPZ, j, i, k0);
+  st_field<T, NV, CG>(spz + c, opz, sk, F_SPZ);
   if (PRE && rp) {  // cells the loop skipped keep the values loaded
     stv(p.psr[R_ERR] + cr, ur_rr);
     stv(p.psr[Q_EPP] + cr, uq_pp);

@@ -211,6 +211,13 @@ def pipeline_test(a, log, params, train_rep):
     acc = S.gate(Xt, k=k, tol=TOL * margin)
     t_inf = time.perf_counter() - t0
     e_test = rel_err(P, Yt)
+    # the same gate at other margins on the same answers: the trade-off the chosen margin sits on
+    sweep = []
+    for m in np.arange(0.1, 1.0001, 0.1):
+        am = S.gate(Xt, k=k, tol=TOL * float(m))
+        sweep.append({"margin": round(float(m), 2), "accepted_frac": float(am.mean()),
+                      "false_accepts": int(np.sum(am & (e_test > TOL))),
+                      "max_accepted_rel_l2": float(e_test[am].max()) if am.any() else None})
     rejected = np.flatnonzero(~acc)
     t0 = time.perf_counter()
     if len(rejected):
@@ -241,13 +248,17 @@ def pipeline_test(a, log, params, train_rep):
         "fallback_cases_per_s": 1.0 / per_sim,
         "speedup_vs_fallback": per_sim * n / (t_inf + t_fb),
         "speedup_vs_plain": (per_plain * n / (t_inf + t_fb)) if per_plain else None,
+        "gate_sweep": sweep,
         "test_rel_l2": [float(x) for x in e_test], "test_accepted": [bool(x) for x in acc],
     })
     if train_rep and "epoch_loss" in train_rep:
         rep["epoch_loss"] = train_rep["epoch_loss"]
     json.dump(rep, open(os.path.join(a.out_dir, "report.json"), "w"), indent=1)
-    log(json.dumps({k_: v for k_, v in rep.items() if k_ not in ("epoch_loss", "test_rel_l2", "test_accepted")},
-                   indent=1))
+    log(json.dumps({k_: v for k_, v in rep.items() if k_ not in ("epoch_loss", "test_rel_l2", "test_accepted",
+                                                                  "gate_sweep")}, indent=1))
+    for row in sweep:
+        log(f"margin {row['margin']}: accepted {row['accepted_frac']:.3f}, false accepts {row['false_accepts']}, "
+            f"max accepted rel-L2 {row['max_accepted_rel_l2']}")
     return rep
 
 

@@ -152,8 +152,15 @@ def test_reduced_storage_step_matches_the_rounded_oracle(storage):
             a = np.abs(g[d > 0])
             print(f"{storage} {f}: {int((d > 0).sum())} of {g.size} one ulp apart; |stored| quantiles "
                   f"{np.quantile(a, [0, 0.5, 1])}, of those below 2^-14: {int((a < 2.0 ** -14).sum())}")
-        # the axisymmetric well has no azimuthal motion: v_phi, s_rphi, s_phiz stay zero
-        assert (np.abs(g).max() > 0) == (f not in ("vp", "srp", "spz")), f
+        # the axisymmetric well has no azimuthal motion: v_phi, s_rphi, s_phiz stay
+        # zero, except under stochastic rounding, whose dither differs from one
+        # theta plane to the next: the stored state loses its exact azimuthal
+        # symmetry, and those fields carry rounding noise
+        if storage == "f16sr" and f in ("vp", "srp", "spz"):
+            main = oracle.round_storage(after["vr" if f == "vp" else "srr"] * sc_f, "f16")
+            assert np.abs(g).max() <= 0.05 * np.abs(main).max(), f
+        else:
+            assert (np.abs(g).max() > 0) == (f not in ("vp", "srp", "spz")), f
     print(f"{storage}: {diff} of {total} stored values one ulp apart after one step")
     assert diff <= FLIP_FRACTION[storage] * total, (diff, total)
     # the step's receiver sample from the same stored stresses (a one-ulp

@@ -64,8 +64,9 @@ def test_slabs_reproduce_the_whole_well(ws, kind):
             t = e.sim.traces()
             tr[mine] = t[mine]
             assert np.all(t[~mine] == 0)
-        assert rel_l2(tr, ref_tr) <= 1e-5
-        assert np.abs(ref_tr).max() > 0
+        # the torsion ring makes no pressure (pure shear): its traces are zero
+        assert (np.abs(ref_tr).max() > 0) == (kind != 3)
+        assert np.abs(tr - ref_tr).max() <= 1e-5 * max(np.abs(ref_tr).max(), 1e-30)
     finally:
         for e in engines:
             e.sim.close()

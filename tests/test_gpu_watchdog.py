@@ -49,15 +49,18 @@ def test_watchdog_proxy_equals_its_definition(storage, kernel):
 
 
 def test_watchdog_is_silent_on_a_stable_run():
-    """PML on and off: after the pulse the proxy stays within a small factor
-    of its reference (no trip), step after step."""
+    """1600 steps, long enough for the waves to reach the PML (0.3 m from the
+    source, about 670 steps in the liquid), with the PML and with rigid walls:
+    no trip; with rigid walls (nothing leaves) the proxy stays within a small
+    factor of its reference, with the PML it ends far lower (absorbed)."""
     from paper_2302_13907_gb300.binding import Simulation
+    final = {}
     for pml_on in (True, False):
         sc = _short_pulse(f0=2e5)
-        with Simulation(sc, watchdog_every=10, pml_on=pml_on, max_steps=600) as s:
+        with Simulation(sc, watchdog_every=20, pml_on=pml_on, max_steps=1600) as s:
             hist = []
-            for _ in range(60):
-                s.step(10)
+            for _ in range(80):
+                s.step(20)
                 hist.append(s.watchdog())
             s.sync()
             ref = hist[-1][1]
@@ -65,22 +68,26 @@ def test_watchdog_is_silent_on_a_stable_run():
             after = [e for e, r, n in hist if r > 0]
             assert all(np.isfinite(after))
             print(f"pml_on={pml_on}: reference {ref:.4g}, later proxies {min(after) / ref:.3f} .. "
-                  f"{max(after) / ref:.3f} of it")
+                  f"{max(after) / ref:.3f} of it, last {after[-1] / ref:.3f}")
             assert max(after) <= 5 * ref, pml_on
-            if not pml_on:  # rigid walls: nothing leaves, the proxy stays near the energy
-                assert min(after) >= 0.2 * ref
+            if not pml_on:
+                assert min(after) >= 0.1 * ref
+            final[pml_on] = after[-1]
+    assert final[True] < 0.5 * final[False], final
 
 
 def test_watchdog_trips_on_growth_past_the_stability_limit():
     """CFL 1.4 (the scheme's limit on this grid is about 1.07, from the power
-    iteration of the oracle's operator): the grid-scale modes grow about 4.7x
-    per step.  With a check after every step the watchdog trips a few steps
-    after the source falls silent, on growth while every value is finite."""
+    iteration of the oracle's operator, and the steel casing sets it): the
+    grid-scale modes of the casing grow about 4.7x per step once the wave from
+    the axis reaches it (0.1 m at 1500 m/s, about 80 steps), long after the
+    source fell silent (21 steps).  With a check after every step the watchdog
+    trips on growth while every value is still finite."""
     from paper_2302_13907_gb300.binding import SIM_EUNSTABLE, SimError, Simulation
     sc = _short_pulse(cfl=1.4)
-    with Simulation(sc, watchdog_every=1, max_steps=200, graph_chunk=-1) as s:
+    with Simulation(sc, watchdog_every=1, max_steps=250, graph_chunk=-1) as s:
         tripped = None
-        for n in range(1, 60):
+        for n in range(1, 240):
             s.step(1)
             try:
                 s.sync()
