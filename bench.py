@@ -369,7 +369,8 @@ SURROGATE_PARAMS = os.path.join(ROOT, "paper_2302_13907_gb300", "data", "surroga
 
 def bench_surrogate(stream, n_check=8, n_plain=2):
     """The trace surrogate on its 512 held-out cement cases (seeds 9000 ..
-    9511): inference of all cases, the kNN gate, the simulator on every
+    9511): inference of all cases, the gate (nearest validation errors and
+    the network's sensitivity), the simulator on every
     rejected case (the fallback: the refined-grid simulator on the case's
     reach crop, which generated the training data), timed together as cases/s;
     against the plain FP32 solver (uniform grid, whole well, 6000 steps),
@@ -396,7 +397,7 @@ def bench_surrogate(stream, n_check=8, n_plain=2):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     P = S.forward(Xt)
-    acc = S.gate(Xt, k=k, tol=R.TOL * margin)
+    acc = R.gate_decision(S, Xt, d)  # the neighbour rule and, when saved, the sensitivity bound
     t_inf = time.perf_counter() - t0
     rejected = np.flatnonzero(~acc)
     t0 = time.perf_counter()
@@ -436,6 +437,7 @@ def bench_surrogate(stream, n_check=8, n_plain=2):
             "max_accepted_rel_l2_sampled": max(errs) if errs else None, "accepted_checked": len(errs),
             "max_accepted_rel_l2": full.get("max_accepted_rel_l2"),
             "false_accepts": full.get("false_accepts"), "gate_margin": margin, "gate_k": k,
+            "gate_sens_max": float(d["gate_sens_max"]) if "gate_sens_max" in d.files else None,
             "tolerance": R.TOL,
             "workload": "512 held-out cement cases (seeds 9000-9511); inputs: top depth, ramp, top shear fraction, "
                         "casing thickness, cement Vs, rock Vs; output 8 x 2048 reflected-window traces",

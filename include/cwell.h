@@ -478,6 +478,15 @@ int sur_train(sur_t *s, const float *X, const float *Y, int n, int epochs, int b
  * (normalised distance) is <= tol, else the caller runs the simulator. */
 int sur_gate_fit(sur_t *s, const float *X, const float *err, int n);
 int sur_gate(sur_t *s, const float *X, int n, int k, float tol, int *accept);
+/* Local sensitivity of the network at each of the n host inputs X[n][in_dim]:
+ * sens[q] = max over input dimensions d of ||f(x_q + step scale_d e_d) -
+ * f(x_q)|| / ||f(x_q)|| (L2 over the whole output; step in normalised input
+ * units, scale_d the normalisation's scale), from (in_dim + 1) forward passes
+ * per query on the device.  A second gate signal: an answer whose output
+ * swings under a small move of its inputs sits where the network is least
+ * trustworthy.  step > 0; sens is a host array of n floats (infinity where
+ * f(x_q) = 0). */
+int sur_sensitivity(sur_t *s, const float *X, int n, float step, float *sens);
 void sur_destroy(sur_t *s);
 const char *sur_last_error(const sur_t *s);
 

@@ -567,6 +567,8 @@ def _sur_sigs(L):
     L.sur_gate_fit.argtypes = [p, fp, fp, i]
     L.sur_gate_fit.restype = i
     L.sur_gate.argtypes = [p, fp, i, i, ctypes.c_float, ctypes.POINTER(i)]
+    L.sur_sensitivity.argtypes = [p, fp, i, ctypes.c_float, fp]
+    L.sur_sensitivity.restype = i
     L.sur_gate.restype = i
     L.sur_destroy.argtypes = [p]
     L.sur_destroy.restype = None
@@ -686,6 +688,14 @@ class Surrogate:
         X = np.ascontiguousarray(X, np.float32)
         e = np.ascontiguousarray(err, np.float32)
         self._chk(self.L.sur_gate_fit(self.h, _fp(X), _fp(e), X.shape[0]))
+
+    def sensitivity(self, X, step=0.1) -> np.ndarray:
+        """sur_sensitivity: the largest relative output change over unit
+        moves of `step` (normalised units) along each input dimension."""
+        X = np.ascontiguousarray(X, np.float32)
+        out = np.zeros(X.shape[0], np.float32)
+        self._chk(self.L.sur_sensitivity(self.h, _fp(X), X.shape[0], float(step), _fp(out)))
+        return out
 
     def gate(self, X, k=3, tol=0.05) -> np.ndarray:
         X = np.ascontiguousarray(X, np.float32)

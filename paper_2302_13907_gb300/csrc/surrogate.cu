@@ -275,6 +275,34 @@ __global__ void k_adam(float *w, const float *g, float *m, float *v, __nv_bfloat
 }
 
 // gather rows of the device training set into a minibatch
+// per case b: num[b] = sum (y - y0)^2 and den[b] = sum y0^2 over its `per`
+// outputs (one block per case, fixed-order tree in the block)
+__global__ void __launch_bounds__(256) k_diff_norms(const float *y, const float *y0, long long per, float *num,
+                                                    float *den) {
+  const long long o = (long long)blockIdx.x * per;
+  float a = 0.f, b = 0.f;
+  for (long long q = threadIdx.x; q < per; q += 256) {
+    const float u = y0[o + q], d = y[o + q] - u;
+    a += d * d;
+    b += u * u;
+  }
+  __shared__ float sa[256], sb[256];
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sa[threadIdx.x] += sa[threadIdx.x + w];
+      sb[threadIdx.x] += sb[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    num[blockIdx.x] = sa[0];
+    den[blockIdx.x] = sb[0];
+  }
+}
+
 __global__ void k_gather(const float *src, const int *idx, int n, long long row, float *dst) {
   GRID_STRIDE(q, (long long)n * row) dst[q] = src[(long long)idx[q / row] * row + q % row];
 }
@@ -624,6 +652,41 @@ extern "C" int sur_forward(sur_t *s, const float *X, int n, float *Y) {
                            cudaMemcpyDeviceToHost, s->stream));
   }
   SCK(s, cudaStreamSynchronize(s->stream));
+  return tc_status(s);
+}
+
+extern "C" int sur_sensitivity(sur_t *s, const float *X, int n, float step, float *sens) {
+  if (!s || n < 0 || (n > 0 && (!X || !sens)) || !(step > 0.f))
+    return s ? sfail(s, SIM_EINVAL, "bad arguments") : SIM_EINVAL;
+  SCK(s, cudaSetDevice(s->device));
+  const sur_cfg_t &c = s->cfg;
+  const long long per = (long long)L_out(s) * c.out_ch;
+  std::vector<float> scale(c.in_dim), xp((size_t)s->max_batch * c.in_dim), num(s->max_batch), den(s->max_batch);
+  SCK(s, cudaMemcpy(scale.data(), s->x_scale, c.in_dim * 4, cudaMemcpyDeviceToHost));
+  float *nd = s->part;  // [2][max_batch] partial norms (the column-sum scratch, idle here)
+  for (int b0 = 0; b0 < n; b0 += s->max_batch) {
+    const int nb = std::min(s->max_batch, n - b0);
+    const float *xc = X + (size_t)b0 * c.in_dim;
+    SCK(s, cudaMemcpyAsync(s->xb, xc, (size_t)nb * c.in_dim * 4, cudaMemcpyHostToDevice, s->stream));
+    SCK(s, forward(s, nb));
+    SCK(s, cudaMemcpyAsync(s->dy, s->y, (size_t)nb * per * 4, cudaMemcpyDeviceToDevice, s->stream));
+    for (int q = 0; q < nb; q++) sens[b0 + q] = 0.f;
+    for (int d = 0; d < c.in_dim; d++) {
+      // the input moved by `step` in normalised units along dimension d
+      for (int q = 0; q < nb; q++)
+        for (int e = 0; e < c.in_dim; e++)
+          xp[(size_t)q * c.in_dim + e] = xc[(size_t)q * c.in_dim + e] + (e == d ? step * scale[d] : 0.f);
+      SCK(s, cudaMemcpyAsync(s->xb, xp.data(), (size_t)nb * c.in_dim * 4, cudaMemcpyHostToDevice, s->stream));
+      SCK(s, forward(s, nb));
+      k_diff_norms<<<nb, 256, 0, s->stream>>>(s->y, s->dy, per, nd, nd + s->max_batch);
+      SCK(s, cudaGetLastError());
+      SCK(s, cudaMemcpyAsync(num.data(), nd, nb * 4, cudaMemcpyDeviceToHost, s->stream));
+      SCK(s, cudaMemcpyAsync(den.data(), nd + s->max_batch, nb * 4, cudaMemcpyDeviceToHost, s->stream));
+      SCK(s, cudaStreamSynchronize(s->stream));
+      for (int q = 0; q < nb; q++)
+        sens[b0 + q] = std::max(sens[b0 + q], den[q] > 0.f ? std::sqrt(num[q] / den[q]) : INFINITY);
+    }
+  }
   return tc_status(s);
 }
 

@@ -10,17 +10,19 @@ training and inference runs in the library's kernels; the simulator runs the
 cases the gate rejects.
 
     python -m paper_2302_13907_gb300.surrogate_run --pipeline --out-dir DIR \
-        [--phase all|train|test] [--params P] \
+        [--phase all|train|gate|test] [--params P] \
         [--train-seeds 1000:5096] [--test-seeds 9000:9512] [--epochs 400]
 
 runs the job with the refined generator of `surrogate_data`.  Phase "train"
 generates the training cases, trains, chooses the gate's margin on the
 validation cases alone (leave-one-out) and writes DIR/params.npz (weights as
 BF16 bit patterns, biases, normalisation, the gate's validation data and
-margin) and DIR/train_report.json; phase "test" generates the held-out
-cases, times the plain solver on a sample of them, runs the saved network and
-gate, falls back to the simulator on the rejected cases and writes
-DIR/report.json; "all" runs both in one process.
+margin) and DIR/train_report.json; phase "gate" adds the second gate signal
+(the network's sensitivity, `choose_gate`, on the validation cases alone) to
+the saved params; phase "test" generates the held-out cases, times the plain
+solver on a sample of them, runs the saved network and gate, falls back to the
+simulator on the rejected cases and writes DIR/report.json; "all" runs the
+three in one process.
 """
 from __future__ import annotations
 
@@ -121,6 +123,36 @@ def choose_margin(Xn_val, e_val, k, tol=TOL):
     return best
 
 
+SENS_STEP = 0.1  # input move (normalised units) of the sensitivity signal
+
+
+def choose_gate(Xn_val, e_val, s_val, k, tol=TOL):
+    """The two-signal gate chosen on the validation cases alone: accept a
+    query when the largest error among its k nearest validation cases is at
+    most margin x tol (leave one out here) and its sensitivity is at most
+    sens_max.  For each margin (steps of 0.05) sens_max is the largest
+    validation sensitivity below that of every case above tol the neighbour
+    rule lets through (infinite when it lets none through); the pair that
+    accepts the most validation cases wins (the smaller margin on a tie).
+    Returns (margin, sens_max, accepted fraction); no validation case above
+    tol is accepted by construction."""
+    worst = knn_worst(Xn_val, Xn_val, e_val, k, exclude_self=True)
+    bad = e_val > tol
+    best = (0.0, 0.0, 0.0)
+    for m in np.arange(0.05, 1.0001, 0.05):
+        knn_ok = worst <= m * tol
+        through = knn_ok & bad
+        if through.any():
+            below = s_val[s_val < s_val[through].min()]
+            smax = float(below.max()) if below.size else -np.inf
+        else:
+            smax = np.inf
+        acc = float(np.mean(knn_ok & (s_val <= smax)))
+        if acc > best[2]:
+            best = (round(float(m), 2), smax, acc)
+    return best
+
+
 def _load_params(path, arch):
     """A Surrogate holding the saved BF16 weights, normalisation and gate."""
     z = np.load(path)
@@ -129,6 +161,43 @@ def _load_params(path, arch):
     S.set_params(unpack_params(z["w_bf16"], z["biases"], arch))
     S.gate_fit(z["gate_x"], z["gate_err"])
     return S, z
+
+
+def gate_decision(S, X, z, margin=None, sens_max=None):
+    """The saved gate on queries X: the neighbour rule at the saved margin,
+    and, when the saved gate has one, the sensitivity bound."""
+    k = int(z["gate_k"])
+    margin = float(z["gate_margin"]) if margin is None else margin
+    acc = S.gate(X, k=k, tol=TOL * margin)
+    if sens_max is None and "gate_sens_max" in z.files:
+        sens_max = float(z["gate_sens_max"])
+    if sens_max is not None and np.isfinite(sens_max):
+        step = float(z["gate_sens_step"]) if "gate_sens_step" in z.files else SENS_STEP
+        acc &= S.sensitivity(X, step=step) <= sens_max
+    return acc
+
+
+def pipeline_gate(a, log, params):
+    """Add the sensitivity signal to a trained network's gate: the
+    sensitivity of every validation case on the device, then choose_gate on
+    the validation cases alone; the params file is rewritten with the new
+    margin and bound."""
+    from .binding import SURROGATE_DEFAULT
+    S, z = _load_params(params, SURROGATE_DEFAULT)
+    Xv, ev = z["gate_x"].astype(np.float32), z["gate_err"].astype(np.float64)
+    sv = S.sensitivity(Xv, step=SENS_STEP).astype(np.float64)
+    Xn = (Xv - z["x_mean"]) / z["x_scale"]
+    margin, smax, acc = choose_gate(Xn, ev, sv, int(z["gate_k"]))
+    out = {f: z[f] for f in z.files}
+    out.update(gate_margin=np.float64(margin), gate_sens_max=np.float64(smax),
+               gate_sens_step=np.float64(SENS_STEP), gate_sens=sv.astype(np.float32),
+               gate_margin_knn_only=z["gate_margin"] if "gate_margin_knn_only" not in z.files
+               else z["gate_margin_knn_only"])
+    np.savez_compressed(params, **out)
+    log(f"gate: margin {margin}, sensitivity bound {smax:.4g} (step {SENS_STEP}); "
+        f"validation accepted {acc:.3f}; validation sensitivity quantiles "
+        f"{np.quantile(sv, [0.5, 0.9, 0.99]).round(4)}")
+    return margin, smax
 
 
 def pipeline_train(a, log):
@@ -205,16 +274,19 @@ def pipeline_test(a, log, params, train_rep):
     Xt, Yt = Xt.astype(np.float32), Yt.astype(np.float32)
     S, z = _load_params(params, SURROGATE_DEFAULT)
     k, margin = int(z["gate_k"]), float(z["gate_margin"])
+    sens_max = float(z["gate_sens_max"]) if "gate_sens_max" in z.files else None
     S.forward(Xt[:4])
     t0 = time.perf_counter()
     P = S.forward(Xt)
-    acc = S.gate(Xt, k=k, tol=TOL * margin)
+    acc = gate_decision(S, Xt, z)
     t_inf = time.perf_counter() - t0
     e_test = rel_err(P, Yt)
-    # the same gate at other margins on the same answers: the trade-off the chosen margin sits on
+    sens = S.sensitivity(Xt, step=SENS_STEP) if sens_max is not None else None
+    # the neighbour rule alone at other margins on the same answers: the
+    # trade-off the sensitivity bound removes
     sweep = []
     for m in np.arange(0.1, 1.0001, 0.1):
-        am = S.gate(Xt, k=k, tol=TOL * float(m))
+        am = gate_decision(S, Xt, z, margin=float(m), sens_max=np.inf)
         sweep.append({"margin": round(float(m), 2), "accepted_frac": float(am.mean()),
                       "false_accepts": int(np.sum(am & (e_test > TOL))),
                       "max_accepted_rel_l2": float(e_test[am].max()) if am.any() else None})
@@ -238,6 +310,8 @@ def pipeline_test(a, log, params, train_rep):
         "test_rel_l2_median": float(np.median(e_test)), "test_rel_l2_p90": float(np.quantile(e_test, 0.9)),
         "test_rel_l2_max": float(e_test.max()), "test_frac_within_5pct": float(np.mean(e_test <= TOL)),
         "gate_k": k, "gate_margin": margin, "gate_tol": TOL * margin,
+        "gate_sens_max": sens_max, "gate_sens_step": SENS_STEP if sens_max is not None else None,
+        "test_sens": [round(float(x), 5) for x in sens] if sens is not None else None,
         "accepted": int(acc.sum()), "accepted_frac": float(acc.mean()),
         "max_accepted_rel_l2": float(e_test[acc].max()) if acc.any() else None,
         "false_accepts": int(np.sum(acc & (e_test > TOL))),
@@ -263,8 +337,8 @@ def pipeline_test(a, log, params, train_rep):
 
 
 def pipeline(a):
-    """The surrogate job (see the module docstring): phase "train", "test"
-    or "all"; the test phase reads the weights and gate the train phase saved
+    """The surrogate job (see the module docstring): phase "train", "gate",
+    "test" or "all"; the test phase reads the weights and gate the train phase saved
     (--params, by default DIR/params.npz) and the training figures
     (DIR/train_report.json, else the one beside the params)."""
     import os
@@ -273,6 +347,8 @@ def pipeline(a):
     train_rep = None
     if a.phase in ("train", "all"):
         train_rep = pipeline_train(a, log)
+    if a.phase in ("gate", "all"):
+        pipeline_gate(a, log, a.params or os.path.join(a.out_dir, "params.npz"))
     if a.phase in ("test", "all"):
         params = a.params or os.path.join(a.out_dir, "params.npz")
         if train_rep is None:
@@ -287,7 +363,7 @@ def pipeline(a):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--pipeline", action="store_true", help="generate, train, gate and report")
-    ap.add_argument("--phase", choices=("all", "train", "test"), default="all")
+    ap.add_argument("--phase", choices=("all", "train", "gate", "test"), default="all")
     ap.add_argument("--out-dir", default=None)
     ap.add_argument("--train-seeds", default="1000:5096")
     ap.add_argument("--test-seeds", default="9000:9512")

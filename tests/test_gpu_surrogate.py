@@ -159,3 +159,31 @@ def test_adam_steps_match_fp64_adam():
             assert not bad.any(), (t, int(bad.sum()), float(np.abs(w_gpu - w_ref).max()))
             assert np.abs(w_gpu - w).max() > 0.5 * lr  # the step moved the weights
             w = w_gpu
+
+
+def test_sensitivity_against_the_reference_network():
+    """sur_sensitivity (the gate's second signal) against the same quantity
+    from the FP64 reference with the GPU's BF16 rounding points: for each
+    query the largest relative output change over moves of 0.1 along each
+    input, over queries split across several device batches."""
+    from paper_2302_13907_gb300.binding import Surrogate
+    shp = R.shapes()
+    rng = np.random.default_rng(13)
+    X = rng.uniform(-1, 1, (10, 6)).astype(np.float32)
+    with Surrogate(max_batch=4, seed=5) as s:
+        th = s.params()
+        sens = s.sensitivity(X, step=0.1)
+    thb = _bf16_theta(th, shp)
+
+    def f(x):
+        return R.forward(thb, x.astype(np.float64), shp, q=bf16_round).reshape(len(x), -1)
+
+    y0 = f(X)
+    ref = np.zeros(len(X))
+    for d in range(6):
+        Xp = X.copy()
+        Xp[:, d] += np.float32(0.1)  # the move as the library makes it, in FP32
+        ref = np.maximum(ref, np.linalg.norm(f(Xp) - y0, axis=1) / np.linalg.norm(y0, axis=1))
+    print("sensitivity", sens.round(4), "reference", ref.round(4))
+    assert np.all(ref > 0)
+    assert np.all(np.abs(sens - ref) <= 0.05 * ref + 1e-3), (sens, ref)

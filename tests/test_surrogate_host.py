@@ -2,6 +2,7 @@
 BF16 packing of the weights, the gate's nearest-neighbour rule and the
 leave-one-out choice of its margin."""
 import numpy as np
+import pytest
 
 from oracle import surrogate_ref as Ref
 from paper_2302_13907_gb300 import surrogate_run as R
@@ -57,3 +58,29 @@ def test_margin_is_the_largest_that_admits_no_bad_validation_case():
         assert np.any(e[worst <= (m + 0.05) * R.TOL] > R.TOL)
     e_ok = np.full(60, 0.01)
     assert R.choose_margin(X, e_ok, 3) == 1.0
+
+
+def test_two_signal_gate_admits_no_bad_validation_case_and_uses_the_sensitivity():
+    """choose_gate: whatever margin and bound it returns, the gate (neighbour
+    rule leave one out, sensitivity bound) accepts no validation case above
+    the tolerance and the reported share is the share it accepts; a bad case
+    that sits among good neighbours but has a high sensitivity no longer
+    forces the tiny margin the neighbour rule alone needs."""
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((200, 6))
+    e = 0.005 + 0.005 * rng.random(200)
+    sens = 0.01 + 0.01 * rng.random(200)
+    e[[7, 60]] = [0.09, 0.12]       # two bad cases among good neighbours
+    sens[[7, 60]] = [0.08, 0.11]    # with high sensitivity
+    m, smax, acc = R.choose_gate(X, e, sens, 3)
+    worst = R.knn_worst(X, X, e, 3, exclude_self=True)
+    a = (worst <= m * R.TOL) & (sens <= smax)
+    assert np.all(e[a] <= R.TOL)
+    assert acc == pytest.approx(a.mean())
+    assert smax < 0.08 and acc > 0.9
+    m_knn = R.choose_margin(X, e, 3)
+    assert m_knn < m
+    assert acc > np.mean(worst <= m_knn * R.TOL)
+    # no bad case at all: no bound needed
+    m2, smax2, acc2 = R.choose_gate(X, np.full(200, 0.01), sens, 3)
+    assert np.isinf(smax2) and acc2 == 1.0
