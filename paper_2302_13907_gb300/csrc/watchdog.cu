@@ -64,8 +64,8 @@ __global__ void __launch_bounds__(WATCH_THREADS) watch_reduce(const WParams p) {
   }
 }
 
-// one thread: the verdict on the sum the reduction left in acc[0]
-__global__ void watch_judge(const WParams p) {
+// one thread: the decision on the sum the reduction left in acc[0]
+__global__ void watch_check(const WParams p) {
   const int n = *p.step;
   if (n % p.every != 0) return;
   double *a = p.acc;
@@ -97,7 +97,7 @@ cudaError_t launch_watchdog(int storage, const WParams &p, int blocks, cudaStrea
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  watch_judge<<<1, 1, 0, s>>>(p);
+  watch_check<<<1, 1, 0, s>>>(p);
   return cudaGetLastError();
 }
 

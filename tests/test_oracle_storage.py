@@ -19,7 +19,7 @@ from paper_2302_13907_gb300 import workloads as W
 
 
 # ---------------------------------------------------------------- time step (R7)
-# Hand values (survey of the workloads, reading c-7):
+# Hand values of the time step, worked out from each geometry (reading R7):
 #  * 70x16x320 cased well, dr = dz = 5 mm, 16 azimuthal nodes: the innermost
 #    steel cell (centre 0.1025 m, Vp 5900 m/s) limits: 2.985e-7 s.
 #  * the 20 m well, dr = dz = 2.5 mm, 64 nodes: the axis liquid ring
