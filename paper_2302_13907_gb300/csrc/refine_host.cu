@@ -49,6 +49,13 @@ struct simr_s {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // streams of the zones other than the largest in each half (forked from
+  // `stream` by zfork, joined back by zjoin): the zones of a half update
+  // disjoint arrays from inputs no launch of the half writes
+  static constexpr int MAX_ZSTREAMS = 7;
+  cudaStream_t zs[MAX_ZSTREAMS] = {};
+  cudaEvent_t zfork = nullptr, zjoin[MAX_ZSTREAMS] = {};
+  int big_zone = 0;
   sim_grid_t grid{};
   int NR = 0, NZ = 0, NZp = 0, M = 0;
   double dt = 0;
@@ -107,6 +114,11 @@ void rrelease(simr_t *h) {
   for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
   h->allocs.clear();
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int k = 0; k < simr_t::MAX_ZSTREAMS; k++) {
+    if (h->zs[k]) cudaStreamDestroy(h->zs[k]);
+    if (h->zjoin[k]) cudaEventDestroy(h->zjoin[k]);
+  }
+  if (h->zfork) cudaEventDestroy(h->zfork);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -125,15 +137,34 @@ bool pow2_in(int n) { return n == 4 || n == 8 || n == 16 || n == 32 || n == 64; 
 // interior and edge for the stresses)
 constexpr int REFINED_VEL_CODE = 2285, REFINED_STR_CODE = 2294;
 
+// one half of every zone: the largest zone on the handle's stream, each other
+// zone on a stream of its own forked from it, all joined back before the
+// interface transfer that follows
+cudaError_t zones_half(simr_t *h, int code, int parts) {
+  const int nz = (int)h->kps.size();
+  cudaError_t e = cudaSuccess;
+  if (nz > 1) {
+    e = cudaEventRecord(h->zfork, h->stream);
+    for (int k = 0; k < nz - 1 && e == cudaSuccess; k++) e = cudaStreamWaitEvent(h->zs[k], h->zfork, 0);
+  }
+  for (int m = 0, k = 0; m < nz && e == cudaSuccess; m++) {
+    const cudaStream_t st = m == h->big_zone ? h->stream : h->zs[k++];
+    e = launch_hoist(0, code, h->kps[m], st, nullptr, parts);
+  }
+  for (int k = 0; k < nz - 1 && e == cudaSuccess; k++) {
+    e = cudaEventRecord(h->zjoin[k], h->zs[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->zjoin[k], 0);
+  }
+  return e;
+}
+
 cudaError_t enqueue_refined_step(simr_t *h) {
   cudaError_t e = cudaSuccess;
   const bool force = h->src_kind == 1 || h->src_kind == 2;
-  for (size_t m = 0; m < h->kps.size() && e == cudaSuccess; m++)
-    e = launch_hoist(0, REFINED_VEL_CODE, h->kps[m], h->stream, nullptr, 1);
+  e = zones_half(h, REFINED_VEL_CODE, 1);
   if (e == cudaSuccess && force) e = launch_inject(0, h->ip, h->stream);
   if (e == cudaSuccess) e = launch_xfer(h->xv, h->stream);
-  for (size_t m = 0; m < h->kps.size() && e == cudaSuccess; m++)
-    e = launch_hoist(0, REFINED_STR_CODE, h->kps[m], h->stream, nullptr, 2);
+  if (e == cudaSuccess) e = zones_half(h, REFINED_STR_CODE, 2);
   if (e == cudaSuccess && h->src_kind == 3) e = launch_inject(0, h->ip, h->stream);
   if (e == cudaSuccess) e = launch_xfer(h->xs, h->stream);
   if (e == cudaSuccess) e = launch_batch_receivers(0, h->d_rp, (int)h->kps.size(), h->stream);
@@ -457,6 +488,21 @@ extern "C" int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, co
     r.step = Z.step;
     r.status = h->status;
     h->kps.push_back(p);
+  }
+  // the zones' streams: the largest zone stays on the handle's stream
+  {
+    long long most = -1;
+    for (int m = 0; m < M; m++) {
+      const long long cells = (long long)h->kps[m].nth * (h->kps[m].i_hi - h->kps[m].i_lo);
+      if (cells > most) most = cells, h->big_zone = m;
+    }
+    for (int k = 0; k < M - 1; k++) {
+      if ((e = cudaStreamCreateWithFlags(&h->zs[k], cudaStreamNonBlocking)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&h->zjoin[k], cudaEventDisableTiming)) != cudaSuccess)
+        return bail(rcuda(h, e, "zone streams"));
+    }
+    if (M > 1 && (e = cudaEventCreateWithFlags(&h->zfork, cudaEventDisableTiming)) != cudaSuccess)
+      return bail(rcuda(h, e, "zone streams"));
   }
   {
     std::vector<RParams> rp(M);
