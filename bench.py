@@ -329,7 +329,7 @@ def bench_batch_small(stream, n_cases=64, steps=400, warm=8, rank=0, ws=1, pg=No
             "workload": "64 miniature cement cases: 44 x 8 x 256 cells with PML, FP32"}
 
 
-def bench_refined(stream, sc, uniform_value, uniform_dt, steps=400, warm=20):
+def bench_refined(stream, sc, uniform_value, uniform_dt, steps=400, warm=20, tile=0):
     """The same well on the azimuthally refined grid (zones by the paper's
     rule, Sec. 3: 4 / 8 / 16 / 32 / 64 azimuthal nodes from the axis out):
     cell-update throughput, and the physical time simulated per wall-clock
@@ -342,7 +342,8 @@ def bench_refined(stream, sc, uniform_value, uniform_dt, steps=400, warm=20):
     g = sc.grid
     rows = W.refinement_rows(g)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with RefinedSimulation(sc, rows, graph_chunk=steps // 2, stream=stream.cuda_stream, max_steps=steps + warm) as r:
+    with RefinedSimulation(sc, rows, graph_chunk=steps // 2, stream=stream.cuda_stream, max_steps=steps + warm,
+                           tile=tile) as r:
         r.step(warm)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()  # a second profiler range: the refined grid's timed steps
@@ -361,6 +362,7 @@ def bench_refined(stream, sc, uniform_value, uniform_dt, steps=400, warm=20):
             "gcell_updates_per_s": cells * steps / t / 1e9, "cells_per_step": cells,
             "uniform_cells_per_step": uniform_cells, "dt": dt, "uniform_dt": uniform_dt,
             "zones": [{"first_row": a, "rows": b, "nth": c} for a, b, c in zones], "steps_timed": steps,
+            "split_codes": tile or 22852324,
             "error": "GPU vs the refined FP64 oracle: fields <= 2e-5 of scale, traces <= 1e-4 rel-L2 (tested)"}
 
 
@@ -490,6 +492,8 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16", "f16sr"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused", "fused4", "march", "sweep"])
     ap.add_argument("--tile", type=int, default=0, help="tile code to force (0: the autotuner picks)")
+    ap.add_argument("--refined-tile", type=int, default=0,
+                    help="split code (or pair) of the refined grid's zones (0: 2285 / 2324)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nz", type=int, default=8192, help="interior z cells (8192 = the 20 m well; smaller for profiling)")
@@ -648,7 +652,7 @@ def main():
         batch["small_cases"] = bench_batch_small(stream, rank=rank, ws=ws, pg=pg)
     refined = None
     if not args.no_refined and args.storage == "f32" and args.nz == 8192 and args.nr == 180:
-        refined = bench_refined(stream, sc, value / ws, uniform_dt)
+        refined = bench_refined(stream, sc, value / ws, uniform_dt, tile=args.refined_tile)
     surrogate = None
     if not args.no_surrogate and rank == 0:
         surrogate = bench_surrogate(stream)

@@ -393,7 +393,10 @@ const char *simb_last_error(const simb_t *b);
  * rows per zone, the radial PML inside the last zone (row0 <= nr - 2); FP32
  * storage; any source kind, placed on the nodes of the zone that holds it
  * (the transverse force off the axis and the torsion ring not on a zone's
- * first row, SIM_EUNSUPPORTED).
+ * first row, SIM_EUNSUPPORTED).  Every zone runs the split kernels, velocity
+ * code 2285 and stress code 2324 unless opts.tile names a 22xx / 23xx split
+ * code or pair code (SIM_EINVAL otherwise); the zones of a half run on
+ * parallel streams.
  * Ownership and errors as sim_create; simr_last_error(NULL) after a failed create.
  * ------------------------------------------------------------------------ */
 typedef struct {

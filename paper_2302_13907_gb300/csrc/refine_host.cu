@@ -56,6 +56,7 @@ struct simr_s {
   cudaStream_t zs[MAX_ZSTREAMS] = {};
   cudaEvent_t zfork = nullptr, zjoin[MAX_ZSTREAMS] = {};
   int big_zone = 0;
+  int vel_code = 0, str_code = 0;  // split codes of every zone's halves
   sim_grid_t grid{};
   int NR = 0, NZ = 0, NZp = 0, M = 0;
   double dt = 0;
@@ -132,10 +133,16 @@ double dirichlet(int N, double t) {
 
 bool pow2_in(int n) { return n == 4 || n == 8 || n == 16 || n == 32 || n == 64; }
 
-// split codes each zone's halves run with: the single-well tuner's pair on the
-// 20 m well (plain interior + prefetching edge for the velocities, prefetching
-// interior and edge for the stresses)
-constexpr int REFINED_VEL_CODE = 2285, REFINED_STR_CODE = 2294;
+// split codes each zone's halves run with, the fastest pair measured on the
+// 20 m well's zones: plain interior + prefetching edge for the velocities;
+// prefetching interior, radial-PML rows and z ends for the stresses
+constexpr int REFINED_VEL_CODE = 2285, REFINED_STR_CODE = 2324;
+// opts.tile of a refined handle: 0, or a split code or pair code whose halves
+// are interior / edge (22xx) or three-way (23xx) split codes
+bool refined_tile_ok(int t) {
+  auto ok = [](int c) { return c >= 2200 && c < 2400; };
+  return t == 0 || (is_split_single(t) && ok(t)) || (is_split_pair(t) && ok(split_vel_code(t)) && ok(split_str_code(t)));
+}
 
 // one half of every zone: the largest zone on the handle's stream, each other
 // zone on a stream of its own forked from it, all joined back before the
@@ -161,10 +168,10 @@ cudaError_t zones_half(simr_t *h, int code, int parts) {
 cudaError_t enqueue_refined_step(simr_t *h) {
   cudaError_t e = cudaSuccess;
   const bool force = h->src_kind == 1 || h->src_kind == 2;
-  e = zones_half(h, REFINED_VEL_CODE, 1);
+  e = zones_half(h, h->vel_code, 1);
   if (e == cudaSuccess && force) e = launch_inject(0, h->ip, h->stream);
   if (e == cudaSuccess) e = launch_xfer(h->xv, h->stream);
-  if (e == cudaSuccess) e = zones_half(h, REFINED_STR_CODE, 2);
+  if (e == cudaSuccess) e = zones_half(h, h->str_code, 2);
   if (e == cudaSuccess && h->src_kind == 3) e = launch_inject(0, h->ip, h->stream);
   if (e == cudaSuccess) e = launch_xfer(h->xs, h->stream);
   if (e == cudaSuccess) e = launch_batch_receivers(0, h->d_rp, (int)h->kps.size(), h->stream);
@@ -201,6 +208,8 @@ extern "C" int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, co
     return rfail(nullptr, SIM_EUNSUPPORTED, "refined grid: no device watchdog (uniform-grid handles only)");
   if (opts->kernel != SIM_KERNEL_AUTO && opts->kernel != SIM_KERNEL_SPLIT)
     return rfail(nullptr, SIM_EUNSUPPORTED, "refined grid: the split kernels only");
+  if (!refined_tile_ok(opts->tile))
+    return rfail(nullptr, SIM_EINVAL, "refined grid: opts.tile must be 0 or a 22xx / 23xx split code or pair");
   if (M < 1 || M > 5 || (M > 1 && !zones->row0)) return rfail(nullptr, SIM_EINVAL, "zones: 1 to 5 zones");
   const int nth0 = g.nth >> (M - 1);
   if (nth0 < 4 || (nth0 << (M - 1)) != g.nth || (nth0 & 1))
@@ -503,6 +512,19 @@ extern "C" int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, co
     }
     if (M > 1 && (e = cudaEventCreateWithFlags(&h->zfork, cudaEventDisableTiming)) != cudaSuccess)
       return bail(rcuda(h, e, "zone streams"));
+  }
+  // the zones' split codes; a forced one is tried once per half on the still
+  // zero state of zone 0 with the source off (the state stays zero)
+  h->vel_code = opts->tile ? split_vel_code(opts->tile) : REFINED_VEL_CODE;
+  h->str_code = opts->tile ? split_str_code(opts->tile) : REFINED_STR_CODE;
+  if (opts->tile) {
+    KParams dry = h->kps[0];
+    dry.src_i = -1;
+    e = launch_hoist(0, h->vel_code, dry, h->stream, nullptr, 1);
+    if (e == cudaSuccess) e = launch_hoist(0, h->str_code, dry, h->stream, nullptr, 2);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaErrorInvalidValue) return bail(rfail(h, SIM_EINVAL, "opts.tile: no such split code"));
+    if (e != cudaSuccess) return bail(rcuda(h, e, "opts.tile"));
   }
   {
     std::vector<RParams> rp(M);

@@ -105,6 +105,7 @@ def _refined(nth=16, nr=16):
     ([4, 8], dict(nth=24), B.SIM_EINVAL),                 # nth not a power of two
     ([4, 8], dict(source_kind=1, source_r=0.02), B.SIM_EUNSUPPORTED),  # force node on a zone's first row
     ([4, 8], dict(watchdog_every=10), B.SIM_EUNSUPPORTED),  # no watchdog on the refined grid
+    ([4, 8], dict(tile=2004), B.SIM_EINVAL),              # zones run 22xx / 23xx split codes only
 ])
 def test_refined_grid_host_validation(rows, kw, code):
     """simr_create checks its zones, storage, kernel and source on the host

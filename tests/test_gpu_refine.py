@@ -36,11 +36,11 @@ def _ragged(seed=0, nth=16, nr=14, nz=61, kind=0, src_r=0.0, steps=200):
     return W.Scenario("ragged-refined", med, src, rec, steps=steps)
 
 
-def _compare(sc, rows, steps):
+def _compare(sc, rows, steps, tile=0):
     from paper_2302_13907_gb300.binding import RefinedSimulation
     o = oracle.RefinedOracle(sc, rows=rows)
     o.step(steps)
-    with RefinedSimulation(sc, rows, graph_chunk=32) as s:
+    with RefinedSimulation(sc, rows, graph_chunk=32, tile=tile) as s:
         assert s.dt == pytest.approx(o.dt, rel=1e-15)
         assert [z[:3] for z in o.zones] == s.zones
         s.step(steps)
@@ -75,6 +75,15 @@ def test_refined_fields_elementwise(rows, kind, src_r):
     row0 = [0] + rows + [g.NR]
     M = len(rows) + 1
     assert cells == sum((nth >> (M - 1 - m)) * (row0[m + 1] - row0[m]) * g.NZ for m in range(M))
+
+
+@pytest.mark.parametrize("tile", [2204, 22852324, 23342305])
+def test_refined_zones_on_other_split_codes(tile):
+    """opts.tile of a refined handle: every zone's halves on the split code(s)
+    named (interior / edge and three-way, one code or a pair), against the
+    oracle as above."""
+    sc = _ragged(seed=5, nth=16, kind=0, src_r=0.0305)
+    _compare(sc, [4, 8], steps=120, tile=tile)
 
 
 def test_single_zone_equals_uniform_simulator():
