@@ -493,7 +493,7 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "split", "fused", "fused4", "march", "sweep"])
     ap.add_argument("--tile", type=int, default=0, help="tile code to force (0: the autotuner picks)")
     ap.add_argument("--refined-tile", type=int, default=0,
-                    help="split code (or pair) of the refined grid's zones (0: 2285 / 2324)")
+                    help="split code (or pair) of the refined grid's zones (0: the library's choice by size)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nz", type=int, default=8192, help="interior z cells (8192 = the 20 m well; smaller for profiling)")

@@ -394,9 +394,10 @@ const char *simb_last_error(const simb_t *b);
  * storage; any source kind, placed on the nodes of the zone that holds it
  * (the transverse force off the axis and the torsion ring not on a zone's
  * first row, SIM_EUNSUPPORTED).  Every zone runs the split kernels, velocity
- * code 2285 and stress code 2324 unless opts.tile names a 22xx / 23xx split
- * code or pair code (SIM_EINVAL otherwise); the zones of a half run on
- * parallel streams.
+ * code 2285 and stress code 2324 (largest zone of at least 8 Mi cells; the
+ * zones of a half then run on parallel streams) or 2294 (smaller grids, zones
+ * one after another) unless opts.tile names a 22xx / 23xx split code or pair
+ * code (SIM_EINVAL otherwise).
  * Ownership and errors as sim_create; simr_last_error(NULL) after a failed create.
  * ------------------------------------------------------------------------ */
 typedef struct {

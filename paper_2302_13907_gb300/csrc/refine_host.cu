@@ -56,6 +56,7 @@ struct simr_s {
   cudaStream_t zs[MAX_ZSTREAMS] = {};
   cudaEvent_t zfork = nullptr, zjoin[MAX_ZSTREAMS] = {};
   int big_zone = 0;
+  bool zone_streams = false;
   int vel_code = 0, str_code = 0;  // split codes of every zone's halves
   sim_grid_t grid{};
   int NR = 0, NZ = 0, NZp = 0, M = 0;
@@ -133,10 +134,14 @@ double dirichlet(int N, double t) {
 
 bool pow2_in(int n) { return n == 4 || n == 8 || n == 16 || n == 32 || n == 64; }
 
-// split codes each zone's halves run with, the fastest pair measured on the
-// 20 m well's zones: plain interior + prefetching edge for the velocities;
-// prefetching interior, radial-PML rows and z ends for the stresses
-constexpr int REFINED_VEL_CODE = 2285, REFINED_STR_CODE = 2324;
+// split codes each zone's halves run with, the fastest pairs measured: plain
+// interior + prefetching edge for the velocities; for the stresses on a grid
+// whose largest zone fills the GPU (the 20 m well) the three-way split with
+// the zones on parallel streams, on a smaller one (a 1.6 m crop, several
+// handles side by side) the prefetching interior and edge kernels with the
+// zones one after another, whose fewer launches pay there
+constexpr int REFINED_VEL_CODE = 2285, REFINED_STR_CODE = 2324, REFINED_STR_CODE_SMALL = 2294;
+constexpr long long ZONE_STREAM_CELLS = 8LL << 20;
 // opts.tile of a refined handle: 0, or a split code or pair code whose halves
 // are interior / edge (22xx) or three-way (23xx) split codes
 bool refined_tile_ok(int t) {
@@ -146,9 +151,17 @@ bool refined_tile_ok(int t) {
 
 // one half of every zone: the largest zone on the handle's stream, each other
 // zone on a stream of its own forked from it, all joined back before the
-// interface transfer that follows
+// interface transfer that follows.  Only where the largest zone fills the GPU
+// by itself (ZONE_STREAM_CELLS): on small grids the zones run one after
+// another, since several such handles usually run side by side already and the
+// extra streams there cost more than they overlap.
 cudaError_t zones_half(simr_t *h, int code, int parts) {
-  const int nz = (int)h->kps.size();
+  const int nz = h->zone_streams ? (int)h->kps.size() : 1;
+  if (!h->zone_streams) {  // one after another on the handle's stream
+    cudaError_t e = cudaSuccess;
+    for (size_t m = 0; m < h->kps.size() && e == cudaSuccess; m++) e = launch_hoist(0, code, h->kps[m], h->stream, nullptr, parts);
+    return e;
+  }
   cudaError_t e = cudaSuccess;
   if (nz > 1) {
     e = cudaEventRecord(h->zfork, h->stream);
@@ -502,9 +515,10 @@ extern "C" int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, co
   {
     long long most = -1;
     for (int m = 0; m < M; m++) {
-      const long long cells = (long long)h->kps[m].nth * (h->kps[m].i_hi - h->kps[m].i_lo);
+      const long long cells = (long long)h->kps[m].nth * (h->kps[m].i_hi - h->kps[m].i_lo) * NZ;
       if (cells > most) most = cells, h->big_zone = m;
     }
+    h->zone_streams = M > 1 && most >= ZONE_STREAM_CELLS;
     for (int k = 0; k < M - 1; k++) {
       if ((e = cudaStreamCreateWithFlags(&h->zs[k], cudaStreamNonBlocking)) != cudaSuccess ||
           (e = cudaEventCreateWithFlags(&h->zjoin[k], cudaEventDisableTiming)) != cudaSuccess)
@@ -516,7 +530,9 @@ extern "C" int simr_create(const sim_grid_t *grid, const simr_zones_t *zones, co
   // the zones' split codes; a forced one is tried once per half on the still
   // zero state of zone 0 with the source off (the state stays zero)
   h->vel_code = opts->tile ? split_vel_code(opts->tile) : REFINED_VEL_CODE;
-  h->str_code = opts->tile ? split_str_code(opts->tile) : REFINED_STR_CODE;
+  h->str_code = opts->tile            ? split_str_code(opts->tile)
+                : h->zone_streams ? REFINED_STR_CODE
+                                  : REFINED_STR_CODE_SMALL;
   if (opts->tile) {
     KParams dry = h->kps[0];
     dry.src_i = -1;

@@ -51,13 +51,15 @@ def window_times(sc):
     return dt, (m + 1) * dt
 
 
-def _refined_start(sc, stream=None, reach=1.6, chunk=128):
+def _refined_start(sc, stream=None, reach=1.6, chunk=128, tile=0):
     """Create the refined-grid handle of a case's reach crop and enqueue its
-    steps (asynchronous); returns (handle, uniform window times, steps)."""
+    steps (asynchronous); returns (handle, uniform window times, steps).
+    tile: the zones' split codes (0: the library's default)."""
     from .binding import RefinedSimulation
     dt_u, t = window_times(sc)
     crop = W.reach_crop(sc, reach)
-    R = RefinedSimulation(crop, W.refinement_rows(crop.grid), graph_chunk=chunk, stream=stream, max_steps=sc.steps)
+    R = RefinedSimulation(crop, W.refinement_rows(crop.grid), graph_chunk=chunk, stream=stream, max_steps=sc.steps,
+                          tile=tile)
     # the refined step is the larger one, so sc.steps samples cover the window
     n = int(np.ceil(t[-1] / R.dt)) + 1
     if n > sc.steps:
@@ -82,7 +84,7 @@ def refined_window(sc, stream=None, reach=1.6):
     return _refined_finish(*_refined_start(sc, stream, reach))
 
 
-def generate_refined(seeds, stream=None, log=print, every=256, slots=6):
+def generate_refined(seeds, stream=None, log=print, every=256, slots=6, tile=0):
     """Refined-window traces of many cases, `slots` of them in flight at once:
     each on its own stream (the handles free their memory stream-ordered), so
     one case's launches fill what another's leave idle and the host builds the
@@ -104,7 +106,7 @@ def generate_refined(seeds, stream=None, log=print, every=256, slots=6):
 
     for q, s in enumerate(seeds):
         sc = W.scenario_case(s, surrogate_inputs=True)
-        pending.append((q, W.surrogate_features(sc), _refined_start(sc, None if slots > 1 else stream)))
+        pending.append((q, W.surrogate_features(sc), _refined_start(sc, None if slots > 1 else stream, tile=tile)))
         if len(pending) >= slots:
             finish()
     while pending:
