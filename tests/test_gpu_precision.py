@@ -103,8 +103,9 @@ def _ulp(x, storage):
 FLIP_FRACTION = {"bf16": 1e-3, "f16": 1e-2, "f16sr": 3e-2}
 
 
+@pytest.mark.parametrize("kernel", ["auto", "sweep"])
 @pytest.mark.parametrize("storage", ["bf16", "f16", "f16sr"])
-def test_reduced_storage_step_matches_the_rounded_oracle(storage):
+def test_reduced_storage_step_matches_the_rounded_oracle(storage, kernel):
     """One leapfrog step of the GPU's 16-bit storage path against one step of
     the oracle with the same storage rounding, both started from the GPU's
     state after 700 steps (near the Ricker peak) of the 70x16x320 well with
@@ -116,13 +117,15 @@ def test_reduced_storage_step_matches_the_rounded_oracle(storage):
     everywhere.  Over hundreds of steps such one-ulp differences seed others
     (an increment of the order of the storage ulp makes every rounding
     decision sensitive), so long runs are compared with the FP64 oracle
-    instead (above)."""
+    instead (above).  Both the split kernels the tuner picks and the
+    single-pass sweep kernel."""
     import oracle
     from paper_2302_13907_gb300.binding import Simulation
     sc = W.config1(steps=701)
     scales = fp16_scales(sc) if storage in ("f16", "f16sr") else (1.0, 1.0)
     n = 700
-    with Simulation(sc, storage=storage, pml_on=False) as s:
+    with Simulation(sc, storage=storage, pml_on=False, kernel=kernel) as s:
+        assert (s.config()[0] == 5) == (kernel == "sweep")
         s.step(n)
         before = {f: s.field(f).astype(np.float64) for f in oracle.FIELDS}
         s.step(1)
