@@ -220,6 +220,31 @@ def test_checkpoint_resume_bitwise():
             assert np.array_equal(c.field("vz"), ref_f)
 
 
+def test_checkpoint_resume_bitwise_with_stochastic_rounding_and_watchdog():
+    """FP16 storage with stochastic rounding: the dithers are keyed on the
+    device step counter, which the checkpoint carries, so the resumed run
+    repeats the uninterrupted one bit for bit, and the watchdog's energy
+    proxy after it equals the uninterrupted run's."""
+    sc = W.config1(steps=120)
+    kw = dict(storage="f16sr", watchdog_every=10)
+    with sim(sc, **kw) as a:
+        a.step(120)
+        ref, ref_f, ref_w = a.traces(), a.field("srr"), a.watchdog()
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        with sim(sc, **kw) as b:
+            b.step(50)
+            b.save(path)
+        with sim(sc, **kw) as c:
+            c.load(path)
+            c.step(70)
+            assert np.array_equal(c.traces(), ref)
+            assert np.array_equal(c.field("srr"), ref_f)
+            e, r, n = c.watchdog()
+            assert n == 120 and e == pytest.approx(ref_w[0], rel=1e-12)
+            c.sync()
+
+
 def test_trace_capacity_and_stepping_beyond():
     sc = W.config1(steps=800)
     o = oracle.Oracle(sc)
