@@ -153,7 +153,7 @@ def choose_gate(Xn_val, e_val, s_val, k, tol=TOL):
     return best
 
 
-def _load_params(path, arch):
+def load_params(path, arch):
     """A Surrogate holding the saved BF16 weights, normalisation and gate."""
     z = np.load(path)
     S = Surrogate(max_batch=64, seed=0)
@@ -183,7 +183,7 @@ def pipeline_gate(a, log, params):
     the validation cases alone; the params file is rewritten with the new
     margin and bound."""
     from .binding import SURROGATE_DEFAULT
-    S, z = _load_params(params, SURROGATE_DEFAULT)
+    S, z = load_params(params, SURROGATE_DEFAULT)
     Xv, ev = z["gate_x"].astype(np.float32), z["gate_err"].astype(np.float64)
     sv = S.sensitivity(Xv, step=SENS_STEP).astype(np.float64)
     Xn = (Xv - z["x_mean"]) / z["x_scale"]
@@ -272,7 +272,7 @@ def pipeline_test(a, log, params, train_rep):
         plain_t.append(time.perf_counter() - t0)
         plain_err.append(float(np.linalg.norm(y_ref - tr) / np.linalg.norm(tr)))
     Xt, Yt = Xt.astype(np.float32), Yt.astype(np.float32)
-    S, z = _load_params(params, SURROGATE_DEFAULT)
+    S, z = load_params(params, SURROGATE_DEFAULT)
     k, margin = int(z["gate_k"]), float(z["gate_margin"])
     sens_max = float(z["gate_sens_max"]) if "gate_sens_max" in z.files else None
     S.forward(Xt[:4])
