@@ -18,20 +18,26 @@ from tests.helpers import rel_l2
 pytestmark = pytest.mark.gpu
 
 
-def _scenario(kind=0):
+def _scenario(kind=0, ks=None):
+    """ks: the stored z index of the source (None: z = 0.36 m)."""
     g = W.Grid(nr=40, nth=16, nz=300, pml_r=8, pml_z=8, dr=0.004, dz=0.003)
     med = W.cased_well(g, z_top=0.5, casing_in=0.08, casing_t=0.01, cement_out=0.12)
     rec = W.Receivers(r=np.array([0.0, 0.013, 0.0, 0.03]), theta=np.array([0.0, 1.1, 0.0, 2.0]),
                       z=np.array([0.1, 0.35, 0.5, 0.8]))
-    src = W.Source(kind=kind, r=0.006 if kind != 3 else 0.085, theta=0.4, z=0.36, f0=40e3)
+    z = 0.36 if ks is None else (ks - g.pml_z) * g.dz
+    src = W.Source(kind=kind, r=0.006 if kind != 3 else 0.085, theta=0.4, z=z, f0=40e3)
     return W.Scenario("slabs", med, src, rec, steps=400)
 
 
-@pytest.mark.parametrize("ws,kind", [(2, 0), (3, 0), (2, 1), (3, 3)])
-def test_slabs_reproduce_the_whole_well(ws, kind):
+@pytest.mark.parametrize("ws,kind,ks", [(2, 0, None), (3, 0, None), (2, 1, None), (3, 3, None),
+                                        # on the cut of two slabs (stored k 160 is slab 1's first cell)
+                                        (2, 0, 160), (2, 1, 159), (2, 2, 159)])
+def test_slabs_reproduce_the_whole_well(ws, kind, ks):
     import torch
     from paper_2302_13907_gb300.binding import Simulation
-    sc = _scenario(kind)
+    sc = _scenario(kind, ks)
+    if ks is not None:
+        assert slabs.plan(sc.grid.NZ, 2).owned(1)[0] == 160
     g = sc.grid
     p = slabs.plan(g.NZ, ws)
     stream = torch.cuda.current_stream().cuda_stream

@@ -3,7 +3,8 @@ the CPU: each rank runs the FP64 oracle on its slab only (updates, sources
 and receivers restricted to its own z cells) and swaps the boundary planes
 of the fields it just updated with its neighbours after each half-step
 (paper_2302_13907_gb300/slabs.py).  Every field of every owned cell and
-every receiver trace equals the undivided oracle run bit for bit."""
+every receiver trace equals the undivided oracle run bit for bit, also with
+the volumetric source and the two point forces placed on a slab boundary."""
 import json
 import os
 import socket
@@ -21,13 +22,16 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _scenario():
+def _scenario(kind=0, ks=None):
+    """ks: the stored z index of the source (None: z = 0.1 m); on a cut the
+    source's nodes fall on both sides of a slab boundary."""
     from paper_2302_13907_gb300 import workloads as W
     g = W.Grid(nr=12, nth=6, nz=70, pml_r=4, pml_z=4, dr=0.004, dz=0.003)
     med = W.cased_well(g, z_top=0.12, casing_in=0.016, casing_t=0.008, cement_out=0.032)
     rec = W.Receivers(r=np.array([0.0, 0.013, 0.0, 0.03]), theta=np.array([0.0, 1.1, 0.0, 2.0]),
                       z=np.array([0.02, 0.09, 0.16, 0.2]))
-    return W.Scenario("slabs", med, W.Source(r=0.006, theta=0.4, z=0.1, f0=60e3), rec, steps=160)
+    z = 0.1 if ks is None else (ks - g.pml_z) * g.dz
+    return W.Scenario("slabs", med, W.Source(kind=kind, r=0.006, theta=0.4, z=z, f0=60e3), rec, steps=160)
 
 
 class OracleSlab:
@@ -62,12 +66,12 @@ class OracleSlab:
             self.o.field(f)[:, :, k0:k0 + a.shape[-1]] = a[q]
 
 
-def _rank(rank, ws, port, out_dir):
+def _rank(rank, ws, port, out_dir, kind=0, ks=None):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
     dist.init_process_group("gloo", rank=rank, world_size=ws)
     try:
-        sc = _scenario()
+        sc = _scenario(kind, ks)
         p = slabs.plan(sc.grid.NZ, ws)
         s0, s1 = p.owned(rank)
         e = OracleSlab(sc, s0, s1)
@@ -80,11 +84,15 @@ def _rank(rank, ws, port, out_dir):
 
 
 @pytest.mark.timeout(600)
-@pytest.mark.parametrize("ws", [2, 3])
-def test_slab_ranks_reproduce_the_whole_well(tmp_path, ws):
+@pytest.mark.parametrize("ws,kind,ks", [(2, 0, None), (3, 0, None),
+                                        # on the cut of two slabs (stored k 40 is rank 1's first cell)
+                                        (2, 0, 40), (2, 1, 39), (2, 2, 39)])
+def test_slab_ranks_reproduce_the_whole_well(tmp_path, ws, kind, ks):
     import oracle
-    mp.spawn(_rank, args=(ws, _free_port(), str(tmp_path)), nprocs=ws, join=True)
-    sc = _scenario()
+    if ks is not None:
+        assert slabs.plan(78, 2).owned(1)[0] == 40
+    mp.spawn(_rank, args=(ws, _free_port(), str(tmp_path), kind, ks), nprocs=ws, join=True)
+    sc = _scenario(kind, ks)
     ref = oracle.Oracle(sc)
     ref.step(sc.steps)
     p = slabs.plan(sc.grid.NZ, ws)
